@@ -1,0 +1,413 @@
+#!/usr/bin/env python
+"""Benchmark of the EAM lattice-list MD step on one GB300 (or N replicas).
+
+Workload (the roofline headline case): bcc Fe-like crystal of 300 x 300 x 300
+cells (54,000,000 atoms), Finnis-Sinclair/Morse EAM tabulated on 5000-knot
+splines, Maxwell velocities at 600 K (seed 2), a 10 keV knock-on atom along a
+seeded direction, adaptive timestep (1 fs cap, 0.02 A max displacement),
+hash update every 10 steps, FP32 force path with FP64 integration.  A bench
+"step" is one full MD step (kick/drift, hash update, density, embedding,
+force, kick, next timestep).  The state (~8 GB) is far larger than L2, so no
+flush is needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores instead (the baseline arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2107_07866_gb300 import synth  # noqa: E402
+
+METRIC = "EAM atom-steps/s at 54M atoms, FP32-force vs FP64 path; % HBM roofline"
+UNIT = "atom-steps/s"
+
+# Algorithmic work per site and pass ("Roofline"): FP32 flops with
+# FMA = 2, counted from the method's arithmetic: 112 offset candidates (the
+# neighbour offset index out to rc + 2 skin), 58 pairs inside rc per atom of
+# the crystal.
+CAND, PAIRS = 112, 58
+FLOP_CAND, FLOP_DENS_PAIR, FLOP_FORCE_PAIR = 11, 21, 41
+FLOPS_FORCE_SITE = CAND * FLOP_CAND + PAIRS * FLOP_FORCE_PAIR
+FLOPS_DENS_SITE = CAND * FLOP_CAND + PAIRS * FLOP_DENS_PAIR
+# FP32 peak: 152 SMs x 128 lanes x 2 flops (FMA) x 2.07 GHz max SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Algorithmic HBM bytes per atom-step of the whole FP32-force step:
+#   kick/drift: read u64, v64, a32 (60), write u64, v64, u32 shadow (60)
+#   density:    read u32 (12), write F' (4)
+#   force:      read u32 (12), F' (4), v64 (24); write v64 (24), a32 (12)
+BYTES_STEP_FP32 = 120 + 16 + 76
+BYTES_FORCE_SITE = 76
+# DRAM traffic of k_force<float> per launch from one ncu capture, scaled to
+# the 54M-atom launch, keyed by the kernel source it was measured on.
+NCU_FORCE_TRAFFIC = {"source_sha": None, "bytes_per_launch": None}
+
+
+def kernel_source_sha():
+    p = os.path.join(ROOT, "paper_2107_07866_gb300", "csrc", "misa_kernels.cuh")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [t.strip() for t in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), f[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+WORKLOADS = {
+    # headline: the 54M-atom FP32-force cascade
+    "c3": dict(n=300, T=600.0, seed=2, pka_eV=10000.0, dx_max=0.02, reassign=10,
+               desc="300x300x300 cells (54,000,000 atoms), 600 K seed 2, 10 keV PKA, FP32 forces, "
+                    "adaptive dt (1 fs, 0.02 A), hash update every 10 steps"),
+    # smaller cascade (parity-size check of the bench path)
+    "c2": dict(n=100, T=600.0, seed=1, pka_eV=5000.0, dx_max=0.02, reassign=1,
+               desc="100x100x100 cells (2,000,000 atoms), 600 K seed 1, 5 keV PKA, adaptive dt, hash update every step"),
+}
+
+
+def init_dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if os.environ.get("MISA_BENCH_GLOO") is None else "gloo")
+    return ws, rank, local
+
+
+def barrier_max(ws, value):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def make_inputs(w, rank):
+    n = w["n"]
+    natoms = 2 * n ** 3
+    v = synth.maxwell_velocities(natoms, w["T"], synth.MASS_FE, w["seed"] + 1000 * rank)
+    d = synth.random_direction(w["seed"] + 17 + 1000 * rank)
+    return v, d
+
+
+def cpu_baseline(target_s=12.0, max_cells=100):
+    """The oracle as it stands (cell list, OpenMP on all host cores): velocity
+    Verlet steps on a sub-box of the same crystal, potential and temperature,
+    grown until the sample takes ~target_s.  atom-steps/s."""
+    from oracle import oracle as O
+    O.build()
+    pot = synth.potential()
+    op = O.Pot(pot)
+    n = 20
+    while True:
+        x = synth.bcc_positions(n, n, n)
+        v = synth.maxwell_velocities(len(x), 600.0, synth.MASS_FE, 2)
+        L = synth.box(n, n, n)
+        t0 = time.perf_counter()
+        _, _, a, _, _ = O.md_run(op, x, v, L, synth.MASS_FE, 1.0, 0.02, 1, mode=1)
+        t1 = time.perf_counter()
+        # the first call also evaluates the initial forces (2 force passes);
+        # time a clean second step
+        t2 = time.perf_counter()
+        O.md_run(op, x, v, L, synth.MASS_FE, 1.0, 0.02, 1, mode=1, a=a)
+        t3 = time.perf_counter()
+        dt = t3 - t2
+        if dt * 4 >= target_s or n >= max_cells:
+            steps = max(1, int(target_s / max(dt, 1e-3)))
+            t4 = time.perf_counter()
+            O.md_run(op, x, v, L, synth.MASS_FE, 1.0, 0.02, steps, mode=1, a=a)
+            t5 = time.perf_counter()
+            val = len(x) * steps / (t5 - t4)
+            return {"value": val, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                    "sample": f"{steps} velocity-Verlet steps of a {n}x{n}x{n}-cell ({len(x)}-atom) box of the same "
+                              f"crystal, potential and temperature (FP64 cell-list oracle; its cost per atom-step "
+                              f"does not depend on box size)", "seconds": t5 - t4}
+        n = min(max_cells, int(n * 1.6))
+
+
+def run_reference(args):
+    ws, rank, _ = init_dist()
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.workload]
+    from oracle import oracle as O
+    O.build()
+    pot = synth.potential()
+    op = O.Pot(pot)
+    # one bench step = one oracle MD step of a bounded sample of the workload:
+    # a 24^3-cell box of the same crystal, potential, temperature and PKA
+    n = args.ref_cells
+    x = synth.bcc_positions(n, n, n)
+    v = synth.maxwell_velocities(len(x), w["T"], synth.MASS_FE, w["seed"])
+    O.insert_pka(v, synth.pka_atom(n, n, n), synth.MASS_FE, w["pka_eV"], synth.random_direction(w["seed"] + 17))
+    L = synth.box(n, n, n)
+    x, v, a, _, _ = O.md_run(op, x, v, L, synth.MASS_FE, 1.0, w["dx_max"], args.warmup, mode=1)
+    t0 = time.perf_counter()
+    x, v, a, _, _ = O.md_run(op, x, v, L, synth.MASS_FE, 1.0, w["dx_max"], args.steps, mode=1, a=a)
+    el = time.perf_counter() - t0
+    val = len(x) * args.steps / el
+    cores = O.num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"oracle sample: {n}x{n}x{n} cells ({len(x)} atoms) of the {args.workload} "
+                                   f"workload ({w['desc']})", "cache": "cpu"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} MD steps of a {n}^3-cell box per run"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    ws, rank, local = init_dist()
+    torch.cuda.set_device(local)
+    from paper_2107_07866_gb300 import build
+    build.build()
+    from paper_2107_07866_gb300 import misa
+
+    w = WORKLOADS[args.workload]
+    n = w["n"]
+    natoms = 2 * n ** 3
+    pot = synth.potential()
+    v, d = make_inputs(w, rank)
+
+    def fresh(prec):
+        s = misa.Sim(pot, n, precision=prec, dt_max=1.0, dx_max=w["dx_max"], reassign_period=w["reassign"],
+                     tile=args.tile)
+        s.set_velocities(v)
+        s.insert_pka(-1, w["pka_eV"], d)
+        return s
+
+    # ---- FP32-force path: the timed value ---------------------------------
+    sim = fresh("fp32")
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    st0 = sim.stats()
+    launches0 = st0["launches"]
+    sim.timing(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+    el_ms = e0.elapsed_time(e1)
+    phases, nsteps = sim.timing_get()
+    sim.timing(False)
+    st1 = sim.stats()
+    gpu_launches = st1["launches"] - launches0
+    el_max = barrier_max(ws, el_ms)
+    value = natoms * ws * args.steps / (el_max / 1e3)
+    clocks = clk.summary()
+
+    # roofline of the dominant kernel (force pass) measured inside the timed region
+    t_force = phases["force"] / max(nsteps, 1) / 1e3
+    t_dens = phases["density"] / max(nsteps, 1) / 1e3
+    ach = FLOPS_FORCE_SITE * natoms / t_force / 1e12
+    traffic = None
+    if NCU_FORCE_TRAFFIC["source_sha"] == kernel_source_sha():
+        traffic = NCU_FORCE_TRAFFIC["bytes_per_launch"]
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    step_s = el_ms / 1e3 / args.steps
+    roofline = {"bound": "alu", "kernel": "k_force<float>", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "peak_note": "FP32 FMA issue peak: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, not measured)",
+                "algorithmic_flops_per_site": FLOPS_FORCE_SITE,
+                "force_ms": 1e3 * t_force, "density_ms": 1e3 * t_dens,
+                "density_tflops": FLOPS_DENS_SITE * natoms / t_dens / 1e12,
+                "step_hbm": {"bytes_per_atom_step": BYTES_STEP_FP32,
+                             "achieved_gbs": BYTES_STEP_FP32 * natoms / step_s / 1e9,
+                             "peak_gbs": hbm_peak, "frac": BYTES_STEP_FP32 * natoms / step_s / 1e9 / hbm_peak,
+                             "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json)"},
+                "phase_ms_per_step": {k: v_ / max(nsteps, 1) for k, v_ in phases.items()}}
+    stats_end = sim.stats()
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    # ---- e2e through the C ABI with host buffers ----------------------------
+    e2e = None
+    if not args.no_e2e:
+        s = misa.Sim(pot, n, precision="fp32", dt_max=1.0, dx_max=w["dx_max"], reassign_period=w["reassign"],
+                     tile=args.tile)
+        x_host = torch.from_numpy(synth.bcc_positions(n, n, n)).pin_memory()
+        v0 = v.copy()
+        pka = synth.pka_atom(n, n, n)
+        spd = math.sqrt(2.0 * w["pka_eV"] / synth.MASS_FE / synth.EV_PER_AMU_A2_FS2)
+        v0[pka] = spd * d
+        v_host = torch.from_numpy(v0).pin_memory()
+        inner = w["reassign"]
+        iters = max(1, args.e2e_iters)
+        s.set_state(x_host, v_host)
+        s.step(inner)
+        s.stats()
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(iters):
+            s.set_state(x_host, v_host)      # H2D: positions + velocities from pinned memory
+            s.step(inner)
+            s.stats()                        # D2H: step, time, dt, run-away count, status
+        torch.cuda.synchronize()
+        el = barrier_max(ws, time.perf_counter() - t0)
+        e2e = {"value": natoms * ws * inner * iters / el, "unit": UNIT,
+               "h2d_bytes_per_step": 48 * natoms, "d2h_bytes_per_step": 80,
+               "note": f"one e2e step = set_state from pinned host x, v + {inner} MD steps + stats read-back"}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+
+    # ---- FP64 path on the same inputs -----------------------------------------
+    fp64 = None
+    if not args.no_fp64:
+        s = fresh("fp64")
+        s.step(1)
+        torch.cuda.synchronize()
+        k64 = args.fp64_steps
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        s.step(k64)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        el64 = a0.elapsed_time(a1)
+        fp64 = {"value": natoms * k64 / (el64 / 1e3), "unit": UNIT, "steps": k64, "ms_per_step": el64 / k64}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": el_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w["desc"], "atoms": natoms, "parallelism": f"replicas{ws}",
+                           "cache": "state ~8 GB >> 129 MB L2 (no flush needed)", "tile": args.tile},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+                "clocks": clocks, "fp64_path": fp64,
+                "end_state": {"step": stats_end["step"], "time_fs": stats_end["time"],
+                              "n_runaway": stats_end["n_runaway"], "status": stats_end["status"]}}
+        print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="misa", choices=["misa", "reference"])
+    ap.add_argument("--workload", default="c3", choices=list(WORKLOADS))
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-iters", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-cells", type=int, default=24)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,198 @@
+/*
+ * misa.h -- C ABI of the GB300 (sm_103a) EAM lattice-list molecular dynamics
+ * library: the per-timestep hot path of MISA-MD (Chu et al., arXiv:2107.07866).
+ *
+ * One simulation handle owns one periodic bcc crystal of nx x ny x nz cubic
+ * cells (2 nx ny nz lattice sites and as many atoms) on one GPU.  Atoms live
+ * in the lattice list of Sec. 3: a hash array with one slot per lattice site
+ * (index = 2 nx ny z + 2 nx y + x, x in [0, 2 nx): even x = cube corner,
+ * odd x = body centre) and a run-away list for atoms that have left their
+ * site (the paper's hash-clash tree).  Each step evaluates the EAM potential
+ * (Eq. eam_base, Eq. eam_force_ij, the five steps of Sec. 2.2) with spline
+ * tables (Sec. 4.1) by a full-neighbour gather through the neighbour offset
+ * index, then advances velocity Verlet (Fig. 1).
+ *
+ * Conventions
+ *  - Units: Angstrom, eV, fs, amu, K.
+ *  - Atom ids are 0 .. natoms-1; per-atom host arrays are indexed by atom id
+ *    and hold x,y,z (or vx,vy,vz ...) interleaved: a[3*id + d].
+ *  - Host array arguments may also be device pointers (copies use unified
+ *    addressing); the caller keeps ownership of every buffer it passes.
+ *  - Every call is asynchronous on the handle's stream except those that
+ *    return host data (misa_get_*, misa_stats), which synchronise it.
+ *  - Return value: MISA_OK (0) or a negative MISA_E* code; the message is in
+ *    misa_last_error().  No call traps or aborts; device-side problems are
+ *    reported through status bits (misa_stats) and MISA_EUNSTABLE /
+ *    MISA_ERUNAWAY_OVERFLOW from the next synchronising call.
+ *  - A handle is not thread-safe: one host thread and one stream per handle.
+ */
+#ifndef MISA_H
+#define MISA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define MISA_OK 0
+#define MISA_EINVAL (-1)             /* bad argument or parameter */
+#define MISA_EOOM (-2)               /* device allocation failed */
+#define MISA_ECUDA (-3)              /* a CUDA runtime call failed */
+#define MISA_ERUNAWAY_OVERFLOW (-4)  /* more run-away atoms than the list holds */
+#define MISA_EUNSTABLE (-5)          /* non-finite force or velocity */
+#define MISA_ETIMEOUT (-6)           /* a bounded device wait gave up */
+
+/* arithmetic of the force path */
+#define MISA_FP64 0       /* everything in FP64 */
+#define MISA_FP32_FORCE 1 /* FP32 density/force arithmetic with compensated sums; FP64 integration */
+
+/* status bits (misa_stats.status), sticky until misa_clear_status */
+#define MISA_ST_RUNAWAY_OVERFLOW 0x1u /* run-away list full: atoms were dropped from the physics */
+#define MISA_ST_NONFINITE 0x2u        /* NaN/Inf in a force or velocity */
+#define MISA_ST_RFLOOR 0x4u           /* a pair closer than 1e-4 A (value clamped, no force) */
+#define MISA_ST_RHO_EXTRAP 0x8u       /* a density above the embedding table (linear tail used) */
+
+/* Optional device allocator: the library calls alloc(bytes, ctx) for every
+ * device buffer it owns and free(ptr, bytes, ctx) on destroy.  NULL: the
+ * library uses cudaMalloc / cudaFree. */
+typedef void *(*misa_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*misa_free_fn)(void *ptr, size_t bytes, void *ctx);
+
+typedef struct misa_params {
+    int32_t nx, ny, nz;       /* cubic cells per axis, each >= 6 */
+    double a0;                /* lattice constant (A) */
+    double mass;              /* atomic mass (amu) */
+    double rc;                /* cutoff (A); f and phi are zero at and beyond it */
+    double skin;              /* delta (A): an array atom farther than this from its site
+                                 becomes a run-away; (rc + 2 skin) / (a0/2) must be < sqrt(27) */
+    int32_t n_knots;          /* knots per table (>= 8) */
+    const double *f_knots;    /* electron density f(r) at r_k = k rc/(n-1)      (Sec. 4.1) */
+    const double *phi_knots;  /* pair potential phi(r) at the same r_k          (Sec. 4.1) */
+    const double *F_knots;    /* embedding F(rho) at rho_k = k rho_max/(n-1)    (Sec. 4.1) */
+    double rho_max;           /* end of the embedding table; linear beyond */
+    int32_t precision;        /* MISA_FP64 or MISA_FP32_FORCE */
+    int32_t reassign_period;  /* steps between hash updates that move run-aways back (Alg. 2) */
+    double dt_max;            /* timestep cap (fs) */
+    double dx_max;            /* adaptive step: dt = min(dt_max, dx_max / max|v|); 0 = fixed dt */
+    int64_t runaway_capacity; /* run-away list size; 0 = max(4096, natoms/64); at most 16384 */
+    misa_alloc_fn alloc;      /* optional allocator hooks (both or neither) */
+    misa_free_fn free;
+    void *alloc_ctx;
+    int32_t tile;             /* gather tile choice: 0 = autotuned, else a misa_tile_* index */
+} misa_params;
+
+typedef struct misa_stats {
+    int64_t step;       /* steps taken since create */
+    double time;        /* simulated time (fs) */
+    double dt;          /* timestep the next step will use (fs) */
+    int64_t natoms;
+    int64_t nsites;
+    int64_t n_runaway;  /* atoms in the run-away list */
+    int64_t n_vacant;   /* lattice sites without an atom (equals n_runaway) */
+    uint32_t status;    /* MISA_ST_* bits */
+    double vmax;        /* largest speed (A/fs) at the last step end */
+    int64_t launches;   /* kernels this handle has launched (host-side count) */
+} misa_stats;
+
+/* Phases timed by misa_timing_get, in step order. */
+#define MISA_PHASE_KICK_DRIFT 0   /* opening half kick + drift + demotions */
+#define MISA_PHASE_LIST 1         /* hash update (Alg. 2), run-away list sort, tile marks */
+#define MISA_PHASE_DENSITY 2      /* array density pass + embedding derivative */
+#define MISA_PHASE_RA_DENSITY 3   /* run-away density */
+#define MISA_PHASE_FORCE 4        /* array force pass + closing half kick */
+#define MISA_PHASE_RA_FORCE 5     /* run-away force + closing half kick */
+#define MISA_PHASE_END 6          /* step bookkeeping */
+#define MISA_NPHASE 7
+
+typedef struct misa_sim misa_sim;
+
+/* Fills p with the analytic-potential-free defaults (a0 2.855, mass 55.845,
+ * rc 5.6, skin 0.6, FP32_FORCE, reassign 10, dt_max 1, dx_max 0); the caller
+ * still sets the box and the three knot tables. */
+void misa_default_params(misa_params *p);
+
+/* Creates the lattice list of a perfect crystal (Sec. 3, hash
+ * initialization: every atom on its own site, no clashes; atom id = lattice
+ * id), builds the neighbour offset index and the spline coefficients
+ * (Sec. 4.1) on the device, sets velocities to zero and evaluates the
+ * initial forces.  stream: a cudaStream_t (NULL = default stream).  The
+ * knot arrays are copied.  On success *out owns all device memory. */
+int misa_create(const misa_params *p, void *stream, misa_sim **out);
+
+/* Frees the handle and its device memory (after synchronising its stream). */
+void misa_destroy(misa_sim *s);
+
+/* Message of the last failed call on s (or of the last failed create when
+ * s is NULL).  Valid until the next call on s. */
+const char *misa_last_error(const misa_sim *s);
+
+/* Replaces positions x (3 natoms, A, any periodic image) and, if v is not
+ * NULL, velocities (3 natoms, A/fs); n must equal natoms.  Atoms are hashed to
+ * their nearest sites (Sec. 3): an atom takes its site if the site is free
+ * and the atom lies within skin of it (lowest atom id first), else it joins
+ * the run-away list.  Then the forces of the new positions are evaluated. */
+int misa_set_state(misa_sim *s, const double *x, const double *v, int64_t n);
+
+/* Replaces the velocities (3 natoms, A/fs). */
+int misa_set_velocities(misa_sim *s, const double *v, int64_t n);
+
+/* Primary knock-on atom (Sec. 5.1): atom gets kinetic energy energy_eV along
+ * dir (normalised here); atom = -1 picks the atom on the cube corner of cell
+ * (nx/2, ny/2, nz/2), the box centre. */
+int misa_insert_pka(misa_sim *s, int64_t atom, double energy_eV, const double dir[3]);
+
+/* Advances n steps of NVE velocity Verlet: kick, drift (array atoms leaving
+ * their skin move to the run-away list), hash update every reassign_period
+ * steps (Alg. 2), EAM density / embedding derivative / force passes
+ * (Alg. 1 with the offset index), kick, next adaptive timestep.  Launches
+ * only; never synchronises. */
+int misa_step(misa_sim *s, int n);
+
+/* Potential energy (sum of E_i, Eq. eam_base) and kinetic energy (eV) of
+ * the current state; per_atom (natoms, may be NULL) receives E_i.
+ * Synchronises. */
+int misa_get_energies(misa_sim *s, double *pe, double *ke, double *per_atom);
+
+/* Per-atom host outputs (3 natoms doubles, or natoms for the density),
+ * indexed by atom id; n must be >= natoms.  Positions are wrapped into the
+ * box.  Forces are those of the current positions (eV/A).  Synchronise. */
+int misa_get_positions(misa_sim *s, double *x, int64_t n);
+int misa_get_velocities(misa_sim *s, double *v, int64_t n);
+int misa_get_forces(misa_sim *s, double *f, int64_t n);
+int misa_get_density(misa_sim *s, double *rho, int64_t n);
+
+/* Lattice-list storage (for checks): site_atom (nsites) = atom id per site
+ * or -1; runaway_ids (cap) = run-away atom ids in list order; *n_runaway =
+ * their count.  Synchronises. */
+int misa_get_site_map(misa_sim *s, int64_t *site_atom, int64_t *runaway_ids, int64_t cap,
+                      int64_t *n_runaway);
+
+/* Per-phase device timing of misa_step (CUDA events on the handle's
+ * stream, recorded only while enabled).  misa_timing_get synchronises and
+ * writes, for each of the MISA_NPHASE phases, the summed milliseconds
+ * (ms[phase]) over the steps taken since timing was enabled or last read,
+ * and their count (*steps); then it restarts the sums. */
+int misa_timing_enable(misa_sim *s, int enable);
+int misa_timing_get(misa_sim *s, double ms[MISA_NPHASE], int64_t *steps);
+
+/* Counters and status bits.  Synchronises. */
+int misa_stats_get(misa_sim *s, misa_stats *out);
+int misa_clear_status(misa_sim *s);
+
+/* Checkpoint / restart of the full dynamic state (positions, velocities,
+ * accelerations, lattice list, step, time, dt) to a binary file. */
+int misa_save(misa_sim *s, const char *path);
+int misa_load(misa_sim *s, const char *path);
+
+/* Number of built gather tile shapes, and the shape of each (cells). */
+int misa_tile_count(void);
+int misa_tile_shape(int index, int *tx, int *ty, int *tz);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MISA_H */

@@ -1,0 +1,725 @@
+// misa_kernels.cuh -- the CUDA kernels of the EAM lattice-list MD step.
+//
+// Hot path of MISA-MD (arXiv:2107.07866) re-designed for one GB300:
+//   density pass   rho_i = sum_j f(r_ij)               (Sec. 2.2 step 1)
+//   embedding      F'(rho_i)                           (Sec. 2.2 step 2)
+//   force pass     F_i = sum_j [(F'_i + F'_j) f'(r) + phi'(r)] (x_j - x_i)/r
+//                                                      (Eq. eam_force_ij, steps 3-5)
+// over the lattice list (Sec. 3): array atoms are reached through the
+// neighbour offset index (Alg. 1 part 1), run-away atoms through a short
+// list that every nearby tile and every run-away scans (Alg. 1 parts 2-3,
+// read symmetrically).  Every per-atom result is written by exactly one
+// thread: a full-neighbour gather with no atomics on densities or forces.
+//
+// A CTA owns one tile of TX x TY x TZ cells at a time (persistent loop over
+// tiles) and stages the displacements of the tile plus a 2-cell halo into
+// shared memory as (ux, uy, uz, F') vectors, split by parity so that the 8
+// lanes of a quarter warp read 128 contiguous bytes.  The FP32 path keeps the
+// spline coefficients of the pass in shared memory for the whole launch.
+#pragma once
+
+#include "misa_common.cuh"
+
+namespace misa {
+
+constexpr int kRaChunk = 128;  // run-away atoms staged per round in a tile CTA
+constexpr double kRws = 1.1180339887498949;  // max distance to the nearest bcc site: sqrt(5)/2 (a0/2 units)
+
+// ---------------------------------------------------------------------------
+// arithmetic traits
+// ---------------------------------------------------------------------------
+
+template <typename T>
+struct Arith;
+
+template <>
+struct Arith<float> {
+    static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
+    // split x into floor (as int) and fraction, with ALU adds only: round
+    // (x - 0.5) to an integer by the 1.5*2^23 trick.  At an exact integer x
+    // either neighbouring segment may be chosen (t = 0 or t = 1); the spline
+    // is C1 there, so both give the same value.
+    static __device__ __forceinline__ int split(float x, float &t)
+    {
+        const float magic = 12582912.0f;
+        float y = __fadd_rn(__fsub_rn(x, 0.5f), magic);
+        float fl = __fsub_rn(y, magic);
+        t = __fsub_rn(x, fl);
+        return __float_as_int(y) - 0x4B400000;
+    }
+};
+
+template <>
+struct Arith<double> {
+    static __device__ __forceinline__ double rsqrt(double x) { return 1.0 / sqrt(x); }
+    static __device__ __forceinline__ int split(double x, double &t)
+    {
+        double fl = floor(x);
+        t = x - fl;
+        return (int)fl;
+    }
+};
+
+// Compensated accumulator: Kahan summation in FP32, plain sum in FP64.
+template <typename T>
+struct Acc {
+    T s = 0, c = 0;
+    __device__ __forceinline__ void add(T v)
+    {
+        if constexpr (sizeof(T) == 4) {
+            T y = v - c;
+            T t = s + y;
+            c = (t - s) - y;
+            s = t;
+        } else {
+            s += v;
+        }
+    }
+    __device__ __forceinline__ T value() const { return s - c; }
+};
+
+// ---------------------------------------------------------------------------
+// spline tables (Sec. 4.1)
+// ---------------------------------------------------------------------------
+// Knot slopes of the local cubic Hermite reading (central differences, 4th
+// order inside, 2nd order at the two outer knots of each end), then the
+// power form of segment k in t = x/h - k:
+//   S = ((a t + b) t + c) t + d,   S'(x) = (3a t^2 + 2b t + c) / h.
+
+__device__ __forceinline__ double knot_slope(const double *y, int n, double h, int k)
+{
+    if (k == 0) return (-3.0 * y[0] + 4.0 * y[1] - y[2]) / (2.0 * h);
+    if (k == n - 1) return (3.0 * y[n - 1] - 4.0 * y[n - 2] + y[n - 3]) / (2.0 * h);
+    if (k == 1 || k == n - 2) return (y[k + 1] - y[k - 1]) / (2.0 * h);
+    return (y[k - 2] - 8.0 * y[k - 1] + 8.0 * y[k + 1] - y[k + 2]) / (12.0 * h);
+}
+
+// tab_f, tab_phi, tab_F: value coefficients; tab_d0/tab_d1: derivative
+// coefficients of f and phi with respect to r, (A, B, C) with S' = (A t + B) t + C.
+template <typename T>
+__global__ void k_spline_tables(const double *fk, const double *pk, const double *Fk, int n, double hr,
+                                double hrho, Vec4<T> *tab_f, Vec4<T> *tab_phi, Vec4<T> *tab_F,
+                                Vec4<T> *tab_d0, Vec2<T> *tab_d1)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n - 1) return;
+    double cf[4], cp[4], cF[4];
+    const double *ys[3] = {fk, pk, Fk};
+    double hs[3] = {hr, hr, hrho};
+    double *cs[3] = {cf, cp, cF};
+    for (int q = 0; q < 3; ++q) {
+        const double *y = ys[q];
+        double h = hs[q];
+        double m0 = knot_slope(y, n, h, k) * h, m1 = knot_slope(y, n, h, k + 1) * h;
+        double y0 = y[k], y1 = y[k + 1];
+        cs[q][0] = 2.0 * (y0 - y1) + m0 + m1;
+        cs[q][1] = 3.0 * (y1 - y0) - 2.0 * m0 - m1;
+        cs[q][2] = m0;
+        cs[q][3] = y0;
+    }
+    tab_f[k] = Vec4<T>{(T)cf[0], (T)cf[1], (T)cf[2], (T)cf[3]};
+    tab_phi[k] = Vec4<T>{(T)cp[0], (T)cp[1], (T)cp[2], (T)cp[3]};
+    tab_F[k] = Vec4<T>{(T)cF[0], (T)cF[1], (T)cF[2], (T)cF[3]};
+    tab_d0[k] = Vec4<T>{(T)(3.0 * cf[0] / hr), (T)(2.0 * cf[1] / hr), (T)(cf[2] / hr), (T)(3.0 * cp[0] / hr)};
+    tab_d1[k] = Vec2<T>{(T)(2.0 * cp[1] / hr), (T)(cp[2] / hr)};
+}
+
+// Embedding F(rho) and F'(rho); linear continuation above rho_max.
+template <typename T>
+__device__ __forceinline__ T embed(const Vec4<T> *__restrict__ tab, int nseg, T Srho, T rho_max, T rho, T &dF,
+                                   unsigned &st)
+{
+    if (rho > rho_max) {
+        Vec4<T> c = tab[nseg - 1];
+        T S1 = c.x + c.y + c.z + c.w;
+        T D1 = (3 * c.x + 2 * c.y + c.z) * Srho;
+        dF = D1;
+        st |= kStRhoExtrap;
+        return S1 + D1 * (rho - rho_max);
+    }
+    if (!(rho > 0)) rho = 0;
+    T t;
+    int k = Arith<T>::split(rho * Srho, t);
+    k = min(max(k, 0), nseg - 1);
+    if (k == nseg - 1 && t > 1) t = 1;
+    Vec4<T> c = tab[k];
+    dF = ((3 * c.x * t + 2 * c.y) * t + c.z) * Srho;
+    return ((c.x * t + c.y) * t + c.z) * t + c.w;
+}
+
+// ---------------------------------------------------------------------------
+// gather arguments
+// ---------------------------------------------------------------------------
+
+struct ShellInfo {
+    int n2[kMaxShell];
+    int begin[kMaxShell + 1];
+    float thr[kMaxShell];   // rc^2 - n^2 (lattice units)
+    float nrm[kMaxShell];   // |n|
+    float xfrac[kMaxShell]; // |n| S = xint + xfrac, xfrac in [0, 1)
+    int xint[kMaxShell];
+    double thr_d[kMaxShell];
+    int nshell;
+};
+
+template <typename T>
+struct GatherArgs {
+    int nx, ny, nz;
+    int tx, ty, tz;
+    int ntx, nty, ntz, ntiles;
+    const T *ux, *uy, *uz;  // displacement per site, lattice units; vacant = kVacant
+    const T *fp;            // force pass input: F' per site
+    T *fp_out;              // density pass output
+    T *rho_out;             // density (energy mode) or null
+    double *e_out;          // per-site energy (energy mode) or null
+    T *ax, *ay, *az;        // acceleration out (A/fs^2)
+    double *vx, *vy, *vz;   // velocity (kick)
+    const Vec4<T> *tab_f, *tab_phi, *tab_F, *tab_d0;
+    const Vec2<T> *tab_d1;
+    int nseg;
+    T S;        // knot index per lattice unit of r: (a0/2)/h_r
+    T Srho;     // 1/h_rho
+    T rho_max;
+    T rc2;      // rc^2, lattice units
+    T rc_lat;
+    T rfloor2;  // r_floor^2, lattice units
+    // run-away list
+    const int *ra_home;
+    const T *ra_ux, *ra_uy, *ra_uz;
+    const T *ra_fp;
+    const int *tile_flag;
+    DevScalars *sc;
+    double acc_conv;  // (eV/A) -> (A/fs^2): 1/(m) * 9.6485e-3
+    int kick;
+    int tables_in_smem;
+    // neighbour offset index for this tile shape: per parity, per vector:
+    // (slot displacement as int bits, 2 n_x, 2 n_y, 2 n_z)
+    float4 off[2][kNVec];
+    ShellInfo sh;
+};
+
+template <typename T>
+struct TileGeom {
+    int SX, SY, SZ, SXY, PLANE;
+};
+
+// smem layout helpers
+template <typename T>
+__host__ __device__ inline size_t tile_smem_bytes(int tx, int ty, int tz)
+{
+    return sizeof(Vec4<T>) * 2 * (size_t)(tx + 4) * (ty + 4) * (tz + 4);
+}
+
+struct RaStage {
+    int cnt, next;
+};
+
+// ---------------------------------------------------------------------------
+// tile staging
+// ---------------------------------------------------------------------------
+
+// Loads the displacements (and F' in .w for the force pass) of the tile with
+// cell origin (c0x, c0y, c0z) and a 2-cell periodic halo into sU.  Returns
+// max |u| over the occupied staged sites (lattice units), block-wide.
+template <typename T, bool WITH_FP>
+__device__ __forceinline__ T stage_tile(const GatherArgs<T> &a, Vec4<T> *sU, int c0x, int c0y, int c0z,
+                                        float *sred)
+{
+    const int SX = a.tx + 4, SY = a.ty + 4, SZ = a.tz + 4;
+    const int PLANE = SX * SY * SZ;
+    T umax2 = 0;
+    for (int q = threadIdx.x; q < 2 * PLANE; q += blockDim.x) {
+        int p = q & 1;
+        int r = q >> 1;
+        int x = r % SX;
+        int yz = r / SX;
+        int y = yz % SY;
+        int z = yz / SY;
+        // periodic wrap; tiles may be wider than the box, so a full modulo
+        int gx = (c0x - 2 + x + 2 * a.nx) % a.nx;
+        int gy = (c0y - 2 + y + 2 * a.ny) % a.ny;
+        int gz = (c0z - 2 + z + 2 * a.nz) % a.nz;
+        long long sid = (((long long)gz * a.ny + gy) * a.nx + gx) * 2 + p;
+        Vec4<T> v;
+        v.x = a.ux[sid];
+        v.y = a.uy[sid];
+        v.z = a.uz[sid];
+        v.w = WITH_FP ? a.fp[sid] : (T)0;
+        T u2 = v.x * v.x + v.y * v.y + v.z * v.z;
+        if (v.x < (T)(0.5f * kVacant)) umax2 = umax2 > u2 ? umax2 : u2;
+        sU[p * PLANE + (z * SY + y) * SX + x] = v;
+    }
+    // block max
+    float m = (float)umax2;
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float w = threadIdx.x < (blockDim.x >> 5) ? sred[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) w = fmaxf(w, __shfl_xor_sync(0xffffffffu, w, o));
+        if (threadIdx.x == 0) sred[32] = w;
+    }
+    __syncthreads();
+    return (T)sqrtf(sred[32]);
+}
+
+// Stages the next chunk of run-away atoms whose home cell lies within 3
+// cells of the tile (reach rc + skin + the Wigner-Seitz radius), in list
+// order, as (home lattice coords relative to the tile origin, u, F').
+// Warp 0 scans; returns the staged count (block-uniform).
+template <typename T, bool WITH_FP>
+__device__ __forceinline__ int stage_runaways(const GatherArgs<T> &a, int nra, int &pos, int c0x, int c0y, int c0z,
+                                              int4 *sRh, Vec4<T> *sRu, RaStage *st)
+{
+    if (threadIdx.x < 32) {
+        int lane = threadIdx.x;
+        int cnt = 0;
+        int p0 = pos;
+        while (p0 < nra && cnt < kRaChunk) {
+            int j = p0 + lane;
+            bool take = false;
+            int hx = 0, hy = 0, hz = 0;
+            if (j < nra) {
+                int h = a.ra_home[j];
+                int x2 = h % (2 * a.nx);
+                int rest = h / (2 * a.nx);
+                int cy = rest % a.ny, cz = rest / a.ny;
+                int par = x2 & 1, cx = x2 >> 1;
+                int dx = cx - c0x, dy = cy - c0y, dz = cz - c0z;
+                // nearest periodic image to the tile centre
+                int mx = a.tx / 2, my = a.ty / 2, mz = a.tz / 2;
+                dx -= mx; dy -= my; dz -= mz;
+                dx -= a.nx * (int)floorf((dx + 0.5f * a.nx) / a.nx);
+                dy -= a.ny * (int)floorf((dy + 0.5f * a.ny) / a.ny);
+                dz -= a.nz * (int)floorf((dz + 0.5f * a.nz) / a.nz);
+                dx += mx; dy += my; dz += mz;
+                take = dx >= -3 && dx < a.tx + 3 && dy >= -3 && dy < a.ty + 3 && dz >= -3 && dz < a.tz + 3;
+                hx = 2 * dx + par;
+                hy = 2 * dy + par;
+                hz = 2 * dz + par;
+            }
+            unsigned bal = __ballot_sync(0xffffffffu, take);
+            int room = kRaChunk - cnt;
+            int rank = __popc(bal & ((1u << lane) - 1u));
+            if (take && rank < room) {
+                sRh[cnt + rank] = make_int4(hx, hy, hz, 0);
+                Vec4<T> u;
+                u.x = a.ra_ux[j];
+                u.y = a.ra_uy[j];
+                u.z = a.ra_uz[j];
+                u.w = WITH_FP ? a.ra_fp[j] : (T)0;
+                sRu[cnt + rank] = u;
+            }
+            int ntake = __popc(bal);
+            if (ntake <= room) {
+                cnt += ntake;
+                p0 += 32;
+            } else {
+                // chunk full: resume at the first lane that did not fit
+                int k = 0;
+                unsigned b = bal;
+                for (int q = 0; q < room; ++q) b &= b - 1;
+                k = __ffs(b) - 1;
+                p0 += k;
+                cnt += room;
+            }
+        }
+        if (lane == 0) {
+            st->cnt = cnt;
+            st->next = p0 < nra ? p0 : nra;
+        }
+    }
+    __syncthreads();
+    int c = st->cnt;
+    pos = st->next;
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// pair geometry
+// ---------------------------------------------------------------------------
+// For an array pair through offset vector n (shell s): q = (2n + d).d with
+// d = u_j - u_i, so r^2 = n^2 + q.  In FP32 the spline argument is formed
+// from r - |n| = q / (r + |n|), which is small, plus the per-shell split
+// |n| S = xint + xfrac: the segment index and t keep full FP32 precision
+// instead of the ~1e-4 absolute error of r S near 2000.
+
+template <typename T>
+__device__ __forceinline__ void shell_arg(const ShellInfo &sh, int s, T q, T S, T rfloor2, int &seg, T &t, T &rinv,
+                                          bool &floor_hit)
+{
+    T n2 = (T)sh.n2[s];
+    T r2 = n2 + q;
+    floor_hit = r2 < rfloor2;
+    r2 = floor_hit ? rfloor2 : r2;
+    T rs = Arith<T>::rsqrt(r2);
+    rinv = rs;
+    if constexpr (sizeof(T) == 4) {
+        T r = r2 * rs;
+        T dr = floor_hit ? (sqrtf(rfloor2) - sh.nrm[s]) : q * __frcp_rn(r + sh.nrm[s]);
+        T x = sh.xfrac[s] + dr * S;
+        seg = sh.xint[s] + Arith<T>::split(x, t);
+    } else {
+        T r = sqrt(r2);
+        seg = Arith<T>::split(r * S, t);
+    }
+}
+
+// Spline argument from r^2 directly (run-away pairs: the offset is not a
+// shell constant).
+template <typename T>
+__device__ __forceinline__ void direct_arg(T r2, T S, T rfloor2, int &seg, T &t, T &rinv, bool &floor_hit)
+{
+    floor_hit = r2 < rfloor2;
+    r2 = floor_hit ? rfloor2 : r2;
+    T rs = Arith<T>::rsqrt(r2);
+    rinv = rs;
+    T r;
+    if constexpr (sizeof(T) == 4) r = r2 * rs;
+    else r = sqrt(r2);
+    seg = Arith<T>::split(r * S, t);
+}
+
+template <typename T>
+__device__ __forceinline__ int clamp_seg(int seg, int nseg, T &t)
+{
+    if (seg < 0) {
+        t = 0;
+        return 0;
+    }
+    if (seg > nseg - 1) {
+        t = 1;
+        return nseg - 1;
+    }
+    return seg;
+}
+
+// ---------------------------------------------------------------------------
+// density pass: rho_i, F'(rho_i)  (Sec. 2.2 steps 1-2)
+// ---------------------------------------------------------------------------
+
+template <typename T, bool ENERGY>
+__global__ void __launch_bounds__(1024, 1) k_density(const __grid_constant__ GatherArgs<T> a)
+{
+    extern __shared__ __align__(32) unsigned char smem[];
+    const Vec4<T> *tabf;
+    size_t off = 0;
+    if (a.tables_in_smem) {
+        Vec4<T> *t = reinterpret_cast<Vec4<T> *>(smem);
+        for (int k = threadIdx.x; k < a.nseg; k += blockDim.x) t[k] = a.tab_f[k];
+        tabf = t;
+        off = sizeof(Vec4<T>) * (size_t)a.nseg;
+    } else {
+        tabf = a.tab_f;
+    }
+    off = (off + 255) & ~(size_t)255;
+    float4 *sOff = reinterpret_cast<float4 *>(smem + off);
+    off += sizeof(float4) * 2 * kNVec;
+    Vec4<T> *sU = reinterpret_cast<Vec4<T> *>(smem + off);
+    off += tile_smem_bytes<T>(a.tx, a.ty, a.tz);
+    int4 *sRh = reinterpret_cast<int4 *>(smem + off);
+    off += sizeof(int4) * kRaChunk;
+    Vec4<T> *sRu = reinterpret_cast<Vec4<T> *>(smem + off);
+    off += sizeof(Vec4<T>) * kRaChunk;
+    float *sred = reinterpret_cast<float *>(smem + off);
+    off += sizeof(float) * 80;
+    RaStage *sst = reinterpret_cast<RaStage *>(smem + off);
+
+    for (int k = threadIdx.x; k < 2 * kNVec; k += blockDim.x) sOff[k] = (&a.off[0][0])[k];
+
+    const int SX = a.tx + 4, SY = a.ty + 4, SZ = a.tz + 4;
+    const int PLANE = SX * SY * SZ;
+    const int per_par = a.tx * a.ty * a.tz;
+    unsigned st = 0;
+    const int nra = a.sc->n_ra;
+
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        int tix = tile % a.ntx, tiy = (tile / a.ntx) % a.nty, tiz = tile / (a.ntx * a.nty);
+        int c0x = tix * a.tx, c0y = tiy * a.ty, c0z = tiz * a.tz;
+        __syncthreads();
+        T U = stage_tile<T, false>(a, sU, c0x, c0y, c0z, sred);
+        const bool has_ra = a.tile_flag[tile] != 0 && nra > 0;
+
+        // this thread's site
+        const int q = threadIdx.x;
+        const int p = q / per_par;
+        const int rr = q % per_par;
+        const int lx = rr % a.tx, ly = (rr / a.tx) % a.ty, lz = rr / (a.tx * a.ty);
+        const bool inbox = (q < 2 * per_par) && (c0x + lx < a.nx) && (c0y + ly < a.ny) && (c0z + lz < a.nz);
+        const int slot = (p * PLANE) + ((lz + 2) * SY + (ly + 2)) * SX + (lx + 2);
+        Vec4<T> ui = inbox ? sU[slot] : Vec4<T>{kVacant, kVacant, kVacant, 0};
+        const bool live = inbox && ui.x < (T)(0.5f * kVacant);
+        Acc<T> rho;
+        if (live) {
+            T ru = sqrt(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z);
+            T lim = a.rc_lat + ru + U;
+            T lim2 = lim * lim;
+            const float4 *po = sOff + p * kNVec;
+            for (int s = 0; s < a.sh.nshell; ++s) {
+                if ((T)a.sh.n2[s] > lim2) break;
+                const T thr = sizeof(T) == 4 ? (T)a.sh.thr[s] : (T)a.sh.thr_d[s];
+                const int kb = a.sh.begin[s], ke = a.sh.begin[s + 1];
+#pragma unroll 4
+                for (int k = kb; k < ke; ++k) {
+                    float4 o = po[k];
+                    Vec4<T> uj = sU[slot + __float_as_int(o.x)];
+                    T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
+                    T qq = (dx + (T)o.y) * dx + (dy + (T)o.z) * dy + (dz + (T)o.w) * dz;
+                    if (qq < thr) {
+                        int seg;
+                        T t, rinv;
+                        bool fh;
+                        shell_arg<T>(a.sh, s, qq, a.S, a.rfloor2, seg, t, rinv, fh);
+                        seg = clamp_seg<T>(seg, a.nseg, t);
+                        if (fh) st |= kStRfloor;
+                        Vec4<T> c = tabf[seg];
+                        rho.add(((c.x * t + c.y) * t + c.z) * t + c.w);
+                    }
+                }
+            }
+        }
+        if (has_ra) {
+            int pos = 0;
+            const int sx = 2 * lx + p, sy = 2 * ly + p, sz = 2 * lz + p;
+            const int Lx = 2 * a.nx, Ly = 2 * a.ny, Lz = 2 * a.nz;
+            while (true) {
+                __syncthreads();
+                int cnt = stage_runaways<T, false>(a, nra, pos, c0x, c0y, c0z, sRh, sRu, sst);
+                if (cnt == 0) break;
+                if (live) {
+                    for (int j = 0; j < cnt; ++j) {
+                        int4 h = sRh[j];
+                        Vec4<T> uj = sRu[j];
+                        int nx_ = h.x - sx, ny_ = h.y - sy, nz_ = h.z - sz;
+                        nx_ -= (nx_ > a.nx) ? Lx : 0;
+                        nx_ += (nx_ < -a.nx) ? Lx : 0;
+                        ny_ -= (ny_ > a.ny) ? Ly : 0;
+                        ny_ += (ny_ < -a.ny) ? Ly : 0;
+                        nz_ -= (nz_ > a.nz) ? Lz : 0;
+                        nz_ += (nz_ < -a.nz) ? Lz : 0;
+                        T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
+                        T qq = (dx + (T)(2 * nx_)) * dx + (dy + (T)(2 * ny_)) * dy + (dz + (T)(2 * nz_)) * dz;
+                        T r2 = (T)(nx_ * nx_ + ny_ * ny_ + nz_ * nz_) + qq;
+                        if (r2 < a.rc2) {
+                            int seg;
+                            T t, rinv;
+                            bool fh;
+                            direct_arg<T>(r2, a.S, a.rfloor2, seg, t, rinv, fh);
+                            seg = clamp_seg<T>(seg, a.nseg, t);
+                            if (fh) st |= kStRfloor;
+                            Vec4<T> c = tabf[seg];
+                            rho.add(((c.x * t + c.y) * t + c.z) * t + c.w);
+                        }
+                    }
+                }
+                if (pos >= nra) break;
+            }
+        }
+        if (live) {
+            long long sid = (((long long)(c0z + lz) * a.ny + (c0y + ly)) * a.nx + (c0x + lx)) * 2 + p;
+            T rh = rho.value();
+            T dF;
+            T Fv = embed<T>(a.tab_F, a.nseg, a.Srho, a.rho_max, rh, dF, st);
+            a.fp_out[sid] = dF;
+            if (ENERGY) {
+                a.rho_out[sid] = rh;
+                a.e_out[sid] = (double)Fv;
+            }
+        }
+    }
+    if (st) atomicOr(&a.sc->status, st);
+}
+
+// ---------------------------------------------------------------------------
+// force pass (Eq. eam_force_ij) + closing half kick of velocity Verlet
+// ---------------------------------------------------------------------------
+
+template <typename T, bool ENERGY>
+__global__ void __launch_bounds__(1024, 1) k_force(const __grid_constant__ GatherArgs<T> a)
+{
+    extern __shared__ __align__(32) unsigned char smem[];
+    const Vec4<T> *tab0;
+    const Vec2<T> *tab1;
+    size_t off = 0;
+    if (a.tables_in_smem) {
+        Vec4<T> *t0 = reinterpret_cast<Vec4<T> *>(smem);
+        Vec2<T> *t1 = reinterpret_cast<Vec2<T> *>(smem + sizeof(Vec4<T>) * (size_t)a.nseg);
+        for (int k = threadIdx.x; k < a.nseg; k += blockDim.x) {
+            t0[k] = a.tab_d0[k];
+            t1[k] = a.tab_d1[k];
+        }
+        tab0 = t0;
+        tab1 = t1;
+        off = (sizeof(Vec4<T>) + sizeof(Vec2<T>)) * (size_t)a.nseg;
+    } else {
+        tab0 = a.tab_d0;
+        tab1 = a.tab_d1;
+    }
+    off = (off + 255) & ~(size_t)255;
+    float4 *sOff = reinterpret_cast<float4 *>(smem + off);
+    off += sizeof(float4) * 2 * kNVec;
+    Vec4<T> *sU = reinterpret_cast<Vec4<T> *>(smem + off);
+    off += tile_smem_bytes<T>(a.tx, a.ty, a.tz);
+    int4 *sRh = reinterpret_cast<int4 *>(smem + off);
+    off += sizeof(int4) * kRaChunk;
+    Vec4<T> *sRu = reinterpret_cast<Vec4<T> *>(smem + off);
+    off += sizeof(Vec4<T>) * kRaChunk;
+    float *sred = reinterpret_cast<float *>(smem + off);
+    off += sizeof(float) * 80;
+    RaStage *sst = reinterpret_cast<RaStage *>(smem + off);
+
+    for (int k = threadIdx.x; k < 2 * kNVec; k += blockDim.x) sOff[k] = (&a.off[0][0])[k];
+
+    const int SX = a.tx + 4, SY = a.ty + 4, SZ = a.tz + 4;
+    const int PLANE = SX * SY * SZ;
+    const int per_par = a.tx * a.ty * a.tz;
+    unsigned st = 0;
+    const int nra = a.sc->n_ra;
+    const double hdt = 0.5 * a.sc->dt;
+    double vmax2 = 0.0;
+
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        int tix = tile % a.ntx, tiy = (tile / a.ntx) % a.nty, tiz = tile / (a.ntx * a.nty);
+        int c0x = tix * a.tx, c0y = tiy * a.ty, c0z = tiz * a.tz;
+        __syncthreads();
+        T U = stage_tile<T, true>(a, sU, c0x, c0y, c0z, sred);
+        const bool has_ra = a.tile_flag[tile] != 0 && nra > 0;
+
+        const int q = threadIdx.x;
+        const int p = q / per_par;
+        const int rr = q % per_par;
+        const int lx = rr % a.tx, ly = (rr / a.tx) % a.ty, lz = rr / (a.tx * a.ty);
+        const bool inbox = (q < 2 * per_par) && (c0x + lx < a.nx) && (c0y + ly < a.ny) && (c0z + lz < a.nz);
+        const int slot = (p * PLANE) + ((lz + 2) * SY + (ly + 2)) * SX + (lx + 2);
+        Vec4<T> ui = inbox ? sU[slot] : Vec4<T>{kVacant, kVacant, kVacant, 0};
+        const bool live = inbox && ui.x < (T)(0.5f * kVacant);
+        Acc<T> fx, fy, fz;
+        double ephi = 0.0;
+        if (live) {
+            T ru = sqrt(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z);
+            T lim = a.rc_lat + ru + U;
+            T lim2 = lim * lim;
+            const float4 *po = sOff + p * kNVec;
+            for (int s = 0; s < a.sh.nshell; ++s) {
+                if ((T)a.sh.n2[s] > lim2) break;
+                const T thr = sizeof(T) == 4 ? (T)a.sh.thr[s] : (T)a.sh.thr_d[s];
+                const int kb = a.sh.begin[s], ke = a.sh.begin[s + 1];
+#pragma unroll 2
+                for (int k = kb; k < ke; ++k) {
+                    float4 o = po[k];
+                    Vec4<T> uj = sU[slot + __float_as_int(o.x)];
+                    T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
+                    T qq = (dx + (T)o.y) * dx + (dy + (T)o.z) * dy + (dz + (T)o.w) * dz;
+                    if (qq < thr) {
+                        int seg;
+                        T t, rinv;
+                        bool fh;
+                        shell_arg<T>(a.sh, s, qq, a.S, a.rfloor2, seg, t, rinv, fh);
+                        seg = clamp_seg<T>(seg, a.nseg, t);
+                        Vec4<T> c0 = tab0[seg];
+                        Vec2<T> c1 = tab1[seg];
+                        T dfr = (c0.x * t + c0.y) * t + c0.z;
+                        T dph = (c0.w * t + c1.x) * t + c1.y;
+                        T coef = (ui.w + uj.w) * dfr + dph;
+                        T sc = fh ? (T)0 : coef * rinv;
+                        if (fh) st |= kStRfloor;
+                        fx.add(sc * (dx + (T)0.5 * (T)o.y));
+                        fy.add(sc * (dy + (T)0.5 * (T)o.z));
+                        fz.add(sc * (dz + (T)0.5 * (T)o.w));
+                        if (ENERGY) {
+                            Vec4<T> cp = a.tab_phi[seg];
+                            ephi += 0.5 * (double)(((cp.x * t + cp.y) * t + cp.z) * t + cp.w);
+                        }
+                    }
+                }
+            }
+        }
+        if (has_ra) {
+            int pos = 0;
+            const int sx = 2 * lx + p, sy = 2 * ly + p, sz = 2 * lz + p;
+            const int Lx = 2 * a.nx, Ly = 2 * a.ny, Lz = 2 * a.nz;
+            while (true) {
+                __syncthreads();
+                int cnt = stage_runaways<T, true>(a, nra, pos, c0x, c0y, c0z, sRh, sRu, sst);
+                if (cnt == 0) break;
+                if (live) {
+                    for (int j = 0; j < cnt; ++j) {
+                        int4 h = sRh[j];
+                        Vec4<T> uj = sRu[j];
+                        int nx_ = h.x - sx, ny_ = h.y - sy, nz_ = h.z - sz;
+                        nx_ -= (nx_ > a.nx) ? Lx : 0;
+                        nx_ += (nx_ < -a.nx) ? Lx : 0;
+                        ny_ -= (ny_ > a.ny) ? Ly : 0;
+                        ny_ += (ny_ < -a.ny) ? Ly : 0;
+                        nz_ -= (nz_ > a.nz) ? Lz : 0;
+                        nz_ += (nz_ < -a.nz) ? Lz : 0;
+                        T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
+                        T qq = (dx + (T)(2 * nx_)) * dx + (dy + (T)(2 * ny_)) * dy + (dz + (T)(2 * nz_)) * dz;
+                        T r2 = (T)(nx_ * nx_ + ny_ * ny_ + nz_ * nz_) + qq;
+                        if (r2 < a.rc2) {
+                            int seg;
+                            T t, rinv;
+                            bool fh;
+                            direct_arg<T>(r2, a.S, a.rfloor2, seg, t, rinv, fh);
+                            seg = clamp_seg<T>(seg, a.nseg, t);
+                            Vec4<T> c0 = tab0[seg];
+                            Vec2<T> c1 = tab1[seg];
+                            T dfr = (c0.x * t + c0.y) * t + c0.z;
+                            T dph = (c0.w * t + c1.x) * t + c1.y;
+                            T coef = (ui.w + uj.w) * dfr + dph;
+                            T sc = fh ? (T)0 : coef * rinv;
+                            if (fh) st |= kStRfloor;
+                            fx.add(sc * (dx + (T)nx_));
+                            fy.add(sc * (dy + (T)ny_));
+                            fz.add(sc * (dz + (T)nz_));
+                            if (ENERGY) {
+                                Vec4<T> cp = a.tab_phi[seg];
+                                ephi += 0.5 * (double)(((cp.x * t + cp.y) * t + cp.z) * t + cp.w);
+                            }
+                        }
+                    }
+                }
+                if (pos >= nra) break;
+            }
+        }
+        if (live) {
+            long long sid = (((long long)(c0z + lz) * a.ny + (c0y + ly)) * a.nx + (c0x + lx)) * 2 + p;
+            double conv = a.acc_conv;
+            double gx = (double)fx.value() * conv, gy = (double)fy.value() * conv, gz = (double)fz.value() * conv;
+            a.ax[sid] = (T)gx;
+            a.ay[sid] = (T)gy;
+            a.az[sid] = (T)gz;
+            if (!isfinite(gx) || !isfinite(gy) || !isfinite(gz)) st |= kStNonfinite;
+            if (a.kick) {
+                // velocities advance with the stored (precision-T) acceleration
+                double vx = a.vx[sid] + hdt * (double)(T)gx;
+                double vy = a.vy[sid] + hdt * (double)(T)gy;
+                double vz = a.vz[sid] + hdt * (double)(T)gz;
+                a.vx[sid] = vx;
+                a.vy[sid] = vy;
+                a.vz[sid] = vz;
+                double v2 = vx * vx + vy * vy + vz * vz;
+                vmax2 = v2 > vmax2 ? v2 : vmax2;
+            }
+            if (ENERGY) a.e_out[sid] += ephi;
+        }
+    }
+    if (st) atomicOr(&a.sc->status, st);
+    if (a.kick) {
+        // block max of |v| -> one atomicMax on the (non-negative) double bits
+        double m = vmax2;
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        __syncthreads();
+        double *sm = reinterpret_cast<double *>(sred);
+        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double w = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) w = fmax(w, sm[k]);
+            w = sqrt(w);
+            atomicMax(&a.sc->vacc_bits, (unsigned long long)__double_as_longlong(w));
+        }
+    }
+}
+
+}  // namespace misa
