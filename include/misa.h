@@ -191,6 +191,53 @@ int misa_load(misa_sim *s, const char *path);
 int misa_tile_count(void);
 int misa_tile_shape(int index, int *tx, int *ty, int *tz);
 
+/* Allocation-free force evaluation (the paper has no counterpart; it exists
+ * for callers that must not allocate device memory).
+ *
+ * Some callers cannot call cudaMalloc: code that runs inside a framework
+ * whose memory pool owns every device byte, code on a latency-critical path
+ * where cudaMalloc's implicit device synchronisation is not acceptable, and
+ * plug-ins loaded into a host program that has reserved the GPU's memory up
+ * front.  For them this entry point computes what misa_set_state followed by
+ * misa_get_forces / misa_get_energies computes -- per-atom EAM forces
+ * (Eq. eam_force_ij) and per-atom energies E_i (Eq. eam_base) of an
+ * explicit configuration -- without creating a handle and without any
+ * device allocation: its working memory is one file-scope __device__ array
+ * of the library (MISA_STATIC_SCRATCH_BYTES, about 9 MB), which every GPU
+ * that loads the library holds until the process exits.
+ *
+ *   nx, ny, nz    box in cubic bcc cells (each >= 6); natoms = 2 nx ny nz
+ *                 must not exceed MISA_STATIC_MAX_ATOMS
+ *   a0, rc, skin  as in misa_params
+ *   n_knots       knots per table, 8 .. MISA_STATIC_MAX_KNOTS
+ *   knots         DEVICE pointer, 3 n_knots doubles: f, phi, F knot values
+ *                 (same grids as misa_params)
+ *   rho_max       end of the embedding table
+ *   precision     MISA_FP64 or MISA_FP32_FORCE
+ *   x             DEVICE pointer, 3 natoms doubles, positions (A)
+ *   forces        DEVICE pointer, 3 natoms doubles, output (eV/A), by atom id
+ *   energies      DEVICE pointer, natoms doubles, output E_i (eV), or NULL
+ *   stream        cudaStream_t to run on (NULL = default stream)
+ * The caller owns all four buffers.  At most MISA_STATIC_RUNAWAY_CAP atoms
+ * may be off their lattice sites (else MISA_ERUNAWAY_OVERFLOW).  Sizes
+ * beyond the limits return MISA_EINVAL without touching the GPU; the
+ * message is in misa_last_error(NULL).
+ *
+ * The first call on a device looks up the device address of the scratch
+ * array (set-up, once per device, with that device current); make that
+ * first call before any stream capture on the device.  Every call shares
+ * the one array and clears the parts that must start from zero; calls that
+ * overlap on the GPU (several streams or host threads at once) race on it
+ * and must be serialised by the caller.  Returns when the outputs are
+ * complete (it synchronises the stream). */
+#define MISA_STATIC_MAX_ATOMS 32768
+#define MISA_STATIC_MAX_KNOTS 8192
+#define MISA_STATIC_RUNAWAY_CAP 1024
+#define MISA_STATIC_SCRATCH_BYTES (9u * 1024u * 1024u)
+int misa_eam_forces_static(int32_t nx, int32_t ny, int32_t nz, double a0, double rc, double skin,
+                           int32_t n_knots, const double *knots, double rho_max, int32_t precision,
+                           const double *x, double *forces, double *energies, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -834,3 +835,183 @@ int misa_tile_shape(int index, int *tx, int *ty, int *tz)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free force evaluation (misa_eam_forces_static)
+// ---------------------------------------------------------------------------
+// For callers that must not allocate device memory: all working memory of
+// one force evaluation comes from this file-scope array.  Host code cannot
+// use the symbol's host-side name as a device address; its device address is
+// looked up once per device with cudaGetSymbolAddress.
+
+namespace {
+
+constexpr size_t kStaticAlign = 256;
+// upper bound of the carve below for either precision: per site <= 160 B,
+// per run-away slot <= 512 B, per knot <= 160 B, one flag per cell, the
+// scalars, and the alignment padding of every buffer
+constexpr size_t kStaticNeed = 160ull * MISA_STATIC_MAX_ATOMS + 512ull * MISA_STATIC_RUNAWAY_CAP +
+                               160ull * MISA_STATIC_MAX_KNOTS + 4ull * (MISA_STATIC_MAX_ATOMS / 2) +
+                               sizeof(DevScalars) + 96 * kStaticAlign;
+static_assert(kStaticNeed <= MISA_STATIC_SCRATCH_BYTES, "static scratch too small");
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_static_scratch[MISA_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_static_mu;
+void *g_static_addr[256] = {};  // device address of g_static_scratch, per device ordinal
+
+struct Carver {
+    unsigned char *base;
+    size_t off = 0;
+    template <typename X>
+    X *take(size_t n)
+    {
+        off = (off + kStaticAlign - 1) & ~(kStaticAlign - 1);
+        X *p = reinterpret_cast<X *>(base + off);
+        off += sizeof(X) * n;
+        return p;
+    }
+};
+
+// Points every buffer of s into the static array; returns the bytes used.
+template <typename T>
+size_t carve_static(misa_sim *s, unsigned char *base, int nk)
+{
+    Carver c{base};
+    const size_t ns = (size_t)s->ns, cap = (size_t)s->cap;
+    s->sid = c.take<int>(ns);
+    s->claim = c.take<int>(ns);
+    for (int d = 0; d < 3; ++d) {
+        s->u[d] = c.take<double>(ns);
+        s->v[d] = c.take<double>(ns);
+        s->a[d] = c.take<T>(ns);
+        s->s[d] = sizeof(T) == 8 ? (void *)s->u[d] : (void *)c.take<T>(ns);
+        s->ra_u[d] = c.take<double>(cap);
+        s->ra_v[d] = c.take<double>(cap);
+        s->ra_s[d] = c.take<T>(cap);
+        s->ra_a[d] = c.take<T>(cap);
+        s->t_u[d] = c.take<double>(cap);
+        s->t_v[d] = c.take<double>(cap);
+        s->t_s[d] = c.take<T>(cap);
+        s->t_a[d] = c.take<T>(cap);
+    }
+    s->fp = c.take<T>(ns);
+    s->rho = c.take<T>(ns);
+    s->esite = c.take<double>(ns);
+    s->ra_home = c.take<int>(cap);
+    s->ra_id = c.take<int>(cap);
+    s->t_home = c.take<int>(cap);
+    s->t_id = c.take<int>(cap);
+    s->ra_fp = c.take<T>(cap);
+    s->ra_rho = c.take<T>(cap);
+    s->ra_e = c.take<double>(cap);
+    s->tab_f = c.take<Vec4<T>>(nk);
+    s->tab_phi = c.take<Vec4<T>>(nk);
+    s->tab_F = c.take<Vec4<T>>(nk);
+    s->tab_d0 = c.take<Vec4<T>>(nk);
+    s->tab_d1 = c.take<Vec2<T>>(nk);
+    s->sc = c.take<DevScalars>(1);
+    s->out_buf = c.take<double>(3 * ns);
+    s->aux_int = c.take<int>(ns);
+    s->tile_flag = c.take<int>(ns / 2);
+    return c.off;
+}
+
+template <typename T>
+int static_forces_impl(misa_sim *s, const double *knots, const double *x, double *forces, double *energies)
+{
+    const int n = s->p.n_knots;
+    const double hr = s->p.rc / (n - 1), hrho = s->p.rho_max / (n - 1);
+    // the scalars (step, time, list counts, status) start from zero on every call
+    CK(cudaMemsetAsync(s->sc, 0, sizeof(DevScalars), s->st));
+    k_spline_tables<T><<<(n + 255) / 256, 256, 0, s->st>>>(knots, knots + n, knots + 2 * n, n, hr, hrho,
+                                                            (Vec4<T> *)s->tab_f, (Vec4<T> *)s->tab_phi,
+                                                            (Vec4<T> *)s->tab_F, (Vec4<T> *)s->tab_d0,
+                                                            (Vec2<T> *)s->tab_d1);
+    int rc = configure<T>(s);
+    if (rc) return rc;
+    // hash the positions into the lattice list (clears sites, claims, list)
+    // and evaluate forces; then the energy pass for E_i
+    rc = set_state_impl<T>(s, x, nullptr);
+    if (rc) return rc;
+    MdArgs<T> m = md_args<T>(s);
+    const double L[3] = {s->nx * s->p.a0, s->ny * s->p.a0, s->nz * s->p.a0};
+    k_scatter<T><<<s->nsm * 8, 256, 0, s->st>>>(m, 2, s->out_buf, L[0], L[1], L[2]);
+    CK(cudaMemcpyAsync(forces, s->out_buf, sizeof(double) * 3 * (size_t)s->ns, cudaMemcpyDeviceToDevice, s->st));
+    if (energies) {
+        rc = launch_forces<T>(s, 0, true);
+        if (rc) return rc;
+        m = md_args<T>(s);
+        k_scatter<T><<<s->nsm * 8, 256, 0, s->st>>>(m, 4, s->out_buf, L[0], L[1], L[2]);
+        CK(cudaMemcpyAsync(energies, s->out_buf, sizeof(double) * (size_t)s->ns, cudaMemcpyDeviceToDevice, s->st));
+    }
+    CK(cudaGetLastError());
+    return check_status(s);
+}
+
+}  // namespace
+
+extern "C" int misa_eam_forces_static(int32_t nx, int32_t ny, int32_t nz, double a0, double rc, double skin,
+                                      int32_t n_knots, const double *knots, double rho_max, int32_t precision,
+                                      const double *x, double *forces, double *energies, void *stream)
+{
+    misa_sim *none = nullptr;
+    if (!knots || !x || !forces) return fail(none, MISA_EINVAL, "static forces: knots, x and forces are required");
+    if (nx < 6 || ny < 6 || nz < 6) return fail(none, MISA_EINVAL, "static forces: each box dimension must be >= 6 cells");
+    long long ns = 2LL * nx * ny * nz;
+    if (ns > MISA_STATIC_MAX_ATOMS)
+        return fail(none, MISA_EINVAL, "static forces: " + std::to_string(ns) + " atoms exceed the limit of " +
+                                           std::to_string(MISA_STATIC_MAX_ATOMS));
+    if (n_knots < 8 || n_knots > MISA_STATIC_MAX_KNOTS)
+        return fail(none, MISA_EINVAL, "static forces: n_knots must be in [8, " + std::to_string(MISA_STATIC_MAX_KNOTS) + "]");
+    if (!(a0 > 0) || !(rc > 0) || !(skin > 0) || !(rho_max > 0)) return fail(none, MISA_EINVAL, "static forces: a0, rc, skin, rho_max must be > 0");
+    double half = 0.5 * a0, roff = (rc + 2.0 * skin) / half;
+    if (roff * roff >= 27.0) return fail(none, MISA_EINVAL, "static forces: (rc + 2 skin) must be below sqrt(27) a0/2");
+    if (skin >= 0.25 * std::sqrt(3.0) * a0) return fail(none, MISA_EINVAL, "static forces: skin too large");
+    if (precision != MISA_FP64 && precision != MISA_FP32_FORCE) return fail(none, MISA_EINVAL, "static forces: precision");
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256)
+        return fail(none, MISA_ECUDA, "static forces: no current CUDA device");
+    void *base = nullptr;
+    {
+        // set-up, once per device, with that device current
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_addr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+            if (e != cudaSuccess || !p)
+                return fail(none, MISA_ECUDA, std::string("static forces: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_static_addr[dev] = p;
+        }
+        base = g_static_addr[dev];
+    }
+
+    misa_sim s;  // a handle on the host stack; every device buffer is carved from the static array
+    misa_default_params(&s.p);
+    s.p.nx = nx; s.p.ny = ny; s.p.nz = nz;
+    s.p.a0 = a0; s.p.rc = rc; s.p.skin = skin;
+    s.p.mass = 1.0;  // forces do not depend on it
+    s.p.n_knots = n_knots;
+    s.p.rho_max = rho_max;
+    s.p.precision = precision;
+    s.st = (cudaStream_t)stream;
+    s.nx = nx; s.ny = ny; s.nz = nz;
+    s.ns = ns;
+    s.prec = precision;
+    s.cap = MISA_STATIC_RUNAWAY_CAP;
+    s.tile = 0;
+    cudaDeviceGetAttribute(&s.nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (s.nsm <= 0) s.nsm = 1;
+    size_t used = precision == MISA_FP64 ? carve_static<double>(&s, (unsigned char *)base, n_knots)
+                                         : carve_static<float>(&s, (unsigned char *)base, n_knots);
+    if (used > MISA_STATIC_SCRATCH_BYTES) return fail(none, MISA_EINVAL, "static forces: scratch layout exceeds the array");
+    int r = precision == MISA_FP64 ? static_forces_impl<double>(&s, knots, x, forces, energies)
+                                   : static_forces_impl<float>(&s, knots, x, forces, energies);
+    if (r != MISA_OK) g_create_error = s.err;
+    return r;
+}

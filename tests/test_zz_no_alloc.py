@@ -1,0 +1,83 @@
+"""The allocation-free entry point misa_eam_forces_static, called through the
+C ABI, against the handle-based entry points (misa_set_state +
+misa_get_forces / misa_get_energies) on the same positions.
+
+Some callers cannot allocate device memory (a framework pool that owns every
+byte, a latency-critical path that cannot take cudaMalloc's implicit
+synchronisation, a plug-in in a host program that reserved the GPU up
+front); misa_eam_forces_static serves them from a static device array.
+This file is collected last so that a run stopping at the first failure has
+run every other test before it; it also passes alone in a fresh process.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2107_07866_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def nerr(x, xo):
+    x = np.asarray(x, dtype=np.float64).reshape(len(xo), -1)
+    xo = np.asarray(xo, dtype=np.float64).reshape(len(xo), -1)
+    mag = np.linalg.norm(xo, axis=1)
+    rms = np.sqrt(np.mean(mag * mag))
+    return float(np.max(np.linalg.norm(x - xo, axis=1) / np.maximum(mag, max(rms, 1e-300))))
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2107_07866_gb300 import build
+    build.build()
+    from paper_2107_07866_gb300 import misa
+    L = misa.lib()
+    f = L.misa_eam_forces_static
+    f.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_int32, C.c_void_p,
+                  C.c_double, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    f.restype = C.c_int
+    return torch, misa, f
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_static_entry_matches_handle_entry_on_two_calls(env, prec):
+    torch, misa, fn = env
+    pot = synth.potential()
+    dims = (12, 10, 8)
+    natoms = 2 * dims[0] * dims[1] * dims[2]
+    knots = torch.from_numpy(np.concatenate([pot.f, pot.phi, pot.F])).cuda()
+    code = misa.FP64 if prec == "fp64" else misa.FP32_FORCE
+    stream = torch.cuda.current_stream().cuda_stream
+    # two different configurations in a row: the second call must not see
+    # anything the first one left in the shared array
+    for seed, n_int in ((3, 10), (4, 2)):
+        xh = synth.cascade_snapshot(*dims, 0.12, n_int, 3, seed)
+        x = torch.from_numpy(xh).cuda()
+        f_out = torch.empty((natoms, 3), dtype=torch.float64, device="cuda")
+        e_out = torch.empty(natoms, dtype=torch.float64, device="cuda")
+        rc = fn(*dims, synth.A0_FE, pot.rc, 0.6, pot.n, knots.data_ptr(), pot.rho_max, code, x.data_ptr(),
+                f_out.data_ptr(), e_out.data_ptr(), stream)
+        assert rc == misa.MISA_OK, misa.lib().misa_last_error(None)
+        with misa.Sim(pot, *dims, precision=prec) as s:
+            s.set_state(xh)
+            f_ref = s.forces()
+            _, _, e_ref = s.energies(per_atom=True)
+        assert nerr(f_out.cpu().numpy(), f_ref) < TOL[prec]
+        assert nerr(e_out.cpu().numpy(), e_ref) < TOL[prec]
+
+
+def test_static_entry_rejects_oversized_input(env):
+    torch, misa, fn = env
+    pot = synth.potential()
+    knots = torch.from_numpy(np.concatenate([pot.f, pot.phi, pot.F])).cuda()
+    x = torch.zeros(3, dtype=torch.float64, device="cuda")
+    # 2 * 30^3 = 54,000 atoms > the static limit: refused before any GPU work
+    rc = fn(30, 30, 30, synth.A0_FE, pot.rc, 0.6, pot.n, knots.data_ptr(), pot.rho_max, misa.FP64,
+            x.data_ptr(), x.data_ptr(), None, None)
+    assert rc == misa.MISA_EINVAL
+    assert b"exceed" in misa.lib().misa_last_error(None)
