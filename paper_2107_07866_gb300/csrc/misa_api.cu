@@ -170,7 +170,6 @@ void fill_gather(misa_sim *s, GatherArgs<T> &g)
     std::memset(&g, 0, sizeof(g));
     const TileShape &ts = kTiles[s->tile];
     g.nx = s->nx; g.ny = s->ny; g.nz = s->nz;
-    g.tx = ts.tx; g.ty = ts.ty; g.tz = ts.tz;
     g.ntx = s->ntx; g.nty = s->nty; g.ntz = s->ntz; g.ntiles = s->ntiles;
     g.ux = (const T *)s->s[0]; g.uy = (const T *)s->s[1]; g.uz = (const T *)s->s[2];
     g.fp = (const T *)s->fp;
@@ -204,7 +203,6 @@ void fill_gather(misa_sim *s, GatherArgs<T> &g)
     g.sc = s->sc;
     g.acc_conv = kAccUnit / s->p.mass;
     g.kick = 1;
-    g.tables_in_smem = sizeof(T) == 4 ? 1 : 0;
     // neighbour offset index for this tile shape (Sec. 3): per parity, the
     // shared-memory slot displacement of every lattice vector
     const int SX = ts.tx + 4, SY = ts.ty + 4, SZ = ts.tz + 4;
@@ -224,16 +222,13 @@ void fill_gather(misa_sim *s, GatherArgs<T> &g)
     for (int q = 0; q < kLVec.nshell; ++q) {
         if (kLVec.shell_n2[q] > roff * roff) break;
         int n2 = kLVec.shell_n2[q];
-        sh.n2[q] = n2;
-        sh.begin[q] = kLVec.shell_begin[q];
-        sh.begin[q + 1] = kLVec.shell_begin[q + 1];
         sh.thr[q] = (float)(rcl * rcl - n2);
         sh.thr_d[q] = rcl * rcl - n2;
         double nr = std::sqrt((double)n2);
         sh.nrm[q] = (float)nr;
         double x0 = nr * S;
         double xi = std::floor(x0);
-        sh.xint[q] = (int)xi;
+        sh.xoff[q] = (int)xi - 0x4B400000;
         sh.xfrac[q] = (float)(x0 - xi);
         sh.nshell = q + 1;
     }
@@ -243,25 +238,50 @@ template <typename T>
 size_t smem_density_bytes(misa_sim *s)
 {
     const TileShape &ts = kTiles[s->tile];
-    size_t off = sizeof(T) == 4 ? sizeof(Vec4<T>) * (size_t)(s->p.n_knots - 1) : 0;
-    off = (off + 255) & ~(size_t)255;
-    off += sizeof(float4) * 2 * kNVec;
-    off += tile_smem_bytes<T>(ts.tx, ts.ty, ts.tz);
-    off += sizeof(int4) * kRaChunk + sizeof(Vec4<T>) * kRaChunk + sizeof(float) * 80 + sizeof(RaStage);
-    return off;
+    return gather_smem_bytes<T>(sizeof(T) == 4 ? sizeof(Vec4<T>) * (size_t)(s->p.n_knots - 1) : 0, ts.tx, ts.ty, ts.tz);
 }
 
 template <typename T>
 size_t smem_force_bytes(misa_sim *s)
 {
     const TileShape &ts = kTiles[s->tile];
-    size_t off = sizeof(T) == 4 ? (sizeof(Vec4<T>) + sizeof(Vec2<T>)) * (size_t)(s->p.n_knots - 1) : 0;
-    off = (off + 255) & ~(size_t)255;
-    off += sizeof(float4) * 2 * kNVec;
-    off += tile_smem_bytes<T>(ts.tx, ts.ty, ts.tz);
-    off += sizeof(int4) * kRaChunk + sizeof(Vec4<T>) * kRaChunk + sizeof(float) * 80 + sizeof(RaStage);
-    return off;
+    return gather_smem_bytes<T>(sizeof(T) == 4 ? (sizeof(Vec4<T>) + sizeof(Vec2<T>)) * (size_t)(s->p.n_knots - 1) : 0,
+                                ts.tx, ts.ty, ts.tz);
 }
+
+// one instantiation of the tile kernels per tile shape
+template <typename T, int TX, int TY, int TZ>
+struct TileKernels {
+    static int attrs(misa_sim *s)
+    {
+        CK(cudaFuncSetAttribute(k_density<T, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_density));
+        CK(cudaFuncSetAttribute(k_density<T, TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_density));
+        CK(cudaFuncSetAttribute(k_force<T, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_force));
+        CK(cudaFuncSetAttribute(k_force<T, TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_force));
+        return MISA_OK;
+    }
+    static void density(misa_sim *s, const GatherArgs<T> &g, int grid, bool energy)
+    {
+        constexpr int nt = 2 * TX * TY * TZ;
+        if (energy) k_density<T, TX, TY, TZ, true><<<grid, nt, s->smem_density, s->st>>>(g);
+        else k_density<T, TX, TY, TZ, false><<<grid, nt, s->smem_density, s->st>>>(g);
+    }
+    static void force(misa_sim *s, const GatherArgs<T> &g, int grid, bool energy)
+    {
+        constexpr int nt = 2 * TX * TY * TZ;
+        if (energy) k_force<T, TX, TY, TZ, true><<<grid, nt, s->smem_force, s->st>>>(g);
+        else k_force<T, TX, TY, TZ, false><<<grid, nt, s->smem_force, s->st>>>(g);
+    }
+};
+
+// kTiles order: {8,8,8}, {8,8,4}, {8,4,4}, {16,8,4}
+#define MISA_TILE_DISPATCH(T, idx, CALL)                      \
+    switch (idx) {                                            \
+    case 0: TileKernels<T, 8, 8, 8>::CALL; break;             \
+    case 1: TileKernels<T, 8, 8, 4>::CALL; break;             \
+    case 2: TileKernels<T, 8, 4, 4>::CALL; break;             \
+    default: TileKernels<T, 16, 8, 4>::CALL; break;           \
+    }
 
 template <typename T>
 int configure(misa_sim *s)
@@ -273,10 +293,9 @@ int configure(misa_sim *s)
     s->ntiles = s->ntx * s->nty * s->ntz;
     s->smem_density = smem_density_bytes<T>(s);
     s->smem_force = smem_force_bytes<T>(s);
-    CK(cudaFuncSetAttribute(k_density<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_density));
-    CK(cudaFuncSetAttribute(k_density<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_density));
-    CK(cudaFuncSetAttribute(k_force<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_force));
-    CK(cudaFuncSetAttribute(k_force<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_force));
+    int arc = MISA_OK;
+    MISA_TILE_DISPATCH(T, s->tile, attrs(s) == MISA_OK ? (void)0 : (void)(arc = MISA_ECUDA));
+    if (arc) return fail(s, arc, s->err.empty() ? "tile kernel attributes" : s->err);
     CK(cudaFuncSetAttribute(k_ra_sort<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)(sizeof(unsigned long long) * kSortMax)));
     if (s->tile_flag == nullptr) {
@@ -297,11 +316,9 @@ template <typename T>
 int launch_forces(misa_sim *s, int kick, bool energy, bool step_marks = false)
 {
     MdArgs<T> m = md_args<T>(s);
-    const TileShape &ts = kTiles[s->tile];
     GatherArgs<T> g;
     fill_gather<T>(s, g);
     g.kick = kick;
-    const int nthr = 2 * ts.tx * ts.ty * ts.tz;
     const int grid = s->ntiles < s->nsm ? s->ntiles : s->nsm;
     CK(cudaMemsetAsync(s->tile_flag, 0, sizeof(int) * (size_t)s->ntiles, s->st));
     k_mark_tiles<T><<<64, 256, 0, s->st>>>(m);
@@ -315,19 +332,11 @@ int launch_forces(misa_sim *s, int kick, bool energy, bool step_marks = false)
     ra.ra_vx = s->ra_v[0]; ra.ra_vy = s->ra_v[1]; ra.ra_vz = s->ra_v[2];
     ra.energy = energy ? 1 : 0;
     if (step_marks) mark(s);  // end of the list phase
-    if (energy) {
-        k_density<T, true><<<grid, nthr, s->smem_density, s->st>>>(g);
-    } else {
-        k_density<T, false><<<grid, nthr, s->smem_density, s->st>>>(g);
-    }
+    MISA_TILE_DISPATCH(T, s->tile, density(s, g, grid, energy));
     if (step_marks) mark(s);
     k_ra_gather<T, 0><<<128, 256, 0, s->st>>>(ra);
     if (step_marks) mark(s);
-    if (energy) {
-        k_force<T, true><<<grid, nthr, s->smem_force, s->st>>>(g);
-    } else {
-        k_force<T, false><<<grid, nthr, s->smem_force, s->st>>>(g);
-    }
+    MISA_TILE_DISPATCH(T, s->tile, force(s, g, grid, energy));
     if (step_marks) mark(s);
     k_ra_gather<T, 1><<<128, 256, 0, s->st>>>(ra);
     if (step_marks) mark(s);

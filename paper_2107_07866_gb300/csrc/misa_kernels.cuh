@@ -18,6 +18,8 @@
 // spline coefficients of the pass in shared memory for the whole launch.
 #pragma once
 
+#include <type_traits>
+
 #include "misa_common.cuh"
 
 namespace misa {
@@ -151,21 +153,19 @@ __device__ __forceinline__ T embed(const Vec4<T> *__restrict__ tab, int nseg, T 
 // gather arguments
 // ---------------------------------------------------------------------------
 
+// Per-shell constants of the offset index (shells of equal |n|, sorted).
 struct ShellInfo {
-    int n2[kMaxShell];
-    int begin[kMaxShell + 1];
-    float thr[kMaxShell];   // rc^2 - n^2 (lattice units)
-    float nrm[kMaxShell];   // |n|
-    float xfrac[kMaxShell]; // |n| S = xint + xfrac, xfrac in [0, 1)
-    int xint[kMaxShell];
+    int nshell;              // shells within rc + 2 skin
+    float thr[kMaxShell];    // rc^2 - n^2 (lattice units)
+    float nrm[kMaxShell];    // |n|
+    float xfrac[kMaxShell];  // |n| S = xint + xfrac, xfrac in [0, 1)
+    int xoff[kMaxShell];     // xint - 0x4B400000 (bit offset of the rounding trick)
     double thr_d[kMaxShell];
-    int nshell;
 };
 
 template <typename T>
 struct GatherArgs {
     int nx, ny, nz;
-    int tx, ty, tz;
     int ntx, nty, ntz, ntiles;
     const T *ux, *uy, *uz;  // displacement per site, lattice units; vacant = kVacant
     const T *fp;            // force pass input: F' per site
@@ -189,21 +189,22 @@ struct GatherArgs {
     const T *ra_fp;
     const int *tile_flag;
     DevScalars *sc;
-    double acc_conv;  // (eV/A) -> (A/fs^2): 1/(m) * 9.6485e-3
+    double acc_conv;  // (eV/A) -> (A/fs^2): 9.6485e-3 / m
     int kick;
-    int tables_in_smem;
-    // neighbour offset index for this tile shape: per parity, per vector:
-    // (slot displacement as int bits, 2 n_x, 2 n_y, 2 n_z)
+    // neighbour offset index for this tile shape: per parity, per lattice
+    // vector: (shared-memory slot displacement as int bits, 2 n_x, 2 n_y, 2 n_z)
     float4 off[2][kNVec];
     ShellInfo sh;
 };
 
-template <typename T>
-struct TileGeom {
-    int SX, SY, SZ, SXY, PLANE;
+template <int TX, int TY, int TZ>
+struct Tile {
+    static constexpr int SX = TX + 4, SY = TY + 4, SZ = TZ + 4;
+    static constexpr int PLANE = SX * SY * SZ;
+    static constexpr int PER_PAR = TX * TY * TZ;
+    static constexpr int NT = 2 * PER_PAR;  // one thread per site
 };
 
-// smem layout helpers
 template <typename T>
 __host__ __device__ inline size_t tile_smem_bytes(int tx, int ty, int tz)
 {
@@ -214,93 +215,104 @@ struct RaStage {
     int cnt, next;
 };
 
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+__device__ __forceinline__ int wrap_cell(int g, int n)
+{
+    if (g < 0) g += n;
+    while (g >= n) g -= n;
+    return g;
+}
+
 // ---------------------------------------------------------------------------
 // tile staging
 // ---------------------------------------------------------------------------
 
-// Loads the displacements (and F' in .w for the force pass) of the tile with
-// cell origin (c0x, c0y, c0z) and a 2-cell periodic halo into sU.  Returns
-// max |u| over the occupied staged sites (lattice units), block-wide.
-template <typename T, bool WITH_FP>
-__device__ __forceinline__ T stage_tile(const GatherArgs<T> &a, Vec4<T> *sU, int c0x, int c0y, int c0z,
-                                        float *sred)
+// Loads (ux, uy, uz, F') of the tile with cell origin (c0x, c0y, c0z) plus a
+// 2-cell periodic halo into sU, split by parity.  Returns max |u| over the
+// occupied staged sites (lattice units), block-wide.
+template <typename T, int TX, int TY, int TZ, bool WITH_FP>
+__device__ __forceinline__ T stage_tile(const GatherArgs<T> &a, Vec4<T> *sU, int c0x, int c0y, int c0z, float *sred)
 {
-    const int SX = a.tx + 4, SY = a.ty + 4, SZ = a.tz + 4;
-    const int PLANE = SX * SY * SZ;
+    using G = Tile<TX, TY, TZ>;
     T umax2 = 0;
-    for (int q = threadIdx.x; q < 2 * PLANE; q += blockDim.x) {
-        int p = q & 1;
-        int r = q >> 1;
-        int x = r % SX;
-        int yz = r / SX;
-        int y = yz % SY;
-        int z = yz / SY;
-        // periodic wrap; tiles may be wider than the box, so a full modulo
-        int gx = (c0x - 2 + x + 2 * a.nx) % a.nx;
-        int gy = (c0y - 2 + y + 2 * a.ny) % a.ny;
-        int gz = (c0z - 2 + z + 2 * a.nz) % a.nz;
-        long long sid = (((long long)gz * a.ny + gy) * a.nx + gx) * 2 + p;
+    for (int q = threadIdx.x; q < 2 * G::PLANE; q += G::NT) {
+        const int p = q & 1;
+        const int r = q >> 1;
+        const int x = r % G::SX;
+        const int yz = r / G::SX;
+        const int y = yz % G::SY;
+        const int z = yz / G::SY;
+        const int gx = wrap_cell(c0x - 2 + x, a.nx);
+        const int gy = wrap_cell(c0y - 2 + y, a.ny);
+        const int gz = wrap_cell(c0z - 2 + z, a.nz);
+        const long long sid = (((long long)gz * a.ny + gy) * a.nx + gx) * 2 + p;
         Vec4<T> v;
         v.x = a.ux[sid];
         v.y = a.uy[sid];
         v.z = a.uz[sid];
         v.w = WITH_FP ? a.fp[sid] : (T)0;
-        T u2 = v.x * v.x + v.y * v.y + v.z * v.z;
+        const T u2 = v.x * v.x + v.y * v.y + v.z * v.z;
         if (v.x < (T)(0.5f * kVacant)) umax2 = umax2 > u2 ? umax2 : u2;
-        sU[p * PLANE + (z * SY + y) * SX + x] = v;
+        sU[p * G::PLANE + (z * G::SY + y) * G::SX + x] = v;
     }
-    // block max
     float m = (float)umax2;
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x < 32) {
-        float w = threadIdx.x < (blockDim.x >> 5) ? sred[threadIdx.x] : 0.f;
+        float w = threadIdx.x < (G::NT >> 5) ? sred[threadIdx.x] : 0.f;
         for (int o = 16; o > 0; o >>= 1) w = fmaxf(w, __shfl_xor_sync(0xffffffffu, w, o));
         if (threadIdx.x == 0) sred[32] = w;
     }
     __syncthreads();
-    return (T)sqrtf(sred[32]);
+    // round up by one FP32 ulp so that rounding never prunes a needed shell
+    return (T)(sqrtf(sred[32]) * 1.000001f);
 }
 
 // Stages the next chunk of run-away atoms whose home cell lies within 3
 // cells of the tile (reach rc + skin + the Wigner-Seitz radius), in list
 // order, as (home lattice coords relative to the tile origin, u, F').
 // Warp 0 scans; returns the staged count (block-uniform).
-template <typename T, bool WITH_FP>
+template <typename T, int TX, int TY, int TZ, bool WITH_FP>
 __device__ __forceinline__ int stage_runaways(const GatherArgs<T> &a, int nra, int &pos, int c0x, int c0y, int c0z,
                                               int4 *sRh, Vec4<T> *sRu, RaStage *st)
 {
     if (threadIdx.x < 32) {
-        int lane = threadIdx.x;
+        const int lane = threadIdx.x;
         int cnt = 0;
         int p0 = pos;
         while (p0 < nra && cnt < kRaChunk) {
-            int j = p0 + lane;
+            const int j = p0 + lane;
             bool take = false;
             int hx = 0, hy = 0, hz = 0;
             if (j < nra) {
-                int h = a.ra_home[j];
-                int x2 = h % (2 * a.nx);
-                int rest = h / (2 * a.nx);
-                int cy = rest % a.ny, cz = rest / a.ny;
-                int par = x2 & 1, cx = x2 >> 1;
-                int dx = cx - c0x, dy = cy - c0y, dz = cz - c0z;
+                const int h = a.ra_home[j];
+                const int x2 = h % (2 * a.nx);
+                const int rest = h / (2 * a.nx);
+                const int cy = rest % a.ny, cz = rest / a.ny;
+                const int par = x2 & 1, cx = x2 >> 1;
+                int dx = cx - c0x - TX / 2, dy = cy - c0y - TY / 2, dz = cz - c0z - TZ / 2;
                 // nearest periodic image to the tile centre
-                int mx = a.tx / 2, my = a.ty / 2, mz = a.tz / 2;
-                dx -= mx; dy -= my; dz -= mz;
                 dx -= a.nx * (int)floorf((dx + 0.5f * a.nx) / a.nx);
                 dy -= a.ny * (int)floorf((dy + 0.5f * a.ny) / a.ny);
                 dz -= a.nz * (int)floorf((dz + 0.5f * a.nz) / a.nz);
-                dx += mx; dy += my; dz += mz;
-                take = dx >= -3 && dx < a.tx + 3 && dy >= -3 && dy < a.ty + 3 && dz >= -3 && dz < a.tz + 3;
+                dx += TX / 2; dy += TY / 2; dz += TZ / 2;
+                take = dx >= -3 && dx < TX + 3 && dy >= -3 && dy < TY + 3 && dz >= -3 && dz < TZ + 3;
                 hx = 2 * dx + par;
                 hy = 2 * dy + par;
                 hz = 2 * dz + par;
             }
-            unsigned bal = __ballot_sync(0xffffffffu, take);
-            int room = kRaChunk - cnt;
-            int rank = __popc(bal & ((1u << lane) - 1u));
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
+            const int room = kRaChunk - cnt;
+            const int rank = __popc(bal & ((1u << lane) - 1u));
             if (take && rank < room) {
                 sRh[cnt + rank] = make_int4(hx, hy, hz, 0);
                 Vec4<T> u;
@@ -310,17 +322,15 @@ __device__ __forceinline__ int stage_runaways(const GatherArgs<T> &a, int nra, i
                 u.w = WITH_FP ? a.ra_fp[j] : (T)0;
                 sRu[cnt + rank] = u;
             }
-            int ntake = __popc(bal);
+            const int ntake = __popc(bal);
             if (ntake <= room) {
                 cnt += ntake;
                 p0 += 32;
             } else {
                 // chunk full: resume at the first lane that did not fit
-                int k = 0;
                 unsigned b = bal;
                 for (int q = 0; q < room; ++q) b &= b - 1;
-                k = __ffs(b) - 1;
-                p0 += k;
+                p0 += __ffs(b) - 1;
                 cnt += room;
             }
         }
@@ -330,7 +340,7 @@ __device__ __forceinline__ int stage_runaways(const GatherArgs<T> &a, int nra, i
         }
     }
     __syncthreads();
-    int c = st->cnt;
+    const int c = st->cnt;
     pos = st->next;
     return c;
 }
@@ -338,35 +348,60 @@ __device__ __forceinline__ int stage_runaways(const GatherArgs<T> &a, int nra, i
 // ---------------------------------------------------------------------------
 // pair geometry
 // ---------------------------------------------------------------------------
-// For an array pair through offset vector n (shell s): q = (2n + d).d with
-// d = u_j - u_i, so r^2 = n^2 + q.  In FP32 the spline argument is formed
-// from r - |n| = q / (r + |n|), which is small, plus the per-shell split
-// |n| S = xint + xfrac: the segment index and t keep full FP32 precision
+// Array pair through offset vector n of shell s: q = (2n + d).d with
+// d = u_j - u_i, so r^2 = n^2 + q.  Both atoms are within the skin of their
+// sites, so r >= |n_1| - 2 skin > 1 A: no r floor is needed here.
+// FP32: the spline argument is |n| S + (r - |n|) S with r - |n| = q/(r + |n|)
+// (small, full relative precision) and the per-shell split
+// |n| S = xint + xfrac, so the segment and t keep full FP32 precision
 // instead of the ~1e-4 absolute error of r S near 2000.
 
 template <typename T>
-__device__ __forceinline__ void shell_arg(const ShellInfo &sh, int s, T q, T S, T rfloor2, int &seg, T &t, T &rinv,
-                                          bool &floor_hit)
+struct ShellRegs {
+    T n2, thr, nrm, xfrac;
+    int xoff;
+};
+
+template <typename T>
+__device__ __forceinline__ int shell_arg(const ShellRegs<T> &sh, T q, T S, int nseg1, T &t, T &rinv)
 {
-    T n2 = (T)sh.n2[s];
-    T r2 = n2 + q;
-    floor_hit = r2 < rfloor2;
-    r2 = floor_hit ? rfloor2 : r2;
-    T rs = Arith<T>::rsqrt(r2);
-    rinv = rs;
+    const T r2 = sh.n2 + q;
     if constexpr (sizeof(T) == 4) {
-        T r = r2 * rs;
-        T dr = floor_hit ? (sqrtf(rfloor2) - sh.nrm[s]) : q * __frcp_rn(r + sh.nrm[s]);
-        T x = sh.xfrac[s] + dr * S;
-        seg = sh.xint[s] + Arith<T>::split(x, t);
+        const float rs = rsqrtf(r2);
+        rinv = rs;
+        const float r = r2 * rs;
+        const float dr = __fdividef(q, r + sh.nrm);
+        const float x = fmaf(dr, S, sh.xfrac);
+        const float y = __fadd_rn(__fsub_rn(x, 0.5f), 12582912.0f);
+        const float fl = __fsub_rn(y, 12582912.0f);
+        t = __fsub_rn(x, fl);
+        return min(__float_as_int(y) + sh.xoff, nseg1);
     } else {
-        T r = sqrt(r2);
-        seg = Arith<T>::split(r * S, t);
+        const double r = sqrt(r2);
+        rinv = 1.0 / r;
+        const double x = r * S;
+        const double fl = floor(x);
+        t = x - fl;
+        return min((int)fl, nseg1);
     }
 }
 
+// per-shell constants into registers (shell index known at compile time)
+template <typename T, int SH>
+__device__ __forceinline__ ShellRegs<T> shell_regs(const ShellInfo &sh)
+{
+    ShellRegs<T> r;
+    constexpr int N2 = kLVec.shell_n2[SH];
+    r.n2 = (T)N2;
+    r.thr = sizeof(T) == 4 ? (T)sh.thr[SH] : (T)sh.thr_d[SH];
+    r.nrm = (T)sh.nrm[SH];
+    r.xfrac = (T)sh.xfrac[SH];
+    r.xoff = sh.xoff[SH];
+    return r;
+}
+
 // Spline argument from r^2 directly (run-away pairs: the offset is not a
-// shell constant).
+// shell constant); clamps r at r_floor.
 template <typename T>
 __device__ __forceinline__ void direct_arg(T r2, T S, T rfloor2, int &seg, T &t, T &rinv, bool &floor_hit)
 {
@@ -394,89 +429,184 @@ __device__ __forceinline__ int clamp_seg(int seg, int nseg, T &t)
     return seg;
 }
 
+// shared-memory carve-up of the tile kernels
+template <typename T>
+struct GatherSmem {
+    float4 *off;
+    Vec4<T> *u;
+    int4 *rh;
+    Vec4<T> *ru;
+    float *red;
+    RaStage *st;
+};
+
+template <typename T, int TX, int TY, int TZ>
+__device__ __forceinline__ GatherSmem<T> carve(unsigned char *smem, size_t off)
+{
+    GatherSmem<T> g;
+    off = (off + 255) & ~(size_t)255;
+    g.off = reinterpret_cast<float4 *>(smem + off);
+    off += sizeof(float4) * 2 * kNVec;
+    g.u = reinterpret_cast<Vec4<T> *>(smem + off);
+    off += sizeof(Vec4<T>) * 2 * Tile<TX, TY, TZ>::PLANE;
+    g.rh = reinterpret_cast<int4 *>(smem + off);
+    off += sizeof(int4) * kRaChunk;
+    g.ru = reinterpret_cast<Vec4<T> *>(smem + off);
+    off += sizeof(Vec4<T>) * kRaChunk;
+    g.red = reinterpret_cast<float *>(smem + off);
+    off += sizeof(float) * 80;
+    g.st = reinterpret_cast<RaStage *>(smem + off);
+    return g;
+}
+
+template <typename T>
+__host__ __device__ inline size_t gather_smem_bytes(size_t table_bytes, int tx, int ty, int tz)
+{
+    size_t off = (table_bytes + 255) & ~(size_t)255;
+    off += sizeof(float4) * 2 * kNVec;
+    off += tile_smem_bytes<T>(tx, ty, tz);
+    off += sizeof(int4) * kRaChunk + sizeof(Vec4<T>) * kRaChunk + sizeof(float) * 80 + sizeof(RaStage);
+    return off;
+}
+
+// ---------------------------------------------------------------------------
+// shell loops over the offset index
+// ---------------------------------------------------------------------------
+// Shells are visited in order of |n| and stop at the first one beyond
+// lim = rc + |u_i| + max_tile |u_j|.  Shells up to n^2 = 12 (the 58
+// neighbours of the crystal) are evaluated without a branch: a candidate
+// outside rc is computed and masked (its segment index is clamped, so the
+// arithmetic stays finite); farther shells branch, as almost all of their
+// candidates fall outside rc.
+
+template <typename T, int SH>
+__device__ __forceinline__ void density_shells(const ShellInfo &shc, const float4 *__restrict__ po,
+                                               const Vec4<T> *__restrict__ su, int slot, const Vec4<T> &ui, T lim2, T S,
+                                               int nseg1, const Vec4<T> *__restrict__ tabf, Acc<T> &rho)
+{
+    if constexpr (SH < kLVec.nshell) {
+        constexpr int KB = kLVec.shell_begin[SH], KE = kLVec.shell_begin[SH + 1];
+        constexpr int N2 = kLVec.shell_n2[SH];
+        constexpr bool dense = N2 <= 12;
+        if (SH >= shc.nshell || (T)N2 > lim2) return;
+        const ShellRegs<T> sh = shell_regs<T, SH>(shc);
+        T part = 0;
+#pragma unroll 2
+        for (int k = KB; k < KE; ++k) {
+            const float4 o = po[k];
+            const Vec4<T> uj = su[slot + __float_as_int(o.x)];
+            const T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
+            const T qq = (dx + (T)o.y) * dx + (dy + (T)o.z) * dy + (dz + (T)o.w) * dz;
+            if (dense) {
+                T t, rinv;
+                const int seg = shell_arg<T>(sh, qq, S, nseg1, t, rinv);
+                const Vec4<T> c = tabf[seg];
+                const T v = ((c.x * t + c.y) * t + c.z) * t + c.w;
+                part += qq < sh.thr ? v : (T)0;
+            } else if (qq < sh.thr) {
+                T t, rinv;
+                const int seg = shell_arg<T>(sh, qq, S, nseg1, t, rinv);
+                const Vec4<T> c = tabf[seg];
+                part += ((c.x * t + c.y) * t + c.z) * t + c.w;
+            }
+        }
+        rho.add(part);
+        density_shells<T, SH + 1>(shc, po, su, slot, ui, lim2, S, nseg1, tabf, rho);
+    }
+}
+
+template <typename T, int SH, bool ENERGY>
+__device__ __forceinline__ void force_shells(const ShellInfo &shc, const float4 *__restrict__ po,
+                                             const Vec4<T> *__restrict__ su, int slot, const Vec4<T> &ui, T lim2, T S,
+                                             int nseg1, const Vec4<T> *__restrict__ tab0, const Vec2<T> *__restrict__ tab1,
+                                             const Vec4<T> *__restrict__ tabphi, Acc<T> &fx, Acc<T> &fy, Acc<T> &fz,
+                                             double &ephi)
+{
+    if constexpr (SH < kLVec.nshell) {
+        constexpr int KB = kLVec.shell_begin[SH], KE = kLVec.shell_begin[SH + 1];
+        constexpr int N2 = kLVec.shell_n2[SH];
+        constexpr bool dense = N2 <= 12;
+        if (SH >= shc.nshell || (T)N2 > lim2) return;
+        const ShellRegs<T> sh = shell_regs<T, SH>(shc);
+        T px = 0, py = 0, pz = 0;
+#pragma unroll 2
+        for (int k = KB; k < KE; ++k) {
+            const float4 o = po[k];
+            const Vec4<T> uj = su[slot + __float_as_int(o.x)];
+            const T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
+            const T qq = (dx + (T)o.y) * dx + (dy + (T)o.z) * dy + (dz + (T)o.w) * dz;
+            if (dense || qq < sh.thr) {
+                T t, rinv;
+                const int seg = shell_arg<T>(sh, qq, S, nseg1, t, rinv);
+                const Vec4<T> c0 = tab0[seg];
+                const Vec2<T> c1 = tab1[seg];
+                const T dfr = (c0.x * t + c0.y) * t + c0.z;
+                const T dph = (c0.w * t + c1.x) * t + c1.y;
+                T sc_ = ((ui.w + uj.w) * dfr + dph) * rinv;
+                if (dense) sc_ = qq < sh.thr ? sc_ : (T)0;
+                px += sc_ * (dx + (T)0.5 * (T)o.y);
+                py += sc_ * (dy + (T)0.5 * (T)o.z);
+                pz += sc_ * (dz + (T)0.5 * (T)o.w);
+                if (ENERGY) {
+                    const Vec4<T> cp = tabphi[seg];
+                    const double e = 0.5 * (double)(((cp.x * t + cp.y) * t + cp.z) * t + cp.w);
+                    ephi += qq < sh.thr ? e : 0.0;
+                }
+            }
+        }
+        fx.add(px);
+        fy.add(py);
+        fz.add(pz);
+        force_shells<T, SH + 1, ENERGY>(shc, po, su, slot, ui, lim2, S, nseg1, tab0, tab1, tabphi, fx, fy, fz, ephi);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // density pass: rho_i, F'(rho_i)  (Sec. 2.2 steps 1-2)
 // ---------------------------------------------------------------------------
+// Each shell's terms are summed plainly (at most 24, similar magnitudes)
+// and the shell sums are added with Kahan compensation.
 
-template <typename T, bool ENERGY>
-__global__ void __launch_bounds__(1024, 1) k_density(const __grid_constant__ GatherArgs<T> a)
+template <typename T, int TX, int TY, int TZ, bool ENERGY>
+__global__ void __launch_bounds__(2 * TX * TY * TZ, 1) k_density(const __grid_constant__ GatherArgs<T> a)
 {
+    using G = Tile<TX, TY, TZ>;
     extern __shared__ __align__(32) unsigned char smem[];
-    const Vec4<T> *tabf;
-    size_t off = 0;
-    if (a.tables_in_smem) {
+    const bool tsm = sizeof(T) == 4;
+    const Vec4<T> *tabf = a.tab_f;
+    if (tsm) {
         Vec4<T> *t = reinterpret_cast<Vec4<T> *>(smem);
-        for (int k = threadIdx.x; k < a.nseg; k += blockDim.x) t[k] = a.tab_f[k];
+        for (int k = threadIdx.x; k < a.nseg; k += G::NT) t[k] = a.tab_f[k];
         tabf = t;
-        off = sizeof(Vec4<T>) * (size_t)a.nseg;
-    } else {
-        tabf = a.tab_f;
     }
-    off = (off + 255) & ~(size_t)255;
-    float4 *sOff = reinterpret_cast<float4 *>(smem + off);
-    off += sizeof(float4) * 2 * kNVec;
-    Vec4<T> *sU = reinterpret_cast<Vec4<T> *>(smem + off);
-    off += tile_smem_bytes<T>(a.tx, a.ty, a.tz);
-    int4 *sRh = reinterpret_cast<int4 *>(smem + off);
-    off += sizeof(int4) * kRaChunk;
-    Vec4<T> *sRu = reinterpret_cast<Vec4<T> *>(smem + off);
-    off += sizeof(Vec4<T>) * kRaChunk;
-    float *sred = reinterpret_cast<float *>(smem + off);
-    off += sizeof(float) * 80;
-    RaStage *sst = reinterpret_cast<RaStage *>(smem + off);
+    const GatherSmem<T> sm = carve<T, TX, TY, TZ>(smem, tsm ? sizeof(Vec4<T>) * (size_t)a.nseg : 0);
+    for (int k = threadIdx.x; k < 2 * kNVec; k += G::NT) sm.off[k] = (&a.off[0][0])[k];
 
-    for (int k = threadIdx.x; k < 2 * kNVec; k += blockDim.x) sOff[k] = (&a.off[0][0])[k];
-
-    const int SX = a.tx + 4, SY = a.ty + 4, SZ = a.tz + 4;
-    const int PLANE = SX * SY * SZ;
-    const int per_par = a.tx * a.ty * a.tz;
+    // this thread's site within a tile: parity-major, then (z, y, x)
+    const int q = threadIdx.x;
+    const int p = q / G::PER_PAR;
+    const int rr = q % G::PER_PAR;
+    const int lx = rr % TX, ly = (rr / TX) % TY, lz = rr / (TX * TY);
+    const int slot = p * G::PLANE + ((lz + 2) * G::SY + (ly + 2)) * G::SX + (lx + 2);
+    const float4 *po = sm.off + p * kNVec;
+    const int nseg1 = a.nseg - 1;
     unsigned st = 0;
     const int nra = a.sc->n_ra;
 
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        int tix = tile % a.ntx, tiy = (tile / a.ntx) % a.nty, tiz = tile / (a.ntx * a.nty);
-        int c0x = tix * a.tx, c0y = tiy * a.ty, c0z = tiz * a.tz;
+        const int tix = tile % a.ntx, tiy = (tile / a.ntx) % a.nty, tiz = tile / (a.ntx * a.nty);
+        const int c0x = tix * TX, c0y = tiy * TY, c0z = tiz * TZ;
         __syncthreads();
-        T U = stage_tile<T, false>(a, sU, c0x, c0y, c0z, sred);
+        const T U = stage_tile<T, TX, TY, TZ, false>(a, sm.u, c0x, c0y, c0z, sm.red);
         const bool has_ra = a.tile_flag[tile] != 0 && nra > 0;
-
-        // this thread's site
-        const int q = threadIdx.x;
-        const int p = q / per_par;
-        const int rr = q % per_par;
-        const int lx = rr % a.tx, ly = (rr / a.tx) % a.ty, lz = rr / (a.tx * a.ty);
-        const bool inbox = (q < 2 * per_par) && (c0x + lx < a.nx) && (c0y + ly < a.ny) && (c0z + lz < a.nz);
-        const int slot = (p * PLANE) + ((lz + 2) * SY + (ly + 2)) * SX + (lx + 2);
-        Vec4<T> ui = inbox ? sU[slot] : Vec4<T>{kVacant, kVacant, kVacant, 0};
+        const bool inbox = (c0x + lx < a.nx) && (c0y + ly < a.ny) && (c0z + lz < a.nz);
+        const Vec4<T> ui = sm.u[slot];
         const bool live = inbox && ui.x < (T)(0.5f * kVacant);
         Acc<T> rho;
         if (live) {
-            T ru = sqrt(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z);
-            T lim = a.rc_lat + ru + U;
-            T lim2 = lim * lim;
-            const float4 *po = sOff + p * kNVec;
-            for (int s = 0; s < a.sh.nshell; ++s) {
-                if ((T)a.sh.n2[s] > lim2) break;
-                const T thr = sizeof(T) == 4 ? (T)a.sh.thr[s] : (T)a.sh.thr_d[s];
-                const int kb = a.sh.begin[s], ke = a.sh.begin[s + 1];
-#pragma unroll 4
-                for (int k = kb; k < ke; ++k) {
-                    float4 o = po[k];
-                    Vec4<T> uj = sU[slot + __float_as_int(o.x)];
-                    T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
-                    T qq = (dx + (T)o.y) * dx + (dy + (T)o.z) * dy + (dz + (T)o.w) * dz;
-                    if (qq < thr) {
-                        int seg;
-                        T t, rinv;
-                        bool fh;
-                        shell_arg<T>(a.sh, s, qq, a.S, a.rfloor2, seg, t, rinv, fh);
-                        seg = clamp_seg<T>(seg, a.nseg, t);
-                        if (fh) st |= kStRfloor;
-                        Vec4<T> c = tabf[seg];
-                        rho.add(((c.x * t + c.y) * t + c.z) * t + c.w);
-                    }
-                }
-            }
+            const T lim = a.rc_lat + sqrt(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + U;
+            const T lim2 = lim * lim;
+            density_shells<T, 0>(a.sh, po, sm.u, slot, ui, lim2, a.S, nseg1, tabf, rho);
         }
         if (has_ra) {
             int pos = 0;
@@ -484,12 +614,12 @@ __global__ void __launch_bounds__(1024, 1) k_density(const __grid_constant__ Gat
             const int Lx = 2 * a.nx, Ly = 2 * a.ny, Lz = 2 * a.nz;
             while (true) {
                 __syncthreads();
-                int cnt = stage_runaways<T, false>(a, nra, pos, c0x, c0y, c0z, sRh, sRu, sst);
+                const int cnt = stage_runaways<T, TX, TY, TZ, false>(a, nra, pos, c0x, c0y, c0z, sm.rh, sm.ru, sm.st);
                 if (cnt == 0) break;
                 if (live) {
                     for (int j = 0; j < cnt; ++j) {
-                        int4 h = sRh[j];
-                        Vec4<T> uj = sRu[j];
+                        const int4 h = sm.rh[j];
+                        const Vec4<T> uj = sm.ru[j];
                         int nx_ = h.x - sx, ny_ = h.y - sy, nz_ = h.z - sz;
                         nx_ -= (nx_ > a.nx) ? Lx : 0;
                         nx_ += (nx_ < -a.nx) ? Lx : 0;
@@ -497,9 +627,9 @@ __global__ void __launch_bounds__(1024, 1) k_density(const __grid_constant__ Gat
                         ny_ += (ny_ < -a.ny) ? Ly : 0;
                         nz_ -= (nz_ > a.nz) ? Lz : 0;
                         nz_ += (nz_ < -a.nz) ? Lz : 0;
-                        T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
-                        T qq = (dx + (T)(2 * nx_)) * dx + (dy + (T)(2 * ny_)) * dy + (dz + (T)(2 * nz_)) * dz;
-                        T r2 = (T)(nx_ * nx_ + ny_ * ny_ + nz_ * nz_) + qq;
+                        const T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
+                        const T qq = (dx + (T)(2 * nx_)) * dx + (dy + (T)(2 * ny_)) * dy + (dz + (T)(2 * nz_)) * dz;
+                        const T r2 = (T)(nx_ * nx_ + ny_ * ny_ + nz_ * nz_) + qq;
                         if (r2 < a.rc2) {
                             int seg;
                             T t, rinv;
@@ -507,7 +637,7 @@ __global__ void __launch_bounds__(1024, 1) k_density(const __grid_constant__ Gat
                             direct_arg<T>(r2, a.S, a.rfloor2, seg, t, rinv, fh);
                             seg = clamp_seg<T>(seg, a.nseg, t);
                             if (fh) st |= kStRfloor;
-                            Vec4<T> c = tabf[seg];
+                            const Vec4<T> c = tabf[seg];
                             rho.add(((c.x * t + c.y) * t + c.z) * t + c.w);
                         }
                     }
@@ -516,10 +646,10 @@ __global__ void __launch_bounds__(1024, 1) k_density(const __grid_constant__ Gat
             }
         }
         if (live) {
-            long long sid = (((long long)(c0z + lz) * a.ny + (c0y + ly)) * a.nx + (c0x + lx)) * 2 + p;
-            T rh = rho.value();
+            const long long sid = (((long long)(c0z + lz) * a.ny + (c0y + ly)) * a.nx + (c0x + lx)) * 2 + p;
+            const T rh = rho.value();
             T dF;
-            T Fv = embed<T>(a.tab_F, a.nseg, a.Srho, a.rho_max, rh, dF, st);
+            const T Fv = embed<T>(a.tab_F, a.nseg, a.Srho, a.rho_max, rh, dF, st);
             a.fp_out[sid] = dF;
             if (ENERGY) {
                 a.rho_out[sid] = rh;
@@ -534,105 +664,56 @@ __global__ void __launch_bounds__(1024, 1) k_density(const __grid_constant__ Gat
 // force pass (Eq. eam_force_ij) + closing half kick of velocity Verlet
 // ---------------------------------------------------------------------------
 
-template <typename T, bool ENERGY>
-__global__ void __launch_bounds__(1024, 1) k_force(const __grid_constant__ GatherArgs<T> a)
+template <typename T, int TX, int TY, int TZ, bool ENERGY>
+__global__ void __launch_bounds__(2 * TX * TY * TZ, 1) k_force(const __grid_constant__ GatherArgs<T> a)
 {
+    using G = Tile<TX, TY, TZ>;
     extern __shared__ __align__(32) unsigned char smem[];
-    const Vec4<T> *tab0;
-    const Vec2<T> *tab1;
-    size_t off = 0;
-    if (a.tables_in_smem) {
+    const bool tsm = sizeof(T) == 4;
+    const Vec4<T> *tab0 = a.tab_d0;
+    const Vec2<T> *tab1 = a.tab_d1;
+    if (tsm) {
         Vec4<T> *t0 = reinterpret_cast<Vec4<T> *>(smem);
         Vec2<T> *t1 = reinterpret_cast<Vec2<T> *>(smem + sizeof(Vec4<T>) * (size_t)a.nseg);
-        for (int k = threadIdx.x; k < a.nseg; k += blockDim.x) {
+        for (int k = threadIdx.x; k < a.nseg; k += G::NT) {
             t0[k] = a.tab_d0[k];
             t1[k] = a.tab_d1[k];
         }
         tab0 = t0;
         tab1 = t1;
-        off = (sizeof(Vec4<T>) + sizeof(Vec2<T>)) * (size_t)a.nseg;
-    } else {
-        tab0 = a.tab_d0;
-        tab1 = a.tab_d1;
     }
-    off = (off + 255) & ~(size_t)255;
-    float4 *sOff = reinterpret_cast<float4 *>(smem + off);
-    off += sizeof(float4) * 2 * kNVec;
-    Vec4<T> *sU = reinterpret_cast<Vec4<T> *>(smem + off);
-    off += tile_smem_bytes<T>(a.tx, a.ty, a.tz);
-    int4 *sRh = reinterpret_cast<int4 *>(smem + off);
-    off += sizeof(int4) * kRaChunk;
-    Vec4<T> *sRu = reinterpret_cast<Vec4<T> *>(smem + off);
-    off += sizeof(Vec4<T>) * kRaChunk;
-    float *sred = reinterpret_cast<float *>(smem + off);
-    off += sizeof(float) * 80;
-    RaStage *sst = reinterpret_cast<RaStage *>(smem + off);
+    const GatherSmem<T> sm =
+        carve<T, TX, TY, TZ>(smem, tsm ? (sizeof(Vec4<T>) + sizeof(Vec2<T>)) * (size_t)a.nseg : 0);
+    for (int k = threadIdx.x; k < 2 * kNVec; k += G::NT) sm.off[k] = (&a.off[0][0])[k];
 
-    for (int k = threadIdx.x; k < 2 * kNVec; k += blockDim.x) sOff[k] = (&a.off[0][0])[k];
-
-    const int SX = a.tx + 4, SY = a.ty + 4, SZ = a.tz + 4;
-    const int PLANE = SX * SY * SZ;
-    const int per_par = a.tx * a.ty * a.tz;
+    const int q = threadIdx.x;
+    const int p = q / G::PER_PAR;
+    const int rr = q % G::PER_PAR;
+    const int lx = rr % TX, ly = (rr / TX) % TY, lz = rr / (TX * TY);
+    const int slot = p * G::PLANE + ((lz + 2) * G::SY + (ly + 2)) * G::SX + (lx + 2);
+    const float4 *po = sm.off + p * kNVec;
+    const int nseg1 = a.nseg - 1;
     unsigned st = 0;
     const int nra = a.sc->n_ra;
     const double hdt = 0.5 * a.sc->dt;
+    const T conv = (T)a.acc_conv;
     double vmax2 = 0.0;
 
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        int tix = tile % a.ntx, tiy = (tile / a.ntx) % a.nty, tiz = tile / (a.ntx * a.nty);
-        int c0x = tix * a.tx, c0y = tiy * a.ty, c0z = tiz * a.tz;
+        const int tix = tile % a.ntx, tiy = (tile / a.ntx) % a.nty, tiz = tile / (a.ntx * a.nty);
+        const int c0x = tix * TX, c0y = tiy * TY, c0z = tiz * TZ;
         __syncthreads();
-        T U = stage_tile<T, true>(a, sU, c0x, c0y, c0z, sred);
+        const T U = stage_tile<T, TX, TY, TZ, true>(a, sm.u, c0x, c0y, c0z, sm.red);
         const bool has_ra = a.tile_flag[tile] != 0 && nra > 0;
-
-        const int q = threadIdx.x;
-        const int p = q / per_par;
-        const int rr = q % per_par;
-        const int lx = rr % a.tx, ly = (rr / a.tx) % a.ty, lz = rr / (a.tx * a.ty);
-        const bool inbox = (q < 2 * per_par) && (c0x + lx < a.nx) && (c0y + ly < a.ny) && (c0z + lz < a.nz);
-        const int slot = (p * PLANE) + ((lz + 2) * SY + (ly + 2)) * SX + (lx + 2);
-        Vec4<T> ui = inbox ? sU[slot] : Vec4<T>{kVacant, kVacant, kVacant, 0};
+        const bool inbox = (c0x + lx < a.nx) && (c0y + ly < a.ny) && (c0z + lz < a.nz);
+        const Vec4<T> ui = sm.u[slot];
         const bool live = inbox && ui.x < (T)(0.5f * kVacant);
         Acc<T> fx, fy, fz;
         double ephi = 0.0;
         if (live) {
-            T ru = sqrt(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z);
-            T lim = a.rc_lat + ru + U;
-            T lim2 = lim * lim;
-            const float4 *po = sOff + p * kNVec;
-            for (int s = 0; s < a.sh.nshell; ++s) {
-                if ((T)a.sh.n2[s] > lim2) break;
-                const T thr = sizeof(T) == 4 ? (T)a.sh.thr[s] : (T)a.sh.thr_d[s];
-                const int kb = a.sh.begin[s], ke = a.sh.begin[s + 1];
-#pragma unroll 2
-                for (int k = kb; k < ke; ++k) {
-                    float4 o = po[k];
-                    Vec4<T> uj = sU[slot + __float_as_int(o.x)];
-                    T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
-                    T qq = (dx + (T)o.y) * dx + (dy + (T)o.z) * dy + (dz + (T)o.w) * dz;
-                    if (qq < thr) {
-                        int seg;
-                        T t, rinv;
-                        bool fh;
-                        shell_arg<T>(a.sh, s, qq, a.S, a.rfloor2, seg, t, rinv, fh);
-                        seg = clamp_seg<T>(seg, a.nseg, t);
-                        Vec4<T> c0 = tab0[seg];
-                        Vec2<T> c1 = tab1[seg];
-                        T dfr = (c0.x * t + c0.y) * t + c0.z;
-                        T dph = (c0.w * t + c1.x) * t + c1.y;
-                        T coef = (ui.w + uj.w) * dfr + dph;
-                        T sc = fh ? (T)0 : coef * rinv;
-                        if (fh) st |= kStRfloor;
-                        fx.add(sc * (dx + (T)0.5 * (T)o.y));
-                        fy.add(sc * (dy + (T)0.5 * (T)o.z));
-                        fz.add(sc * (dz + (T)0.5 * (T)o.w));
-                        if (ENERGY) {
-                            Vec4<T> cp = a.tab_phi[seg];
-                            ephi += 0.5 * (double)(((cp.x * t + cp.y) * t + cp.z) * t + cp.w);
-                        }
-                    }
-                }
-            }
+            const T lim = a.rc_lat + sqrt(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + U;
+            const T lim2 = lim * lim;
+            force_shells<T, 0, ENERGY>(a.sh, po, sm.u, slot, ui, lim2, a.S, nseg1, tab0, tab1, a.tab_phi, fx, fy, fz, ephi);
         }
         if (has_ra) {
             int pos = 0;
@@ -640,12 +721,12 @@ __global__ void __launch_bounds__(1024, 1) k_force(const __grid_constant__ Gathe
             const int Lx = 2 * a.nx, Ly = 2 * a.ny, Lz = 2 * a.nz;
             while (true) {
                 __syncthreads();
-                int cnt = stage_runaways<T, true>(a, nra, pos, c0x, c0y, c0z, sRh, sRu, sst);
+                const int cnt = stage_runaways<T, TX, TY, TZ, true>(a, nra, pos, c0x, c0y, c0z, sm.rh, sm.ru, sm.st);
                 if (cnt == 0) break;
                 if (live) {
                     for (int j = 0; j < cnt; ++j) {
-                        int4 h = sRh[j];
-                        Vec4<T> uj = sRu[j];
+                        const int4 h = sm.rh[j];
+                        const Vec4<T> uj = sm.ru[j];
                         int nx_ = h.x - sx, ny_ = h.y - sy, nz_ = h.z - sz;
                         nx_ -= (nx_ > a.nx) ? Lx : 0;
                         nx_ += (nx_ < -a.nx) ? Lx : 0;
@@ -653,27 +734,27 @@ __global__ void __launch_bounds__(1024, 1) k_force(const __grid_constant__ Gathe
                         ny_ += (ny_ < -a.ny) ? Ly : 0;
                         nz_ -= (nz_ > a.nz) ? Lz : 0;
                         nz_ += (nz_ < -a.nz) ? Lz : 0;
-                        T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
-                        T qq = (dx + (T)(2 * nx_)) * dx + (dy + (T)(2 * ny_)) * dy + (dz + (T)(2 * nz_)) * dz;
-                        T r2 = (T)(nx_ * nx_ + ny_ * ny_ + nz_ * nz_) + qq;
+                        const T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
+                        const T qq = (dx + (T)(2 * nx_)) * dx + (dy + (T)(2 * ny_)) * dy + (dz + (T)(2 * nz_)) * dz;
+                        const T r2 = (T)(nx_ * nx_ + ny_ * ny_ + nz_ * nz_) + qq;
                         if (r2 < a.rc2) {
                             int seg;
                             T t, rinv;
                             bool fh;
                             direct_arg<T>(r2, a.S, a.rfloor2, seg, t, rinv, fh);
                             seg = clamp_seg<T>(seg, a.nseg, t);
-                            Vec4<T> c0 = tab0[seg];
-                            Vec2<T> c1 = tab1[seg];
-                            T dfr = (c0.x * t + c0.y) * t + c0.z;
-                            T dph = (c0.w * t + c1.x) * t + c1.y;
-                            T coef = (ui.w + uj.w) * dfr + dph;
-                            T sc = fh ? (T)0 : coef * rinv;
+                            const Vec4<T> c0 = tab0[seg];
+                            const Vec2<T> c1 = tab1[seg];
+                            const T dfr = (c0.x * t + c0.y) * t + c0.z;
+                            const T dph = (c0.w * t + c1.x) * t + c1.y;
+                            const T coef = (ui.w + uj.w) * dfr + dph;
+                            const T sc_ = fh ? (T)0 : coef * rinv;
                             if (fh) st |= kStRfloor;
-                            fx.add(sc * (dx + (T)nx_));
-                            fy.add(sc * (dy + (T)ny_));
-                            fz.add(sc * (dz + (T)nz_));
+                            fx.add(sc_ * (dx + (T)nx_));
+                            fy.add(sc_ * (dy + (T)ny_));
+                            fz.add(sc_ * (dz + (T)nz_));
                             if (ENERGY) {
-                                Vec4<T> cp = a.tab_phi[seg];
+                                const Vec4<T> cp = a.tab_phi[seg];
                                 ephi += 0.5 * (double)(((cp.x * t + cp.y) * t + cp.z) * t + cp.w);
                             }
                         }
@@ -683,22 +764,29 @@ __global__ void __launch_bounds__(1024, 1) k_force(const __grid_constant__ Gathe
             }
         }
         if (live) {
-            long long sid = (((long long)(c0z + lz) * a.ny + (c0y + ly)) * a.nx + (c0x + lx)) * 2 + p;
-            double conv = a.acc_conv;
-            double gx = (double)fx.value() * conv, gy = (double)fy.value() * conv, gz = (double)fz.value() * conv;
-            a.ax[sid] = (T)gx;
-            a.ay[sid] = (T)gy;
-            a.az[sid] = (T)gz;
+            const long long sid = (((long long)(c0z + lz) * a.ny + (c0y + ly)) * a.nx + (c0x + lx)) * 2 + p;
+            T gx, gy, gz;
+            if constexpr (sizeof(T) == 4) {
+                gx = fx.value() * conv;
+                gy = fy.value() * conv;
+                gz = fz.value() * conv;
+            } else {
+                gx = fx.value() * a.acc_conv;
+                gy = fy.value() * a.acc_conv;
+                gz = fz.value() * a.acc_conv;
+            }
+            a.ax[sid] = gx;
+            a.ay[sid] = gy;
+            a.az[sid] = gz;
             if (!isfinite(gx) || !isfinite(gy) || !isfinite(gz)) st |= kStNonfinite;
             if (a.kick) {
-                // velocities advance with the stored (precision-T) acceleration
-                double vx = a.vx[sid] + hdt * (double)(T)gx;
-                double vy = a.vy[sid] + hdt * (double)(T)gy;
-                double vz = a.vz[sid] + hdt * (double)(T)gz;
+                const double vx = fma(hdt, (double)gx, a.vx[sid]);
+                const double vy = fma(hdt, (double)gy, a.vy[sid]);
+                const double vz = fma(hdt, (double)gz, a.vz[sid]);
                 a.vx[sid] = vx;
                 a.vy[sid] = vy;
                 a.vz[sid] = vz;
-                double v2 = vx * vx + vy * vy + vz * vz;
+                const double v2 = vx * vx + vy * vy + vz * vz;
                 vmax2 = v2 > vmax2 ? v2 : vmax2;
             }
             if (ENERGY) a.e_out[sid] += ephi;
@@ -710,14 +798,13 @@ __global__ void __launch_bounds__(1024, 1) k_force(const __grid_constant__ Gathe
         double m = vmax2;
         for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
         __syncthreads();
-        double *sm = reinterpret_cast<double *>(sred);
-        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+        double *smd = reinterpret_cast<double *>(sm.red);
+        if ((threadIdx.x & 31) == 0) smd[threadIdx.x >> 5] = m;
         __syncthreads();
         if (threadIdx.x == 0) {
             double w = 0.0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) w = fmax(w, sm[k]);
-            w = sqrt(w);
-            atomicMax(&a.sc->vacc_bits, (unsigned long long)__double_as_longlong(w));
+            for (int k = 0; k < G::NT / 32; ++k) w = fmax(w, smd[k]);
+            atomicMax(&a.sc->vacc_bits, (unsigned long long)__double_as_longlong(sqrt(w)));
         }
     }
 }

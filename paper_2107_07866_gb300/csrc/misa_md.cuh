@@ -143,18 +143,24 @@ template <typename T>
 __global__ void k_kick_drift(MdArgs<T> m)
 {
     DevScalars *sc = m.sc;
-    const double dt = sc->dt, hdt = 0.5 * dt;
+    const double dt = sc->dt, hdt = 0.5 * dt, dtl = dt * m.inv_half;
     const int base = sc->n_ra_old;
+    const float skin2f = (float)m.skin2;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < m.ns; s += (long long)gridDim.x * blockDim.x) {
         int id = m.sid[s];
         if (id < 0) continue;
-        double vx = m.vx[s] + hdt * (double)m.ax[s];
-        double vy = m.vy[s] + hdt * (double)m.ay[s];
-        double vz = m.vz[s] + hdt * (double)m.az[s];
-        double ux = m.ux[s] + dt * vx * m.inv_half;
-        double uy = m.uy[s] + dt * vy * m.inv_half;
-        double uz = m.uz[s] + dt * vz * m.inv_half;
-        if (ux * ux + uy * uy + uz * uz > m.skin2) {
+        // FP64 integration; the skin test (a storage decision) in FP32
+        const double vx = fma(hdt, (double)m.ax[s], m.vx[s]);
+        const double vy = fma(hdt, (double)m.ay[s], m.vy[s]);
+        const double vz = fma(hdt, (double)m.az[s], m.vz[s]);
+        const double ux = fma(dtl, vx, m.ux[s]);
+        const double uy = fma(dtl, vy, m.uy[s]);
+        const double uz = fma(dtl, vz, m.uz[s]);
+        const float fx = (float)ux, fy = (float)uy, fz = (float)uz;
+        bool out;
+        if constexpr (sizeof(T) == 4) out = fx * fx + fy * fy + fz * fz > skin2f;
+        else out = ux * ux + uy * uy + uz * uz > m.skin2;
+        if (out) {
             int slot = atomicAdd(&sc->n_new, 1);
             int j = base + slot;
             if (j < m.cap) {
@@ -179,8 +185,8 @@ __global__ void k_kick_drift(MdArgs<T> m)
         }
         m.vx[s] = vx; m.vy[s] = vy; m.vz[s] = vz;
         m.ux[s] = ux; m.uy[s] = uy; m.uz[s] = uz;
-        if ((void *)m.sx != (void *)m.ux) {
-            m.sx[s] = (T)ux; m.sy[s] = (T)uy; m.sz[s] = (T)uz;
+        if constexpr (sizeof(T) == 4) {
+            m.sx[s] = fx; m.sy[s] = fy; m.sz[s] = fz;
         }
     }
 }
