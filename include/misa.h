@@ -122,6 +122,22 @@ void misa_default_params(misa_params *p);
  * knot arrays are copied.  On success *out owns all device memory. */
 int misa_create(const misa_params *p, void *stream, misa_sim **out);
 
+/* Batch of nrep independent replicas (Sec. 1 feature list: batch execution
+ * of simulations) in one handle: replica r is a perfect crystal of
+ * dims[3r] x dims[3r+1] x dims[3r+2] cells (each >= 6); p's own nx, ny, nz are
+ * ignored.  All replicas share the potential, a0, skin, precision and tile
+ * shape, and every step kernel serves all of them in one launch (one
+ * persistent tile launch per pass); each replica keeps its own adaptive
+ * timestep, time and run-away list.  Atom ids are concatenated in replica
+ * order: replica r owns ids [atom_base(r), atom_base(r) + 2 n_x n_y n_z).
+ * Every per-atom call below takes all atoms of the batch.  misa_create is
+ * misa_create_batch with one replica. */
+int misa_create_batch(const misa_params *p, int32_t nrep, const int32_t *dims, void *stream, misa_sim **out);
+
+/* Replica count, and box / first atom id / atom count of replica r. */
+int misa_replica_count(const misa_sim *s);
+int misa_replica_info(const misa_sim *s, int32_t r, int32_t dims[3], int64_t *atom_base, int64_t *natoms);
+
 /* Frees the handle and its device memory (after synchronising its stream). */
 void misa_destroy(misa_sim *s);
 
@@ -144,6 +160,9 @@ int misa_set_velocities(misa_sim *s, const double *v, int64_t n);
  * (nx/2, ny/2, nz/2), the box centre. */
 int misa_insert_pka(misa_sim *s, int64_t atom, double energy_eV, const double dir[3]);
 
+/* PKA of replica r: the atom at the centre of replica r's box. */
+int misa_insert_pka_replica(misa_sim *s, int32_t r, double energy_eV, const double dir[3]);
+
 /* Advances n steps of NVE velocity Verlet: kick, drift (array atoms leaving
  * their skin move to the run-away list), hash update every reassign_period
  * steps (Alg. 2), EAM density / embedding derivative / force passes
@@ -151,10 +170,19 @@ int misa_insert_pka(misa_sim *s, int64_t atom, double energy_eV, const double di
  * only; never synchronises. */
 int misa_step(misa_sim *s, int n);
 
+/* misa_step captures one step as a CUDA graph on an internal stream (joined
+ * to the handle's stream by events) and replays it; enable = 0 launches the
+ * kernels one by one instead.  Timing (misa_timing_enable) always launches
+ * directly. */
+int misa_set_graphs(misa_sim *s, int enable);
+
 /* Potential energy (sum of E_i, Eq. eam_base) and kinetic energy (eV) of
  * the current state; per_atom (natoms, may be NULL) receives E_i.
  * Synchronises. */
 int misa_get_energies(misa_sim *s, double *pe, double *ke, double *per_atom);
+
+/* Potential and kinetic energy of every replica (arrays of nrep). */
+int misa_replica_energies(misa_sim *s, double *pe, double *ke);
 
 /* Per-atom host outputs (3 natoms doubles, or natoms for the density),
  * indexed by atom id; n must be >= natoms.  Positions are wrapped into the
@@ -178,8 +206,11 @@ int misa_get_site_map(misa_sim *s, int64_t *site_atom, int64_t *runaway_ids, int
 int misa_timing_enable(misa_sim *s, int enable);
 int misa_timing_get(misa_sim *s, double ms[MISA_NPHASE], int64_t *steps);
 
-/* Counters and status bits.  Synchronises. */
+/* Counters and status bits of the batch (run-aways summed over replicas,
+ * step / time / dt of replica 0; dt is 0 for batches), and of one replica.
+ * The status bits are shared by the batch.  Synchronise. */
 int misa_stats_get(misa_sim *s, misa_stats *out);
+int misa_replica_stats(misa_sim *s, int32_t r, misa_stats *out);
 int misa_clear_status(misa_sim *s);
 
 /* Checkpoint / restart of the full dynamic state (positions, velocities,
@@ -190,6 +221,11 @@ int misa_load(misa_sim *s, const char *path);
 /* Number of built gather tile shapes, and the shape of each (cells). */
 int misa_tile_count(void);
 int misa_tile_shape(int index, int *tx, int *ty, int *tz);
+
+/* Tile shape in use (1-based index; chosen by the autotuner when
+ * misa_params.tile is 0: each shape's density + force passes are timed on
+ * the initial crystal and the fastest kept). */
+int misa_tile_current(const misa_sim *s);
 
 /* Allocation-free force evaluation (the paper has no counterpart; it exists
  * for callers that must not allocate device memory).

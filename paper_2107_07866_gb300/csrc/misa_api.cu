@@ -1,8 +1,9 @@
 // misa_api.cu -- host runtime and C ABI (include/misa.h) of the GB300 EAM
 // lattice-list MD library.  Owns device memory, builds the neighbour offset
-// index for the chosen tile shape (Sec. 3) and launches the step kernels on
-// the handle's stream.  No host fallback: every step of the path runs in the
-// kernels of misa_kernels.cuh / misa_md.cuh.
+// index for the chosen tile shape (Sec. 3), the replica table of a batch, and
+// launches the step kernels on the handle's stream (directly, or as one
+// captured CUDA graph per step).  No host fallback: every step of the path
+// runs in the kernels of misa_kernels.cuh / misa_md.cuh.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -33,19 +34,25 @@ std::string g_create_error;
 struct misa_sim {
     misa_params p{};
     std::vector<double> fk, pk, Fk;
-    cudaStream_t st = nullptr;
-    int nx = 0, ny = 0, nz = 0;
-    long long ns = 0;
+    cudaStream_t st = nullptr;   // caller's stream
+    cudaStream_t gst = nullptr;  // internal stream the step graph is captured on
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int nrep = 1;
+    std::vector<int> dims;       // 3 per replica
+    std::vector<RepDesc> reps;   // host copy of the replica table
+    long long ns = 0;            // sites (= atoms) of all replicas
     int prec = MISA_FP32_FORCE;
-    int cap = 0;
+    int cap = 0;                 // run-away capacity per replica
     int tile = 0;
     int nsm = 0;
     std::string err;
     std::vector<std::pair<void *, size_t>> allocs;
     // device buffers
+    RepDesc *reps_d = nullptr;
+    int *tile_rep = nullptr;
     int *sid = nullptr, *claim = nullptr, *tile_flag = nullptr;
     double *u[3] = {}, *v[3] = {};
-    void *s[3] = {};   // precision-T shadow of u (FP32 path) or alias of u
+    void *s[3] = {};  // precision-T shadow of u (FP32 path) or alias of u
     void *a[3] = {};
     void *fp = nullptr, *rho = nullptr;
     double *esite = nullptr;
@@ -64,15 +71,18 @@ struct misa_sim {
     double *out_buf = nullptr;  // 3 natoms scratch for read-out / set_state
     int *aux_int = nullptr;     // natoms scratch
     double *aux_dbl = nullptr;  // 3 natoms scratch
-    int ntx = 0, nty = 0, ntz = 0, ntiles = 0;
+    long long ntile_cap = 0;    // tile_flag / tile_rep capacity (smallest tile shape)
+    int ntiles = 0;
     size_t smem_density = 0, smem_force = 0;
     long long launches = 0;
     // phase timing
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
-    std::vector<cudaEvent_t> cur;  // events of the step being launched
-    long long timed_steps = 0;
+    // captured step graph
+    bool use_graph = true;
+    cudaGraphExec_t graph = nullptr;
+    long long graph_launches = 0;  // kernels inside one replay
 };
 
 namespace {
@@ -119,12 +129,21 @@ void mark(misa_sim *s)
     cudaEventRecord(e, s->st);
 }
 
+// launch geometry: 2-D grids, x = blocks per replica, y = replica
+dim3 site_grid(const misa_sim *s)
+{
+    int gx = (s->nsm * 8 + s->nrep - 1) / s->nrep;
+    return dim3(gx < 4 ? 4 : gx, s->nrep);
+}
+dim3 list_grid(const misa_sim *s) { return dim3(8, s->nrep); }
+int rep_blocks(const misa_sim *s) { return (s->nrep + 127) / 128; }
+
 template <typename T>
 MdArgs<T> md_args(misa_sim *s)
 {
     MdArgs<T> m{};
-    m.nx = s->nx; m.ny = s->ny; m.nz = s->nz;
-    m.ns = s->ns;
+    m.reps = s->reps_d;
+    m.nrep = s->nrep;
     m.sid = s->sid;
     m.ux = s->u[0]; m.uy = s->u[1]; m.uz = s->u[2];
     m.sx = (T *)s->s[0]; m.sy = (T *)s->s[1]; m.sz = (T *)s->s[2];
@@ -133,7 +152,6 @@ MdArgs<T> md_args(misa_sim *s)
     m.fp = (T *)s->fp; m.rho = (T *)s->rho;
     m.esite = s->esite;
     m.claim = s->claim;
-    m.cap = s->cap;
     m.ra_home = s->ra_home; m.ra_id = s->ra_id;
     m.ra_ux = s->ra_u[0]; m.ra_uy = s->ra_u[1]; m.ra_uz = s->ra_u[2];
     m.ra_sx = (T *)s->ra_s[0]; m.ra_sy = (T *)s->ra_s[1]; m.ra_sz = (T *)s->ra_s[2];
@@ -150,7 +168,6 @@ MdArgs<T> md_args(misa_sim *s)
     m.tile_flag = s->tile_flag;
     const TileShape &ts = kTiles[s->tile];
     m.tx = ts.tx; m.ty = ts.ty; m.tz = ts.tz;
-    m.ntx = s->ntx; m.nty = s->nty; m.ntz = s->ntz;
     m.sc = s->sc;
     m.half = 0.5 * s->p.a0;
     m.inv_half = 2.0 / s->p.a0;
@@ -164,13 +181,30 @@ MdArgs<T> md_args(misa_sim *s)
     return m;
 }
 
+// First spline segment an array-array pair can reach: both atoms lie within
+// the skin of their sites, so r >= d_nn - 2 skin (d_nn = sqrt(3)/2 a0); two
+// segments of guard for rounding.  The FP32 gathers keep only the table
+// segments from here on in shared memory.
+int seg_lo_of(const misa_sim *s)
+{
+    const int n = s->p.n_knots;
+    const double hr = s->p.rc / (n - 1);
+    const double rlo = 0.5 * std::sqrt(3.0) * s->p.a0 - 2.0 * s->p.skin;
+    int k = (int)std::floor(rlo / hr) - 2;
+    if (k < 0) k = 0;
+    if (k > n - 2) k = n - 2;
+    return k;
+}
+
 template <typename T>
 void fill_gather(misa_sim *s, GatherArgs<T> &g)
 {
     std::memset(&g, 0, sizeof(g));
     const TileShape &ts = kTiles[s->tile];
-    g.nx = s->nx; g.ny = s->ny; g.nz = s->nz;
-    g.ntx = s->ntx; g.nty = s->nty; g.ntz = s->ntz; g.ntiles = s->ntiles;
+    g.reps = s->reps_d;
+    g.tile_rep = s->tile_rep;
+    g.ntiles = s->ntiles;
+    g.nrep = s->nrep;
     g.ux = (const T *)s->s[0]; g.uy = (const T *)s->s[1]; g.uz = (const T *)s->s[2];
     g.fp = (const T *)s->fp;
     g.fp_out = (T *)s->fp;
@@ -185,6 +219,7 @@ void fill_gather(misa_sim *s, GatherArgs<T> &g)
     g.tab_d1 = (const Vec2<T> *)s->tab_d1;
     const int n = s->p.n_knots;
     g.nseg = n - 1;
+    g.seg_lo = seg_lo_of(s);
     const double half = 0.5 * s->p.a0;
     const double hr = s->p.rc / (n - 1);
     const double hrho = s->p.rho_max / (n - 1);
@@ -238,15 +273,17 @@ template <typename T>
 size_t smem_density_bytes(misa_sim *s)
 {
     const TileShape &ts = kTiles[s->tile];
-    return gather_smem_bytes<T>(sizeof(T) == 4 ? sizeof(Vec4<T>) * (size_t)(s->p.n_knots - 1) : 0, ts.tx, ts.ty, ts.tz);
+    const size_t nwin = (size_t)(s->p.n_knots - 1 - seg_lo_of(s));
+    return gather_smem_bytes<T>(sizeof(T) == 4 ? sizeof(Vec4<T>) * nwin : 0, ts.tx, ts.ty, ts.tz, tile_buffers<T>());
 }
 
 template <typename T>
 size_t smem_force_bytes(misa_sim *s)
 {
     const TileShape &ts = kTiles[s->tile];
-    return gather_smem_bytes<T>(sizeof(T) == 4 ? (sizeof(Vec4<T>) + sizeof(Vec2<T>)) * (size_t)(s->p.n_knots - 1) : 0,
-                                ts.tx, ts.ty, ts.tz);
+    const size_t nwin = (size_t)(s->p.n_knots - 1 - seg_lo_of(s));
+    return gather_smem_bytes<T>(sizeof(T) == 4 ? (sizeof(Vec4<T>) + sizeof(Vec2<T>)) * nwin : 0, ts.tx, ts.ty, ts.tz,
+                                (kForceBuffers == 2 && tile_buffers<T>() == 2) ? 2 : 1);
 }
 
 // one instantiation of the tile kernels per tile shape
@@ -283,14 +320,30 @@ struct TileKernels {
     default: TileKernels<T, 16, 8, 4>::CALL; break;           \
     }
 
+// Sets the tile shape: tile counts of every replica, the global tile ->
+// replica map, kernel attributes.  Drops a captured step graph.
 template <typename T>
-int configure(misa_sim *s)
+int configure(misa_sim *s, int tile)
 {
-    const TileShape &ts = kTiles[s->tile];
-    s->ntx = (s->nx + ts.tx - 1) / ts.tx;
-    s->nty = (s->ny + ts.ty - 1) / ts.ty;
-    s->ntz = (s->nz + ts.tz - 1) / ts.tz;
-    s->ntiles = s->ntx * s->nty * s->ntz;
+    s->tile = tile;
+    const TileShape &ts = kTiles[tile];
+    int base = 0;
+    std::vector<int> map;
+    for (int r = 0; r < s->nrep; ++r) {
+        RepDesc &rd = s->reps[r];
+        rd.ntx = (rd.nx + ts.tx - 1) / ts.tx;
+        rd.nty = (rd.ny + ts.ty - 1) / ts.ty;
+        rd.ntz = (rd.nz + ts.tz - 1) / ts.tz;
+        rd.ntiles = rd.ntx * rd.nty * rd.ntz;
+        rd.tile_base = base;
+        base += rd.ntiles;
+        map.insert(map.end(), rd.ntiles, r);
+    }
+    s->ntiles = base;
+    if ((long long)base > s->ntile_cap) return fail(s, MISA_EINVAL, "tile map capacity");
+    CK(cudaMemcpyAsync(s->reps_d, s->reps.data(), sizeof(RepDesc) * s->nrep, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->tile_rep, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));  // map is a host temporary
     s->smem_density = smem_density_bytes<T>(s);
     s->smem_force = smem_force_bytes<T>(s);
     int arc = MISA_OK;
@@ -298,16 +351,9 @@ int configure(misa_sim *s)
     if (arc) return fail(s, arc, s->err.empty() ? "tile kernel attributes" : s->err);
     CK(cudaFuncSetAttribute(k_ra_sort<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)(sizeof(unsigned long long) * kSortMax)));
-    if (s->tile_flag == nullptr) {
-        // sized for the smallest tile shape so that re-tuning never reallocates
-        long long maxt = 0;
-        for (int k = 0; k < kNTiles; ++k) {
-            long long nt = (long long)((s->nx + kTiles[k].tx - 1) / kTiles[k].tx) * ((s->ny + kTiles[k].ty - 1) / kTiles[k].ty) *
-                           ((s->nz + kTiles[k].tz - 1) / kTiles[k].tz);
-            maxt = nt > maxt ? nt : maxt;
-        }
-        s->tile_flag = (int *)dalloc(s, sizeof(int) * (size_t)maxt);
-        if (!s->tile_flag) return fail(s, MISA_EOOM, "tile flags");
+    if (s->graph) {
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
     }
     return MISA_OK;
 }
@@ -321,7 +367,7 @@ int launch_forces(misa_sim *s, int kick, bool energy, bool step_marks = false)
     g.kick = kick;
     const int grid = s->ntiles < s->nsm ? s->ntiles : s->nsm;
     CK(cudaMemsetAsync(s->tile_flag, 0, sizeof(int) * (size_t)s->ntiles, s->st));
-    k_mark_tiles<T><<<64, 256, 0, s->st>>>(m);
+    k_mark_tiles<T><<<list_grid(s), 256, 0, s->st>>>(m);
     RaGatherArgs<T> ra;
     std::memset(&ra, 0, sizeof(ra));
     ra.g = g;
@@ -334,38 +380,71 @@ int launch_forces(misa_sim *s, int kick, bool energy, bool step_marks = false)
     if (step_marks) mark(s);  // end of the list phase
     MISA_TILE_DISPATCH(T, s->tile, density(s, g, grid, energy));
     if (step_marks) mark(s);
-    k_ra_gather<T, 0><<<128, 256, 0, s->st>>>(ra);
+    k_ra_gather<T, 0><<<dim3(16, s->nrep), 256, 0, s->st>>>(ra);
     if (step_marks) mark(s);
     MISA_TILE_DISPATCH(T, s->tile, force(s, g, grid, energy));
     if (step_marks) mark(s);
-    k_ra_gather<T, 1><<<128, 256, 0, s->st>>>(ra);
+    k_ra_gather<T, 1><<<dim3(16, s->nrep), 256, 0, s->st>>>(ra);
     if (step_marks) mark(s);
     s->launches += 5;
     CK(cudaGetLastError());
     return MISA_OK;
 }
 
+// the launches of one MD step on s->st
 template <typename T>
 int launch_step(misa_sim *s)
 {
     MdArgs<T> m = md_args<T>(s);
-    const int gs = s->nsm * 8;
     mark(s);
-    k_begin_step<T><<<1, 1, 0, s->st>>>(m);
-    k_ra_kick_drift<T><<<64, 256, 0, s->st>>>(m);
-    k_kick_drift<T><<<gs, 256, 0, s->st>>>(m);
+    k_begin_step<T><<<rep_blocks(s), 128, 0, s->st>>>(m);
+    k_ra_kick_drift<T><<<list_grid(s), 256, 0, s->st>>>(m);
+    k_kick_drift<T><<<site_grid(s), 256, 0, s->st>>>(m);
     mark(s);
-    k_reassign_claim<T><<<64, 256, 0, s->st>>>(m, 0);
-    k_reassign_promote<T><<<64, 256, 0, s->st>>>(m, 0);
-    k_ra_sort<T><<<1, 1024, sizeof(unsigned long long) * kSortMax, s->st>>>(m);
+    k_reassign_claim<T><<<list_grid(s), 256, 0, s->st>>>(m, 0);
+    k_reassign_promote<T><<<list_grid(s), 256, 0, s->st>>>(m, 0);
+    k_ra_sort<T><<<s->nrep, 1024, sizeof(unsigned long long) * kSortMax, s->st>>>(m);
     s->launches += 6;
     int rc = launch_forces<T>(s, 1, false, true);
     if (rc) return rc;
-    k_end_step<T><<<1, 1, 0, s->st>>>(m);
+    k_end_step<T><<<rep_blocks(s), 128, 0, s->st>>>(m);
     mark(s);
     s->launches += 1;
-    if (s->timing) s->timed_steps += 1;
     CK(cudaGetLastError());
+    return MISA_OK;
+}
+
+// One step captured as a CUDA graph on an internal stream, replayed n times;
+// the caller's stream is joined by events.
+template <typename T>
+int step_graph(misa_sim *s, int n)
+{
+    if (!s->graph) {
+        cudaStream_t user = s->st;
+        s->st = s->gst;
+        long long l0 = s->launches;
+        CK(cudaStreamBeginCapture(s->gst, cudaStreamCaptureModeThreadLocal));
+        int rc = launch_step<T>(s);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s->gst, &g);
+        s->st = user;
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(s, MISA_ECUDA, std::string("step capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&s->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(s, MISA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        s->graph_launches = s->launches - l0;
+        s->launches = l0;
+    }
+    CK(cudaEventRecord(s->ev_in, s->st));
+    CK(cudaStreamWaitEvent(s->gst, s->ev_in, 0));
+    for (int k = 0; k < n; ++k) CK(cudaGraphLaunch(s->graph, s->gst));
+    CK(cudaEventRecord(s->ev_out, s->gst));
+    CK(cudaStreamWaitEvent(s->st, s->ev_out, 0));
+    s->launches += s->graph_launches * n;
     return MISA_OK;
 }
 
@@ -379,18 +458,57 @@ int refresh(misa_sim *s, bool forces)
         int rc = launch_forces<T>(s, 0, false);
         if (rc) return rc;
     }
-    CK(cudaMemsetAsync(&s->sc->vmax_bits, 0, sizeof(unsigned long long), s->st));
-    k_vmax<T><<<s->nsm * 4, 256, 0, s->st>>>(m);
+    for (int r = 0; r < s->nrep; ++r) CK(cudaMemsetAsync(&s->sc[r].vmax_bits, 0, sizeof(unsigned long long), s->st));
+    k_vmax<T><<<site_grid(s), 256, 0, s->st>>>(m);
     CK(cudaGetLastError());
     return MISA_OK;
+}
+
+// Tile autotuner: times the density + force passes of the current state for
+// every tile shape and keeps the fastest.
+template <typename T>
+int autotune(misa_sim *s)
+{
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_k = 0;
+    for (int k = 0; k < kNTiles; ++k) {
+        int rc = configure<T>(s, k);
+        if (rc) return rc;
+        rc = launch_forces<T>(s, 0, false);  // warm-up
+        if (rc) return rc;
+        CK(cudaEventRecord(e0, s->st));
+        for (int q = 0; q < 3; ++q) {
+            rc = launch_forces<T>(s, 0, false);
+            if (rc) return rc;
+        }
+        CK(cudaEventRecord(e1, s->st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return configure<T>(s, best_k);
 }
 
 template <typename T>
 int create_impl(misa_sim *s)
 {
     const long long ns = s->ns;
+    const size_t capt = (size_t)s->cap * s->nrep;
     const int n = s->p.n_knots;
     size_t Tb = sizeof(T);
+    s->reps_d = (RepDesc *)dalloc(s, sizeof(RepDesc) * s->nrep);
+    s->sc = (DevScalars *)dalloc(s, sizeof(DevScalars) * s->nrep);
+    s->tile_rep = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap);
+    s->tile_flag = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap);
     s->sid = (int *)dalloc(s, sizeof(int) * ns);
     s->claim = (int *)dalloc(s, sizeof(int) * ns);
     for (int d = 0; d < 3; ++d) {
@@ -398,14 +516,14 @@ int create_impl(misa_sim *s)
         s->v[d] = (double *)dalloc(s, sizeof(double) * ns);
         s->a[d] = dalloc(s, Tb * ns);
         s->s[d] = sizeof(T) == 8 ? (void *)s->u[d] : dalloc(s, Tb * ns);
-        s->ra_u[d] = (double *)dalloc(s, sizeof(double) * s->cap);
-        s->ra_v[d] = (double *)dalloc(s, sizeof(double) * s->cap);
-        s->ra_s[d] = dalloc(s, Tb * s->cap);
-        s->ra_a[d] = dalloc(s, Tb * s->cap);
-        s->t_u[d] = (double *)dalloc(s, sizeof(double) * s->cap);
-        s->t_v[d] = (double *)dalloc(s, sizeof(double) * s->cap);
-        s->t_s[d] = dalloc(s, Tb * s->cap);
-        s->t_a[d] = dalloc(s, Tb * s->cap);
+        s->ra_u[d] = (double *)dalloc(s, sizeof(double) * capt);
+        s->ra_v[d] = (double *)dalloc(s, sizeof(double) * capt);
+        s->ra_s[d] = dalloc(s, Tb * capt);
+        s->ra_a[d] = dalloc(s, Tb * capt);
+        s->t_u[d] = (double *)dalloc(s, sizeof(double) * capt);
+        s->t_v[d] = (double *)dalloc(s, sizeof(double) * capt);
+        s->t_s[d] = dalloc(s, Tb * capt);
+        s->t_a[d] = dalloc(s, Tb * capt);
         if (!s->u[d] || !s->v[d] || !s->a[d] || !s->s[d] || !s->ra_u[d] || !s->ra_v[d] || !s->ra_s[d] || !s->ra_a[d] ||
             !s->t_u[d] || !s->t_v[d] || !s->t_s[d] || !s->t_a[d])
             return fail(s, MISA_EOOM, "device allocation failed");
@@ -413,28 +531,28 @@ int create_impl(misa_sim *s)
     s->fp = dalloc(s, Tb * ns);
     s->rho = dalloc(s, Tb * ns);
     s->esite = (double *)dalloc(s, sizeof(double) * ns);
-    s->ra_home = (int *)dalloc(s, sizeof(int) * s->cap);
-    s->ra_id = (int *)dalloc(s, sizeof(int) * s->cap);
-    s->t_home = (int *)dalloc(s, sizeof(int) * s->cap);
-    s->t_id = (int *)dalloc(s, sizeof(int) * s->cap);
-    s->ra_fp = dalloc(s, Tb * s->cap);
-    s->ra_rho = dalloc(s, Tb * s->cap);
-    s->ra_e = (double *)dalloc(s, sizeof(double) * s->cap);
+    s->ra_home = (int *)dalloc(s, sizeof(int) * capt);
+    s->ra_id = (int *)dalloc(s, sizeof(int) * capt);
+    s->t_home = (int *)dalloc(s, sizeof(int) * capt);
+    s->t_id = (int *)dalloc(s, sizeof(int) * capt);
+    s->ra_fp = dalloc(s, Tb * capt);
+    s->ra_rho = dalloc(s, Tb * capt);
+    s->ra_e = (double *)dalloc(s, sizeof(double) * capt);
     s->knots = (double *)dalloc(s, sizeof(double) * 3 * n);
     s->tab_f = dalloc(s, sizeof(Vec4<T>) * n);
     s->tab_phi = dalloc(s, sizeof(Vec4<T>) * n);
     s->tab_F = dalloc(s, sizeof(Vec4<T>) * n);
     s->tab_d0 = dalloc(s, sizeof(Vec4<T>) * n);
     s->tab_d1 = dalloc(s, sizeof(Vec2<T>) * n);
-    s->sc = (DevScalars *)dalloc(s, sizeof(DevScalars));
-    s->partial = (double *)dalloc(s, sizeof(double) * 1024);
-    s->red_out = (double *)dalloc(s, sizeof(double) * 2);
+    s->partial = (double *)dalloc(s, sizeof(double) * 512 * s->nrep);
+    s->red_out = (double *)dalloc(s, sizeof(double) * 2 * s->nrep);
     s->out_buf = (double *)dalloc(s, sizeof(double) * 3 * ns);
     s->aux_int = (int *)dalloc(s, sizeof(int) * ns);
     s->aux_dbl = (double *)dalloc(s, sizeof(double) * 3 * ns);
-    if (!s->fp || !s->rho || !s->esite || !s->ra_home || !s->ra_id || !s->t_home || !s->t_id || !s->ra_fp || !s->ra_rho ||
-        !s->ra_e || !s->knots || !s->tab_f || !s->tab_phi || !s->tab_F || !s->tab_d0 || !s->tab_d1 || !s->sc ||
-        !s->partial || !s->red_out || !s->out_buf || !s->aux_int || !s->aux_dbl)
+    if (!s->reps_d || !s->sc || !s->tile_rep || !s->tile_flag || !s->sid || !s->claim || !s->fp || !s->rho ||
+        !s->esite || !s->ra_home || !s->ra_id || !s->t_home || !s->t_id || !s->ra_fp || !s->ra_rho || !s->ra_e ||
+        !s->knots || !s->tab_f || !s->tab_phi || !s->tab_F || !s->tab_d0 || !s->tab_d1 || !s->partial ||
+        !s->red_out || !s->out_buf || !s->aux_int || !s->aux_dbl)
         return fail(s, MISA_EOOM, "device allocation failed");
     CK(cudaMemcpyAsync(s->knots, s->fk.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->knots + n, s->pk.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s->st));
@@ -444,11 +562,15 @@ int create_impl(misa_sim *s)
                                                             (Vec4<T> *)s->tab_f, (Vec4<T> *)s->tab_phi,
                                                             (Vec4<T> *)s->tab_F, (Vec4<T> *)s->tab_d0,
                                                             (Vec2<T> *)s->tab_d1);
-    int rc = configure<T>(s);
+    int rc = configure<T>(s, s->p.tile > 0 ? s->p.tile - 1 : 0);
     if (rc) return rc;
     MdArgs<T> m = md_args<T>(s);
-    k_init_crystal<T><<<s->nsm * 8, 256, 0, s->st>>>(m);
+    k_init_crystal<T><<<site_grid(s), 256, 0, s->st>>>(m);
     CK(cudaGetLastError());
+    if (s->p.tile == 0) {
+        rc = autotune<T>(s);
+        if (rc) return rc;
+    }
     return refresh<T>(s, true);
 }
 
@@ -463,22 +585,22 @@ int set_state_impl(misa_sim *s, const double *x, const double *v)
         CK(cudaMemcpyAsync(s->aux_dbl, v, sizeof(double) * 3 * N, cudaMemcpyDefault, s->st));
         vd = s->aux_dbl;
     }
-    k_reset_list<T><<<1, 1, 0, s->st>>>(m);
-    k_clear_sites<T><<<s->nsm * 8, 256, 0, s->st>>>(m);
-    const double L[3] = {s->nx * s->p.a0, s->ny * s->p.a0, s->nz * s->p.a0};
+    k_reset_list<T><<<rep_blocks(s), 128, 0, s->st>>>(m);
+    k_clear_sites<T><<<site_grid(s), 256, 0, s->st>>>(m);
     // each atom's displacement from its nearest site overwrites its position in place
-    k_state_claim<T><<<s->nsm * 8, 256, 0, s->st>>>(m, s->out_buf, N, L[0], L[1], L[2], s->aux_int, s->out_buf);
+    k_state_claim<T><<<site_grid(s), 256, 0, s->st>>>(m, s->out_buf, s->aux_int, s->out_buf);
     if (!v) {
         CK(cudaMemsetAsync(s->v[0], 0, sizeof(double) * N, s->st));
         CK(cudaMemsetAsync(s->v[1], 0, sizeof(double) * N, s->st));
         CK(cudaMemsetAsync(s->v[2], 0, sizeof(double) * N, s->st));
     }
-    k_state_place<T><<<s->nsm * 8, 256, 0, s->st>>>(m, vd, N, s->aux_int, s->out_buf);
-    k_ra_sort<T><<<1, 1024, sizeof(unsigned long long) * kSortMax, s->st>>>(m);
+    k_state_place<T><<<site_grid(s), 256, 0, s->st>>>(m, vd, s->aux_int, s->out_buf);
+    k_ra_sort<T><<<s->nrep, 1024, sizeof(unsigned long long) * kSortMax, s->st>>>(m);
     CK(cudaGetLastError());
     return refresh<T>(s, true);
 }
 
+// per-replica potential and kinetic energy (eV) into pe[r], ke[r]
 template <typename T>
 int reduce_energy(misa_sim *s, double *pe, double *ke, double *per_atom)
 {
@@ -486,19 +608,21 @@ int reduce_energy(misa_sim *s, double *pe, double *ke, double *per_atom)
     if (rc) return rc;
     MdArgs<T> m = md_args<T>(s);
     const int nb = 512;
-    k_sum_stage1<T><<<nb, 256, 0, s->st>>>(m, 0, s->partial);
-    k_sum_stage2<<<1, 1024, 0, s->st>>>(s->partial, nb, s->red_out);
-    k_sum_stage1<T><<<nb, 256, 0, s->st>>>(m, 1, s->partial);
-    k_sum_stage2<<<1, 1024, 0, s->st>>>(s->partial, nb, s->red_out + 1);
+    k_sum_stage1<T><<<dim3(nb, s->nrep), 256, 0, s->st>>>(m, 0, s->partial);
+    k_sum_stage2<<<s->nrep, 1024, 0, s->st>>>(s->partial, nb, s->red_out);
+    k_sum_stage1<T><<<dim3(nb, s->nrep), 256, 0, s->st>>>(m, 1, s->partial);
+    k_sum_stage2<<<s->nrep, 1024, 0, s->st>>>(s->partial, nb, s->red_out + s->nrep);
     if (per_atom) {
-        k_scatter<T><<<s->nsm * 8, 256, 0, s->st>>>(m, 4, s->out_buf, s->nx * s->p.a0, s->ny * s->p.a0, s->nz * s->p.a0);
+        k_scatter<T><<<site_grid(s), 256, 0, s->st>>>(m, 4, s->out_buf);
         CK(cudaMemcpyAsync(per_atom, s->out_buf, sizeof(double) * s->ns, cudaMemcpyDefault, s->st));
     }
-    double h[2];
-    CK(cudaMemcpyAsync(h, s->red_out, sizeof(h), cudaMemcpyDeviceToHost, s->st));
+    std::vector<double> h(2 * s->nrep);
+    CK(cudaMemcpyAsync(h.data(), s->red_out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
-    if (pe) *pe = h[0];
-    if (ke) *ke = 0.5 * s->p.mass * h[1] / kAccUnit;
+    for (int r = 0; r < s->nrep; ++r) {
+        if (pe) pe[r] = h[r];
+        if (ke) ke[r] = 0.5 * s->p.mass * h[s->nrep + r] / kAccUnit;
+    }
     return MISA_OK;
 }
 
@@ -510,7 +634,7 @@ int scatter_out(misa_sim *s, int kind, double *out)
         int rc = launch_forces<T>(s, 0, true);
         if (rc) return rc;
     }
-    k_scatter<T><<<s->nsm * 8, 256, 0, s->st>>>(m, kind, s->out_buf, s->nx * s->p.a0, s->ny * s->p.a0, s->nz * s->p.a0);
+    k_scatter<T><<<site_grid(s), 256, 0, s->st>>>(m, kind, s->out_buf);
     CK(cudaGetLastError());
     size_t cnt = kind >= 3 ? (size_t)s->ns : 3 * (size_t)s->ns;
     CK(cudaMemcpyAsync(out, s->out_buf, sizeof(double) * cnt, cudaMemcpyDefault, s->st));
@@ -521,10 +645,96 @@ int scatter_out(misa_sim *s, int kind, double *out)
 int check_status(misa_sim *s)
 {
     unsigned st = 0;
-    CK(cudaMemcpyAsync(&st, &s->sc->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(&st, &s->sc[0].status, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
     if (st & kStRunawayOverflow) return fail(s, MISA_ERUNAWAY_OVERFLOW, "run-away list overflow");
     if (st & kStNonfinite) return fail(s, MISA_EUNSTABLE, "non-finite force or velocity");
+    return MISA_OK;
+}
+
+int validate(const misa_params &p, misa_sim *s)
+{
+    if (!(p.a0 > 0) || !(p.mass > 0) || !(p.rc > 0) || !(p.skin > 0)) return fail(s, MISA_EINVAL, "a0, mass, rc, skin must be > 0");
+    if (p.n_knots < 8 || !p.f_knots || !p.phi_knots || !p.F_knots || !(p.rho_max > 0))
+        return fail(s, MISA_EINVAL, "three knot tables (n >= 8) and rho_max > 0 are required");
+    double half = 0.5 * p.a0, roff = (p.rc + 2.0 * p.skin) / half;
+    if (roff * roff >= 27.0) return fail(s, MISA_EINVAL, "(rc + 2 skin) must be below sqrt(27) a0/2 (2-cell halo)");
+    if (p.skin >= 0.25 * std::sqrt(3.0) * p.a0) return fail(s, MISA_EINVAL, "skin must be below half the nearest-neighbour distance");
+    if (p.precision != MISA_FP64 && p.precision != MISA_FP32_FORCE) return fail(s, MISA_EINVAL, "precision");
+    if (!(p.dt_max > 0) || p.dx_max < 0) return fail(s, MISA_EINVAL, "dt_max > 0, dx_max >= 0");
+    if (!!p.alloc != !!p.free) return fail(s, MISA_EINVAL, "alloc and free hooks come together");
+    if (p.tile < 0 || p.tile > kNTiles) return fail(s, MISA_EINVAL, "tile index");
+    return MISA_OK;
+}
+
+// builds the host side of a batch (replica table, knots); no device work
+int init_host(misa_sim *s, const misa_params &p, int nrep, const int32_t *dims)
+{
+    s->p = p;
+    s->fk.assign(p.f_knots, p.f_knots + p.n_knots);
+    s->pk.assign(p.phi_knots, p.phi_knots + p.n_knots);
+    s->Fk.assign(p.F_knots, p.F_knots + p.n_knots);
+    s->p.f_knots = s->fk.data();
+    s->p.phi_knots = s->pk.data();
+    s->p.F_knots = s->Fk.data();
+    s->prec = p.precision;
+    s->nrep = nrep;
+    s->dims.assign(dims, dims + 3 * nrep);
+    long long ns = 0, maxns = 0;
+    for (int r = 0; r < nrep; ++r) {
+        const int nx = dims[3 * r], ny = dims[3 * r + 1], nz = dims[3 * r + 2];
+        if (nx < 6 || ny < 6 || nz < 6) return fail(s, MISA_EINVAL, "each box dimension must be >= 6 cells");
+        long long n = 2LL * nx * ny * nz;
+        maxns = n > maxns ? n : maxns;
+        ns += n;
+    }
+    if (ns >= (1LL << 31)) return fail(s, MISA_EINVAL, "too many atoms for 32-bit ids");
+    s->ns = ns;
+    long long cap = p.runaway_capacity > 0 ? p.runaway_capacity : (maxns / 64 > 4096 ? maxns / 64 : 4096);
+    if (cap > kSortMax) cap = kSortMax;
+    s->cap = (int)cap;
+    s->reps.resize(nrep);
+    long long base = 0;
+    long long tcap = 0;
+    for (int r = 0; r < nrep; ++r) {
+        RepDesc &rd = s->reps[r];
+        std::memset(&rd, 0, sizeof(rd));
+        rd.nx = dims[3 * r];
+        rd.ny = dims[3 * r + 1];
+        rd.nz = dims[3 * r + 2];
+        rd.site_base = base;
+        rd.ns = 2LL * rd.nx * rd.ny * rd.nz;
+        rd.ra_base = r * s->cap;
+        rd.cap = s->cap;
+        base += rd.ns;
+        long long worst = 0;
+        for (int k = 0; k < kNTiles; ++k) {
+            long long nt = (long long)((rd.nx + kTiles[k].tx - 1) / kTiles[k].tx) * ((rd.ny + kTiles[k].ty - 1) / kTiles[k].ty) *
+                           ((rd.nz + kTiles[k].tz - 1) / kTiles[k].tz);
+            worst = nt > worst ? nt : worst;
+        }
+        tcap += worst;
+    }
+    s->ntile_cap = tcap;
+    return MISA_OK;
+}
+
+int stats_of(misa_sim *s, int r, const DevScalars &h, unsigned status, misa_stats *o)
+{
+    o->step = h.step;
+    o->time = h.t;
+    double vmax;
+    std::memcpy(&vmax, &h.vmax_bits, sizeof(double));
+    o->vmax = vmax;
+    double dt = s->p.dt_max;
+    if (s->p.dx_max > 0 && vmax > 0) dt = std::fmin(s->p.dt_max, s->p.dx_max / vmax);
+    o->dt = dt;
+    o->natoms = r < 0 ? s->ns : s->reps[r].ns;
+    o->nsites = o->natoms;
+    o->n_runaway = h.n_ra;
+    o->n_vacant = h.n_ra;
+    o->status = status;
+    o->launches = s->launches;
     return MISA_OK;
 }
 
@@ -554,46 +764,30 @@ void misa_default_params(misa_params *p)
     p->tile = 0;
 }
 
-int misa_create(const misa_params *pp, void *stream, misa_sim **out)
+int misa_create_batch(const misa_params *pp, int32_t nrep, const int32_t *dims, void *stream, misa_sim **out)
 {
-    misa_sim *s = nullptr;
-    if (!pp || !out) return fail(s, MISA_EINVAL, "null argument");
+    misa_sim *none = nullptr;
+    if (!pp || !out || nrep < 1 || !dims) return fail(none, MISA_EINVAL, "null argument or nrep < 1");
     *out = nullptr;
-    const misa_params &p = *pp;
-    if (p.nx < 6 || p.ny < 6 || p.nz < 6) return fail(s, MISA_EINVAL, "each box dimension must be >= 6 cells");
-    if (!(p.a0 > 0) || !(p.mass > 0) || !(p.rc > 0) || !(p.skin > 0)) return fail(s, MISA_EINVAL, "a0, mass, rc, skin must be > 0");
-    if (p.n_knots < 8 || !p.f_knots || !p.phi_knots || !p.F_knots || !(p.rho_max > 0))
-        return fail(s, MISA_EINVAL, "three knot tables (n >= 8) and rho_max > 0 are required");
-    double half = 0.5 * p.a0, roff = (p.rc + 2.0 * p.skin) / half;
-    if (roff * roff >= 27.0) return fail(s, MISA_EINVAL, "(rc + 2 skin) must be below sqrt(27) a0/2 (2-cell halo)");
-    if (p.skin >= 0.25 * std::sqrt(3.0) * p.a0) return fail(s, MISA_EINVAL, "skin must be below half the nearest-neighbour distance");
-    if (p.precision != MISA_FP64 && p.precision != MISA_FP32_FORCE) return fail(s, MISA_EINVAL, "precision");
-    if (!(p.dt_max > 0) || p.dx_max < 0) return fail(s, MISA_EINVAL, "dt_max > 0, dx_max >= 0");
-    if (!!p.alloc != !!p.free) return fail(s, MISA_EINVAL, "alloc and free hooks come together");
-    long long ns = 2LL * p.nx * p.ny * p.nz;
-    if (ns >= (1LL << 31)) return fail(s, MISA_EINVAL, "too many atoms for 32-bit ids");
-    if (p.tile < 0 || p.tile > kNTiles) return fail(s, MISA_EINVAL, "tile index");
-    s = new misa_sim();
-    s->p = p;
-    s->fk.assign(p.f_knots, p.f_knots + p.n_knots);
-    s->pk.assign(p.phi_knots, p.phi_knots + p.n_knots);
-    s->Fk.assign(p.F_knots, p.F_knots + p.n_knots);
-    s->p.f_knots = s->fk.data();
-    s->p.phi_knots = s->pk.data();
-    s->p.F_knots = s->Fk.data();
+    int rc = validate(*pp, none);
+    if (rc) return rc;
+    misa_sim *s = new misa_sim();
+    rc = init_host(s, *pp, nrep, dims);
+    if (rc) {
+        g_create_error = s->err;
+        delete s;
+        return rc;
+    }
     s->st = (cudaStream_t)stream;
-    s->nx = p.nx; s->ny = p.ny; s->nz = p.nz;
-    s->ns = ns;
-    s->prec = p.precision;
-    long long cap = p.runaway_capacity > 0 ? p.runaway_capacity : (ns / 64 > 4096 ? ns / 64 : 4096);
-    if (cap > kSortMax) cap = kSortMax;
-    s->cap = (int)cap;
-    s->tile = p.tile > 0 ? p.tile - 1 : 0;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, dev);
     if (s->nsm <= 0) s->nsm = 1;
-    int rc = s->prec == MISA_FP64 ? create_impl<double>(s) : create_impl<float>(s);
+    if (cudaStreamCreateWithFlags(&s->gst, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming) != cudaSuccess)
+        rc = fail(s, MISA_ECUDA, "stream/event creation failed");
+    if (!rc) rc = s->prec == MISA_FP64 ? create_impl<double>(s) : create_impl<float>(s);
     if (rc == MISA_OK) {
         cudaError_t e = cudaStreamSynchronize(s->st);
         if (e != cudaSuccess) rc = fail(s, MISA_ECUDA, std::string("create: ") + cudaGetErrorString(e));
@@ -607,11 +801,23 @@ int misa_create(const misa_params *pp, void *stream, misa_sim **out)
     return MISA_OK;
 }
 
+int misa_create(const misa_params *pp, void *stream, misa_sim **out)
+{
+    if (!pp) return fail(nullptr, MISA_EINVAL, "null argument");
+    const int32_t dims[3] = {pp->nx, pp->ny, pp->nz};
+    return misa_create_batch(pp, 1, dims, stream, out);
+}
+
 void misa_destroy(misa_sim *s)
 {
     if (!s) return;
     cudaStreamSynchronize(s->st);
+    if (s->gst) cudaStreamSynchronize(s->gst);
+    if (s->graph) cudaGraphExecDestroy(s->graph);
     for (auto e : s->ev_pool) cudaEventDestroy(e);
+    if (s->ev_in) cudaEventDestroy(s->ev_in);
+    if (s->ev_out) cudaEventDestroy(s->ev_out);
+    if (s->gst) cudaStreamDestroy(s->gst);
     for (auto &a : s->allocs) {
         if (s->p.free) s->p.free(a.first, a.second, s->p.alloc_ctx);
         else cudaFree(a.first);
@@ -620,6 +826,21 @@ void misa_destroy(misa_sim *s)
 }
 
 const char *misa_last_error(const misa_sim *s) { return s ? s->err.c_str() : g_create_error.c_str(); }
+
+int misa_replica_count(const misa_sim *s) { return s ? s->nrep : 0; }
+
+int misa_replica_info(const misa_sim *s, int32_t r, int32_t dims[3], int64_t *atom_base, int64_t *natoms)
+{
+    if (!s || r < 0 || r >= s->nrep) return MISA_EINVAL;
+    if (dims) {
+        dims[0] = s->reps[r].nx;
+        dims[1] = s->reps[r].ny;
+        dims[2] = s->reps[r].nz;
+    }
+    if (atom_base) *atom_base = s->reps[r].site_base;
+    if (natoms) *natoms = s->reps[r].ns;
+    return MISA_OK;
+}
 
 int misa_set_state(misa_sim *s, const double *x, const double *v, int64_t n)
 {
@@ -634,10 +855,10 @@ int misa_set_velocities(misa_sim *s, const double *v, int64_t n)
     if (!v || n != s->ns) return fail(s, MISA_EINVAL, "set_velocities: n must equal natoms");
     CK(cudaMemcpyAsync(s->aux_dbl, v, sizeof(double) * 3 * s->ns, cudaMemcpyDefault, s->st));
     if (s->prec == MISA_FP64) {
-        k_set_velocities<double><<<s->nsm * 8, 256, 0, s->st>>>(md_args<double>(s), s->aux_dbl);
+        k_set_velocities<double><<<site_grid(s), 256, 0, s->st>>>(md_args<double>(s), s->aux_dbl);
         return refresh<double>(s, false);
     }
-    k_set_velocities<float><<<s->nsm * 8, 256, 0, s->st>>>(md_args<float>(s), s->aux_dbl);
+    k_set_velocities<float><<<site_grid(s), 256, 0, s->st>>>(md_args<float>(s), s->aux_dbl);
     return refresh<float>(s, false);
 }
 
@@ -647,22 +868,37 @@ int misa_insert_pka(misa_sim *s, int64_t atom, double energy, const double dir[3
     if (!dir || !(energy >= 0)) return fail(s, MISA_EINVAL, "insert_pka: bad direction or energy");
     double nrm = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
     if (!(nrm > 0)) return fail(s, MISA_EINVAL, "insert_pka: zero direction");
-    if (atom < 0) atom = 2LL * (((long long)(s->nz / 2) * s->ny + s->ny / 2) * s->nx + s->nx / 2);
+    if (atom < 0) {
+        const RepDesc &rd = s->reps[0];
+        atom = rd.site_base + 2LL * (((long long)(rd.nz / 2) * rd.ny + rd.ny / 2) * rd.nx + rd.nx / 2);
+    }
     if (atom >= s->ns) return fail(s, MISA_EINVAL, "insert_pka: atom id out of range");
     double speed = std::sqrt(2.0 * energy / s->p.mass * kAccUnit);
     double vx = speed * dir[0] / nrm, vy = speed * dir[1] / nrm, vz = speed * dir[2] / nrm;
     if (s->prec == MISA_FP64) {
-        k_pka<double><<<s->nsm * 8, 256, 0, s->st>>>(md_args<double>(s), (int)atom, vx, vy, vz);
+        k_pka<double><<<site_grid(s), 256, 0, s->st>>>(md_args<double>(s), (int)atom, vx, vy, vz);
         return refresh<double>(s, false);
     }
-    k_pka<float><<<s->nsm * 8, 256, 0, s->st>>>(md_args<float>(s), (int)atom, vx, vy, vz);
+    k_pka<float><<<site_grid(s), 256, 0, s->st>>>(md_args<float>(s), (int)atom, vx, vy, vz);
     return refresh<float>(s, false);
+}
+
+int misa_insert_pka_replica(misa_sim *s, int32_t r, double energy, const double dir[3])
+{
+    if (!s) return MISA_EINVAL;
+    if (r < 0 || r >= s->nrep) return fail(s, MISA_EINVAL, "insert_pka_replica: replica out of range");
+    const RepDesc &rd = s->reps[r];
+    long long atom = rd.site_base + 2LL * (((long long)(rd.nz / 2) * rd.ny + rd.ny / 2) * rd.nx + rd.nx / 2);
+    return misa_insert_pka(s, atom, energy, dir);
 }
 
 int misa_step(misa_sim *s, int n)
 {
     if (!s) return MISA_EINVAL;
     if (n < 0) return fail(s, MISA_EINVAL, "step: n < 0");
+    if (n == 0) return MISA_OK;
+    if (s->use_graph && !s->timing)
+        return s->prec == MISA_FP64 ? step_graph<double>(s, n) : step_graph<float>(s, n);
     for (int k = 0; k < n; ++k) {
         int rc = s->prec == MISA_FP64 ? launch_step<double>(s) : launch_step<float>(s);
         if (rc) return rc;
@@ -670,10 +906,34 @@ int misa_step(misa_sim *s, int n)
     return MISA_OK;
 }
 
+int misa_set_graphs(misa_sim *s, int enable)
+{
+    if (!s) return MISA_EINVAL;
+    s->use_graph = enable != 0;
+    return MISA_OK;
+}
+
 int misa_get_energies(misa_sim *s, double *pe, double *ke, double *per_atom)
 {
     if (!s) return MISA_EINVAL;
-    int rc = s->prec == MISA_FP64 ? reduce_energy<double>(s, pe, ke, per_atom) : reduce_energy<float>(s, pe, ke, per_atom);
+    std::vector<double> p(s->nrep), k(s->nrep);
+    int rc = s->prec == MISA_FP64 ? reduce_energy<double>(s, p.data(), k.data(), per_atom)
+                                  : reduce_energy<float>(s, p.data(), k.data(), per_atom);
+    if (rc) return rc;
+    double P = 0.0, K = 0.0;
+    for (int r = 0; r < s->nrep; ++r) {
+        P += p[r];
+        K += k[r];
+    }
+    if (pe) *pe = P;
+    if (ke) *ke = K;
+    return check_status(s);
+}
+
+int misa_replica_energies(misa_sim *s, double *pe, double *ke)
+{
+    if (!s) return MISA_EINVAL;
+    int rc = s->prec == MISA_FP64 ? reduce_energy<double>(s, pe, ke, nullptr) : reduce_energy<float>(s, pe, ke, nullptr);
     if (rc) return rc;
     return check_status(s);
 }
@@ -695,17 +955,27 @@ int misa_get_density(misa_sim *s, double *rho, int64_t n) { return get_kind(s, 3
 int misa_get_site_map(misa_sim *s, int64_t *site_atom, int64_t *ra_ids, int64_t cap, int64_t *n_runaway)
 {
     if (!s) return MISA_EINVAL;
-    DevScalars h;
-    CK(cudaMemcpyAsync(&h, s->sc, sizeof(h), cudaMemcpyDeviceToHost, s->st));
+    std::vector<DevScalars> h(s->nrep);
+    CK(cudaMemcpyAsync(h.data(), s->sc, sizeof(DevScalars) * s->nrep, cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
-    if (n_runaway) *n_runaway = h.n_ra;
-    if (ra_ids && cap < h.n_ra) return fail(s, MISA_EINVAL, "runaway_ids capacity too small");
-    long long *d_sa = (long long *)s->aux_dbl;          // ns int64 fit in 3 ns doubles
-    long long *d_ra = (long long *)s->out_buf;
-    if (s->prec == MISA_FP64) k_site_map<double><<<s->nsm * 8, 256, 0, s->st>>>(md_args<double>(s), d_sa, d_ra);
-    else k_site_map<float><<<s->nsm * 8, 256, 0, s->st>>>(md_args<float>(s), d_sa, d_ra);
+    long long tot = 0;
+    for (auto &q : h) tot += q.n_ra;
+    if (n_runaway) *n_runaway = tot;
+    if (ra_ids && cap < tot) return fail(s, MISA_EINVAL, "runaway_ids capacity too small");
+    long long *d_sa = (long long *)s->aux_dbl;  // ns int64 fit in 3 ns doubles
+    long long *d_ra = (long long *)s->out_buf;  // pooled run-away slots fit too
+    if (s->prec == MISA_FP64) k_site_map<double><<<site_grid(s), 256, 0, s->st>>>(md_args<double>(s), d_sa, d_ra);
+    else k_site_map<float><<<site_grid(s), 256, 0, s->st>>>(md_args<float>(s), d_sa, d_ra);
     if (site_atom) CK(cudaMemcpyAsync(site_atom, d_sa, sizeof(long long) * s->ns, cudaMemcpyDefault, s->st));
-    if (ra_ids && h.n_ra > 0) CK(cudaMemcpyAsync(ra_ids, d_ra, sizeof(long long) * h.n_ra, cudaMemcpyDefault, s->st));
+    if (ra_ids) {
+        long long off = 0;
+        for (int r = 0; r < s->nrep; ++r) {
+            if (h[r].n_ra > 0)
+                CK(cudaMemcpyAsync(ra_ids + off, d_ra + s->reps[r].ra_base, sizeof(long long) * h[r].n_ra,
+                                   cudaMemcpyDefault, s->st));
+            off += h[r].n_ra;
+        }
+    }
     CK(cudaStreamSynchronize(s->st));
     return MISA_OK;
 }
@@ -713,24 +983,29 @@ int misa_get_site_map(misa_sim *s, int64_t *site_atom, int64_t *ra_ids, int64_t 
 int misa_stats_get(misa_sim *s, misa_stats *o)
 {
     if (!s || !o) return MISA_EINVAL;
-    DevScalars h;
-    CK(cudaMemcpyAsync(&h, s->sc, sizeof(h), cudaMemcpyDeviceToHost, s->st));
+    std::vector<DevScalars> h(s->nrep);
+    CK(cudaMemcpyAsync(h.data(), s->sc, sizeof(DevScalars) * s->nrep, cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
-    o->step = h.step;
-    o->time = h.t;
-    double vmax;
-    std::memcpy(&vmax, &h.vmax_bits, sizeof(double));
-    o->vmax = vmax;
-    double dt = s->p.dt_max;
-    if (s->p.dx_max > 0 && vmax > 0) dt = std::fmin(s->p.dt_max, s->p.dx_max / vmax);
-    o->dt = dt;
-    o->natoms = s->ns;
-    o->nsites = s->ns;
-    o->n_runaway = h.n_ra;
-    o->n_vacant = h.n_ra;
-    o->status = h.status;
-    o->launches = s->launches;
+    DevScalars agg = h[0];
+    agg.n_ra = 0;
+    unsigned long long vb = 0;
+    for (auto &q : h) {
+        agg.n_ra += q.n_ra;
+        vb = q.vmax_bits > vb ? q.vmax_bits : vb;
+    }
+    agg.vmax_bits = vb;
+    stats_of(s, -1, agg, h[0].status, o);
+    if (s->nrep > 1) o->dt = 0.0;  // replicas step with their own dt
     return MISA_OK;
+}
+
+int misa_replica_stats(misa_sim *s, int32_t r, misa_stats *o)
+{
+    if (!s || !o || r < 0 || r >= s->nrep) return MISA_EINVAL;
+    std::vector<DevScalars> h(s->nrep);
+    CK(cudaMemcpyAsync(h.data(), s->sc, sizeof(DevScalars) * s->nrep, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return stats_of(s, r, h[r], h[0].status, o);
 }
 
 // 8 events per step: [start, after kick/drift, after list, after density,
@@ -741,7 +1016,6 @@ int misa_timing_enable(misa_sim *s, int enable)
     CK(cudaStreamSynchronize(s->st));
     s->timing = enable != 0;
     s->ev_used = 0;
-    s->timed_steps = 0;
     return MISA_OK;
 }
 
@@ -760,55 +1034,60 @@ int misa_timing_get(misa_sim *s, double ms[MISA_NPHASE], int64_t *steps)
         }
     if (steps) *steps = (int64_t)nsteps;
     s->ev_used = 0;
-    s->timed_steps = 0;
     return MISA_OK;
 }
 
 int misa_clear_status(misa_sim *s)
 {
     if (!s) return MISA_EINVAL;
-    CK(cudaMemsetAsync(&s->sc->status, 0, sizeof(unsigned), s->st));
+    CK(cudaMemsetAsync(&s->sc[0].status, 0, sizeof(unsigned), s->st));
     return MISA_OK;
 }
 
 // checkpoint: header, then the raw device arrays of the lattice list
 struct CkptHeader {
     char magic[8];
-    int32_t version, nx, ny, nz, prec, cap;
+    int32_t version, nrep, prec, cap;
+    int64_t ns;
 };
 
 static int ckpt_io(misa_sim *s, const char *path, bool save)
 {
     if (!s || !path) return MISA_EINVAL;
+    CK(cudaStreamSynchronize(s->st));
     FILE *f = std::fopen(path, save ? "wb" : "rb");
     if (!f) return fail(s, MISA_EINVAL, std::string("cannot open ") + path);
     CkptHeader hd{};
     std::memcpy(hd.magic, "MISAGB3", 8);
-    hd.version = 1; hd.nx = s->nx; hd.ny = s->ny; hd.nz = s->nz; hd.prec = s->prec; hd.cap = s->cap;
+    hd.version = 2; hd.nrep = s->nrep; hd.prec = s->prec; hd.cap = s->cap; hd.ns = s->ns;
     if (save) {
         std::fwrite(&hd, sizeof(hd), 1, f);
+        std::fwrite(s->dims.data(), sizeof(int), s->dims.size(), f);
     } else {
         CkptHeader in{};
-        if (std::fread(&in, sizeof(in), 1, f) != 1 || std::memcmp(in.magic, hd.magic, 8) != 0 || in.nx != hd.nx ||
-            in.ny != hd.ny || in.nz != hd.nz || in.prec != hd.prec || in.cap != hd.cap) {
+        std::vector<int> dims(s->dims.size());
+        if (std::fread(&in, sizeof(in), 1, f) != 1 || std::memcmp(in.magic, hd.magic, 8) != 0 || in.version != 2 ||
+            in.nrep != hd.nrep || in.prec != hd.prec || in.cap != hd.cap || in.ns != hd.ns ||
+            std::fread(dims.data(), sizeof(int), dims.size(), f) != dims.size() || dims != s->dims) {
             std::fclose(f);
             return fail(s, MISA_EINVAL, "checkpoint does not match this handle");
         }
     }
     size_t Tb = s->prec == MISA_FP64 ? 8 : 4;
-    std::vector<std::pair<void *, size_t>> arrs = {{s->sid, 4 * (size_t)s->ns}, {s->sc, sizeof(DevScalars)}};
+    const size_t capt = (size_t)s->cap * s->nrep;
+    std::vector<std::pair<void *, size_t>> arrs = {{s->sid, 4 * (size_t)s->ns}, {s->sc, sizeof(DevScalars) * s->nrep}};
     for (int d = 0; d < 3; ++d) {
         arrs.push_back({s->u[d], 8 * (size_t)s->ns});
         arrs.push_back({s->v[d], 8 * (size_t)s->ns});
         arrs.push_back({s->a[d], Tb * (size_t)s->ns});
         if (s->prec != MISA_FP64) arrs.push_back({s->s[d], Tb * (size_t)s->ns});
-        arrs.push_back({s->ra_u[d], 8 * (size_t)s->cap});
-        arrs.push_back({s->ra_v[d], 8 * (size_t)s->cap});
-        arrs.push_back({s->ra_s[d], Tb * (size_t)s->cap});
-        arrs.push_back({s->ra_a[d], Tb * (size_t)s->cap});
+        arrs.push_back({s->ra_u[d], 8 * capt});
+        arrs.push_back({s->ra_v[d], 8 * capt});
+        arrs.push_back({s->ra_s[d], Tb * capt});
+        arrs.push_back({s->ra_a[d], Tb * capt});
     }
-    arrs.push_back({s->ra_home, 4 * (size_t)s->cap});
-    arrs.push_back({s->ra_id, 4 * (size_t)s->cap});
+    arrs.push_back({s->ra_home, 4 * capt});
+    arrs.push_back({s->ra_id, 4 * capt});
     std::vector<char> buf;
     int rc = MISA_OK;
     for (auto &a : arrs) {
@@ -843,6 +1122,8 @@ int misa_tile_shape(int index, int *tx, int *ty, int *tz)
     return MISA_OK;
 }
 
+int misa_tile_current(const misa_sim *s) { return s ? s->tile + 1 : 0; }
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
@@ -857,11 +1138,11 @@ namespace {
 
 constexpr size_t kStaticAlign = 256;
 // upper bound of the carve below for either precision: per site <= 160 B,
-// per run-away slot <= 512 B, per knot <= 160 B, one flag per cell, the
-// scalars, and the alignment padding of every buffer
+// per run-away slot <= 512 B, per knot <= 160 B, one flag and one map entry
+// per cell, the replica table and scalars, and the alignment padding
 constexpr size_t kStaticNeed = 160ull * MISA_STATIC_MAX_ATOMS + 512ull * MISA_STATIC_RUNAWAY_CAP +
-                               160ull * MISA_STATIC_MAX_KNOTS + 4ull * (MISA_STATIC_MAX_ATOMS / 2) +
-                               sizeof(DevScalars) + 96 * kStaticAlign;
+                               160ull * MISA_STATIC_MAX_KNOTS + 8ull * (MISA_STATIC_MAX_ATOMS / 2) +
+                               sizeof(DevScalars) + sizeof(RepDesc) + 96 * kStaticAlign;
 static_assert(kStaticNeed <= MISA_STATIC_SCRATCH_BYTES, "static scratch too small");
 
 }  // namespace
@@ -892,6 +1173,8 @@ size_t carve_static(misa_sim *s, unsigned char *base, int nk)
 {
     Carver c{base};
     const size_t ns = (size_t)s->ns, cap = (size_t)s->cap;
+    s->reps_d = c.take<RepDesc>(1);
+    s->sc = c.take<DevScalars>(1);
     s->sid = c.take<int>(ns);
     s->claim = c.take<int>(ns);
     for (int d = 0; d < 3; ++d) {
@@ -923,10 +1206,10 @@ size_t carve_static(misa_sim *s, unsigned char *base, int nk)
     s->tab_F = c.take<Vec4<T>>(nk);
     s->tab_d0 = c.take<Vec4<T>>(nk);
     s->tab_d1 = c.take<Vec2<T>>(nk);
-    s->sc = c.take<DevScalars>(1);
     s->out_buf = c.take<double>(3 * ns);
     s->aux_int = c.take<int>(ns);
     s->tile_flag = c.take<int>(ns / 2);
+    s->tile_rep = c.take<int>(ns / 2);
     return c.off;
 }
 
@@ -941,21 +1224,20 @@ int static_forces_impl(misa_sim *s, const double *knots, const double *x, double
                                                             (Vec4<T> *)s->tab_f, (Vec4<T> *)s->tab_phi,
                                                             (Vec4<T> *)s->tab_F, (Vec4<T> *)s->tab_d0,
                                                             (Vec2<T> *)s->tab_d1);
-    int rc = configure<T>(s);
+    int rc = configure<T>(s, 0);
     if (rc) return rc;
     // hash the positions into the lattice list (clears sites, claims, list)
     // and evaluate forces; then the energy pass for E_i
     rc = set_state_impl<T>(s, x, nullptr);
     if (rc) return rc;
     MdArgs<T> m = md_args<T>(s);
-    const double L[3] = {s->nx * s->p.a0, s->ny * s->p.a0, s->nz * s->p.a0};
-    k_scatter<T><<<s->nsm * 8, 256, 0, s->st>>>(m, 2, s->out_buf, L[0], L[1], L[2]);
+    k_scatter<T><<<site_grid(s), 256, 0, s->st>>>(m, 2, s->out_buf);
     CK(cudaMemcpyAsync(forces, s->out_buf, sizeof(double) * 3 * (size_t)s->ns, cudaMemcpyDeviceToDevice, s->st));
     if (energies) {
         rc = launch_forces<T>(s, 0, true);
         if (rc) return rc;
         m = md_args<T>(s);
-        k_scatter<T><<<s->nsm * 8, 256, 0, s->st>>>(m, 4, s->out_buf, L[0], L[1], L[2]);
+        k_scatter<T><<<site_grid(s), 256, 0, s->st>>>(m, 4, s->out_buf);
         CK(cudaMemcpyAsync(energies, s->out_buf, sizeof(double) * (size_t)s->ns, cudaMemcpyDeviceToDevice, s->st));
     }
     CK(cudaGetLastError());
@@ -1009,11 +1291,16 @@ extern "C" int misa_eam_forces_static(int32_t nx, int32_t ny, int32_t nz, double
     s.p.rho_max = rho_max;
     s.p.precision = precision;
     s.st = (cudaStream_t)stream;
-    s.nx = nx; s.ny = ny; s.nz = nz;
+    s.nrep = 1;
     s.ns = ns;
     s.prec = precision;
     s.cap = MISA_STATIC_RUNAWAY_CAP;
-    s.tile = 0;
+    s.reps.resize(1);
+    std::memset(&s.reps[0], 0, sizeof(RepDesc));
+    s.reps[0].nx = nx; s.reps[0].ny = ny; s.reps[0].nz = nz;
+    s.reps[0].ns = ns;
+    s.reps[0].cap = s.cap;
+    s.ntile_cap = ns / 2;
     cudaDeviceGetAttribute(&s.nsm, cudaDevAttrMultiProcessorCount, dev);
     if (s.nsm <= 0) s.nsm = 1;
     size_t used = precision == MISA_FP64 ? carve_static<double>(&s, (unsigned char *)base, n_knots)

@@ -118,6 +118,19 @@ struct DevScalars {
     int pad;
 };
 
+// One replica (independent periodic box) of a batch.  Sites, atoms and
+// run-away slots of all replicas live in pooled arrays; a replica owns the
+// site range [site_base, site_base + ns), the global tiles
+// [tile_base, tile_base + ntiles) and the run-away slots [ra_base, ra_base + cap).
+// Atom ids equal the initial global site ids.
+struct RepDesc {
+    int nx, ny, nz;
+    int ntx, nty, ntz;
+    int ntiles, tile_base;
+    long long site_base, ns;
+    int ra_base, cap;
+};
+
 template <typename T>
 struct alignas(2 * sizeof(T) == 8 ? 16 : 32) Vec4 {
     T x, y, z, w;

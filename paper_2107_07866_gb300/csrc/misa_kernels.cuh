@@ -25,6 +25,7 @@
 namespace misa {
 
 constexpr int kRaChunk = 128;  // run-away atoms staged per round in a tile CTA
+constexpr int kRedFloats = 112; // block-reduction scratch: 33 floats, then 32 doubles from byte 192
 constexpr double kRws = 1.1180339887498949;  // max distance to the nearest bcc site: sqrt(5)/2 (a0/2 units)
 
 // ---------------------------------------------------------------------------
@@ -165,9 +166,11 @@ struct ShellInfo {
 
 template <typename T>
 struct GatherArgs {
-    int nx, ny, nz;
-    int ntx, nty, ntz, ntiles;
-    const T *ux, *uy, *uz;  // displacement per site, lattice units; vacant = kVacant
+    const RepDesc *reps;    // replica table
+    const int *tile_rep;    // replica of every global tile
+    int ntiles;             // tiles of all replicas
+    int nrep;
+    const T *ux, *uy, *uz;  // displacement per site (pooled), lattice units; vacant = kVacant
     const T *fp;            // force pass input: F' per site
     T *fp_out;              // density pass output
     T *rho_out;             // density (energy mode) or null
@@ -177,19 +180,20 @@ struct GatherArgs {
     const Vec4<T> *tab_f, *tab_phi, *tab_F, *tab_d0;
     const Vec2<T> *tab_d1;
     int nseg;
-    T S;        // knot index per lattice unit of r: (a0/2)/h_r
-    T Srho;     // 1/h_rho
+    int seg_lo;  // first segment an array-array pair can reach (r >= d_nn - 2 skin)
+    T S;         // knot index per lattice unit of r: (a0/2)/h_r
+    T Srho;      // 1/h_rho
     T rho_max;
-    T rc2;      // rc^2, lattice units
+    T rc2;       // rc^2, lattice units
     T rc_lat;
-    T rfloor2;  // r_floor^2, lattice units
-    // run-away list
-    const int *ra_home;
+    T rfloor2;   // r_floor^2, lattice units
+    // run-away lists (pooled; replica r owns [ra_base, ra_base + cap))
+    const int *ra_home;     // home site, local to the replica
     const T *ra_ux, *ra_uy, *ra_uz;
     const T *ra_fp;
-    const int *tile_flag;
-    DevScalars *sc;
-    double acc_conv;  // (eV/A) -> (A/fs^2): 9.6485e-3 / m
+    const int *tile_flag;   // per global tile
+    DevScalars *sc;         // per replica
+    double acc_conv;        // (eV/A) -> (A/fs^2): 9.6485e-3 / m
     int kick;
     // neighbour offset index for this tile shape: per parity, per lattice
     // vector: (shared-memory slot displacement as int bits, 2 n_x, 2 n_y, 2 n_z)
@@ -215,15 +219,6 @@ struct RaStage {
     int cnt, next;
 };
 
-template <int B, int E, typename F>
-__device__ __forceinline__ void static_for(F &&f)
-{
-    if constexpr (B < E) {
-        f(std::integral_constant<int, B>{});
-        static_for<B + 1, E>(f);
-    }
-}
-
 __device__ __forceinline__ int wrap_cell(int g, int n)
 {
     if (g < 0) g += n;
@@ -231,15 +226,41 @@ __device__ __forceinline__ int wrap_cell(int g, int n)
     return g;
 }
 
+// Global tile -> replica, its descriptor and the tile's cell origin.
+struct TileLoc {
+    int rep;
+    RepDesc rd;
+    int c0x, c0y, c0z;
+};
+
+__device__ __forceinline__ TileLoc finish_locate(TileLoc L, int tile, int TX, int TY, int TZ)
+{
+    const int lt = tile - L.rd.tile_base;
+    const int tix = lt % L.rd.ntx, tiy = (lt / L.rd.ntx) % L.rd.nty, tiz = lt / (L.rd.ntx * L.rd.nty);
+    L.c0x = tix * TX;
+    L.c0y = tiy * TY;
+    L.c0z = tiz * TZ;
+    return L;
+}
+
+__device__ __forceinline__ TileLoc locate_tile(const RepDesc *reps, const int *tile_rep, int tile, int TX, int TY,
+                                               int TZ)
+{
+    TileLoc L;
+    L.rep = tile_rep[tile];
+    L.rd = reps[L.rep];
+    return finish_locate(L, tile, TX, TY, TZ);
+}
+
 // ---------------------------------------------------------------------------
 // tile staging
 // ---------------------------------------------------------------------------
 
-// Loads (ux, uy, uz, F') of the tile with cell origin (c0x, c0y, c0z) plus a
+// Loads (ux, uy, uz, F') of the tile at (c0x, c0y, c0z) of replica rd plus a
 // 2-cell periodic halo into sU, split by parity.  Returns max |u| over the
 // occupied staged sites (lattice units), block-wide.
 template <typename T, int TX, int TY, int TZ, bool WITH_FP>
-__device__ __forceinline__ T stage_tile(const GatherArgs<T> &a, Vec4<T> *sU, int c0x, int c0y, int c0z, float *sred)
+__device__ __forceinline__ T stage_tile(const GatherArgs<T> &a, const TileLoc &L, Vec4<T> *sU, float *sred)
 {
     using G = Tile<TX, TY, TZ>;
     T umax2 = 0;
@@ -250,10 +271,10 @@ __device__ __forceinline__ T stage_tile(const GatherArgs<T> &a, Vec4<T> *sU, int
         const int yz = r / G::SX;
         const int y = yz % G::SY;
         const int z = yz / G::SY;
-        const int gx = wrap_cell(c0x - 2 + x, a.nx);
-        const int gy = wrap_cell(c0y - 2 + y, a.ny);
-        const int gz = wrap_cell(c0z - 2 + z, a.nz);
-        const long long sid = (((long long)gz * a.ny + gy) * a.nx + gx) * 2 + p;
+        const int gx = wrap_cell(L.c0x - 2 + x, L.rd.nx);
+        const int gy = wrap_cell(L.c0y - 2 + y, L.rd.ny);
+        const int gz = wrap_cell(L.c0z - 2 + z, L.rd.nz);
+        const long long sid = L.rd.site_base + (((long long)gz * L.rd.ny + gy) * L.rd.nx + gx) * 2 + p;
         Vec4<T> v;
         v.x = a.ux[sid];
         v.y = a.uy[sid];
@@ -277,14 +298,15 @@ __device__ __forceinline__ T stage_tile(const GatherArgs<T> &a, Vec4<T> *sU, int
     return (T)(sqrtf(sred[32]) * 1.000001f);
 }
 
-// Stages the next chunk of run-away atoms whose home cell lies within 3
-// cells of the tile (reach rc + skin + the Wigner-Seitz radius), in list
-// order, as (home lattice coords relative to the tile origin, u, F').
+// Stages the next chunk of the replica's run-away atoms whose home cell lies
+// within 3 cells of the tile (reach rc + skin + the Wigner-Seitz radius), in
+// list order, as (home lattice coords relative to the tile origin, u, F').
 // Warp 0 scans; returns the staged count (block-uniform).
 template <typename T, int TX, int TY, int TZ, bool WITH_FP>
-__device__ __forceinline__ int stage_runaways(const GatherArgs<T> &a, int nra, int &pos, int c0x, int c0y, int c0z,
-                                              int4 *sRh, Vec4<T> *sRu, RaStage *st)
+__device__ __forceinline__ int stage_runaways(const GatherArgs<T> &a, const TileLoc &L, int nra, int &pos, int4 *sRh,
+                                              Vec4<T> *sRu, RaStage *st)
 {
+    const RepDesc &rd = L.rd;
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         int cnt = 0;
@@ -294,16 +316,16 @@ __device__ __forceinline__ int stage_runaways(const GatherArgs<T> &a, int nra, i
             bool take = false;
             int hx = 0, hy = 0, hz = 0;
             if (j < nra) {
-                const int h = a.ra_home[j];
-                const int x2 = h % (2 * a.nx);
-                const int rest = h / (2 * a.nx);
-                const int cy = rest % a.ny, cz = rest / a.ny;
+                const int h = a.ra_home[rd.ra_base + j];
+                const int x2 = h % (2 * rd.nx);
+                const int rest = h / (2 * rd.nx);
+                const int cy = rest % rd.ny, cz = rest / rd.ny;
                 const int par = x2 & 1, cx = x2 >> 1;
-                int dx = cx - c0x - TX / 2, dy = cy - c0y - TY / 2, dz = cz - c0z - TZ / 2;
+                int dx = cx - L.c0x - TX / 2, dy = cy - L.c0y - TY / 2, dz = cz - L.c0z - TZ / 2;
                 // nearest periodic image to the tile centre
-                dx -= a.nx * (int)floorf((dx + 0.5f * a.nx) / a.nx);
-                dy -= a.ny * (int)floorf((dy + 0.5f * a.ny) / a.ny);
-                dz -= a.nz * (int)floorf((dz + 0.5f * a.nz) / a.nz);
+                dx -= rd.nx * (int)floorf((dx + 0.5f * rd.nx) / rd.nx);
+                dy -= rd.ny * (int)floorf((dy + 0.5f * rd.ny) / rd.ny);
+                dz -= rd.nz * (int)floorf((dz + 0.5f * rd.nz) / rd.nz);
                 dx += TX / 2; dy += TY / 2; dz += TZ / 2;
                 take = dx >= -3 && dx < TX + 3 && dy >= -3 && dy < TY + 3 && dz >= -3 && dz < TZ + 3;
                 hx = 2 * dx + par;
@@ -316,10 +338,10 @@ __device__ __forceinline__ int stage_runaways(const GatherArgs<T> &a, int nra, i
             if (take && rank < room) {
                 sRh[cnt + rank] = make_int4(hx, hy, hz, 0);
                 Vec4<T> u;
-                u.x = a.ra_ux[j];
-                u.y = a.ra_uy[j];
-                u.z = a.ra_uz[j];
-                u.w = WITH_FP ? a.ra_fp[j] : (T)0;
+                u.x = a.ra_ux[rd.ra_base + j];
+                u.y = a.ra_uy[rd.ra_base + j];
+                u.z = a.ra_uz[rd.ra_base + j];
+                u.w = WITH_FP ? a.ra_fp[rd.ra_base + j] : (T)0;
                 sRu[cnt + rank] = u;
             }
             const int ntake = __popc(bal);
@@ -363,7 +385,7 @@ struct ShellRegs {
 };
 
 template <typename T>
-__device__ __forceinline__ int shell_arg(const ShellRegs<T> &sh, T q, T S, int nseg1, T &t, T &rinv)
+__device__ __forceinline__ int shell_arg(const ShellRegs<T> &sh, T q, T S, int seglo, int nseg1, T &t, T &rinv)
 {
     const T r2 = sh.n2 + q;
     if constexpr (sizeof(T) == 4) {
@@ -375,14 +397,14 @@ __device__ __forceinline__ int shell_arg(const ShellRegs<T> &sh, T q, T S, int n
         const float y = __fadd_rn(__fsub_rn(x, 0.5f), 12582912.0f);
         const float fl = __fsub_rn(y, 12582912.0f);
         t = __fsub_rn(x, fl);
-        return min(__float_as_int(y) + sh.xoff, nseg1);
+        return min(max(__float_as_int(y) + sh.xoff, seglo), nseg1);
     } else {
         const double r = sqrt(r2);
         rinv = 1.0 / r;
         const double x = r * S;
         const double fl = floor(x);
         t = x - fl;
-        return min((int)fl, nseg1);
+        return min(max((int)fl, seglo), nseg1);
     }
 }
 
@@ -430,8 +452,19 @@ __device__ __forceinline__ int clamp_seg(int seg, int nseg, T &t)
 }
 
 // shared-memory carve-up of the tile kernels
+// per-replica values a tile kernel reads at every tile, cached in shared
+// memory for batches of up to kRepSmem replicas
+constexpr int kRepSmem = 64;
+struct RepCache {
+    RepDesc rd;
+    double dt;
+    int n_ra;
+    int pad;
+};
+
 template <typename T>
 struct GatherSmem {
+    RepCache *rep;
     float4 *off;
     Vec4<T> *u;
     int4 *rh;
@@ -441,32 +474,149 @@ struct GatherSmem {
 };
 
 template <typename T, int TX, int TY, int TZ>
-__device__ __forceinline__ GatherSmem<T> carve(unsigned char *smem, size_t off)
+__device__ __forceinline__ GatherSmem<T> carve(unsigned char *smem, size_t off, int nbuf)
 {
     GatherSmem<T> g;
     off = (off + 255) & ~(size_t)255;
+    g.rep = reinterpret_cast<RepCache *>(smem + off);
+    off += sizeof(RepCache) * kRepSmem;
     g.off = reinterpret_cast<float4 *>(smem + off);
     off += sizeof(float4) * 2 * kNVec;
     g.u = reinterpret_cast<Vec4<T> *>(smem + off);
-    off += sizeof(Vec4<T>) * 2 * Tile<TX, TY, TZ>::PLANE;
+    off += sizeof(Vec4<T>) * 2 * Tile<TX, TY, TZ>::PLANE * nbuf;
     g.rh = reinterpret_cast<int4 *>(smem + off);
     off += sizeof(int4) * kRaChunk;
     g.ru = reinterpret_cast<Vec4<T> *>(smem + off);
     off += sizeof(Vec4<T>) * kRaChunk;
     g.red = reinterpret_cast<float *>(smem + off);
-    off += sizeof(float) * 80;
+    off += sizeof(float) * kRedFloats;
     g.st = reinterpret_cast<RaStage *>(smem + off);
     return g;
 }
 
+// Copies the replica table and each replica's dt and run-away count into
+// shared memory (batches of up to kRepSmem replicas; larger batches read
+// them from global memory at every tile).
 template <typename T>
-__host__ __device__ inline size_t gather_smem_bytes(size_t table_bytes, int tx, int ty, int tz)
+__device__ __forceinline__ void fill_rep_cache(const GatherArgs<T> &a, RepCache *rc)
+{
+    if (a.nrep > kRepSmem) return;
+    for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
+        RepCache c;
+        c.rd = a.reps[r];
+        c.dt = a.sc[r].dt;
+        c.n_ra = a.sc[r].n_ra;
+        c.pad = 0;
+        rc[r] = c;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ TileLoc locate_cached(const GatherArgs<T> &a, const RepCache *rc, int tile, int TX, int TY,
+                                                 int TZ, double &dt, int &nra)
+{
+    TileLoc L;
+    L.rep = a.tile_rep[tile];
+    if (a.nrep <= kRepSmem) {
+        L.rd = rc[L.rep].rd;
+        dt = rc[L.rep].dt;
+        nra = rc[L.rep].n_ra;
+    } else {
+        L.rd = a.reps[L.rep];
+        dt = a.sc[L.rep].dt;
+        nra = a.sc[L.rep].n_ra;
+    }
+    return finish_locate(L, tile, TX, TY, TZ);
+}
+
+// FP32 density tiles are double-buffered (the next tile streams in by
+// cp.async while the current one is computed).  The force pass and the FP64
+// path stage synchronously: they are issue-bound, and the prefetch measured
+// slower there.
+template <typename T>
+__host__ __device__ constexpr int tile_buffers()
+{
+    return sizeof(T) == 4 ? 2 : 1;
+}
+constexpr int kForceBuffers = 1;
+
+template <typename T>
+__host__ __device__ inline size_t gather_smem_bytes(size_t table_bytes, int tx, int ty, int tz, int nbuf)
 {
     size_t off = (table_bytes + 255) & ~(size_t)255;
+    off += sizeof(RepCache) * kRepSmem;
     off += sizeof(float4) * 2 * kNVec;
-    off += tile_smem_bytes<T>(tx, ty, tz);
-    off += sizeof(int4) * kRaChunk + sizeof(Vec4<T>) * kRaChunk + sizeof(float) * 80 + sizeof(RaStage);
+    off += tile_smem_bytes<T>(tx, ty, tz) * nbuf;
+    off += sizeof(int4) * kRaChunk + sizeof(Vec4<T>) * kRaChunk + sizeof(float) * kRedFloats + sizeof(RaStage);
     return off;
+}
+
+// ---------------------------------------------------------------------------
+// asynchronous tile staging (FP32 path): cp.async 4-byte copies of the
+// displacement (and F') of every tile + halo slot straight into shared memory
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int TX, int TY, int TZ, bool WITH_FP>
+__device__ __forceinline__ void issue_tile(const GatherArgs<float> &a, const RepCache *rc, Vec4<float> *sU, int tile)
+{
+    using G = Tile<TX, TY, TZ>;
+    double dt_;
+    int nra_;
+    const TileLoc L = locate_cached(a, rc, tile, TX, TY, TZ, dt_, nra_);
+    for (int q = threadIdx.x; q < 2 * G::PLANE; q += G::NT) {
+        const int p = q & 1;
+        const int r = q >> 1;
+        const int x = r % G::SX;
+        const int yz = r / G::SX;
+        const int y = yz % G::SY;
+        const int z = yz / G::SY;
+        const int gx = wrap_cell(L.c0x - 2 + x, L.rd.nx);
+        const int gy = wrap_cell(L.c0y - 2 + y, L.rd.ny);
+        const int gz = wrap_cell(L.c0z - 2 + z, L.rd.nz);
+        const long long sid = L.rd.site_base + (((long long)gz * L.rd.ny + gy) * L.rd.nx + gx) * 2 + p;
+        Vec4<float> *d = sU + p * G::PLANE + (z * G::SY + y) * G::SX + x;
+        cp_async4(&d->x, a.ux + sid);
+        cp_async4(&d->y, a.uy + sid);
+        cp_async4(&d->z, a.uz + sid);
+        if (WITH_FP) cp_async4(&d->w, a.fp + sid);
+    }
+}
+
+// max |u| over the occupied slots of a staged tile, block-wide
+template <int TX, int TY, int TZ>
+__device__ __forceinline__ float tile_umax(const Vec4<float> *sU, float *sred)
+{
+    using G = Tile<TX, TY, TZ>;
+    float umax2 = 0.f;
+    for (int q = threadIdx.x; q < 2 * G::PLANE; q += G::NT) {
+        const Vec4<float> v = sU[q];
+        const float u2 = v.x * v.x + v.y * v.y + v.z * v.z;
+        if (v.x < 0.5f * kVacant) umax2 = fmaxf(umax2, u2);
+    }
+    for (int o = 16; o > 0; o >>= 1) umax2 = fmaxf(umax2, __shfl_xor_sync(0xffffffffu, umax2, o));
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = umax2;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float w = threadIdx.x < (G::NT >> 5) ? sred[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) w = fmaxf(w, __shfl_xor_sync(0xffffffffu, w, o));
+        if (threadIdx.x == 0) sred[32] = w;
+    }
+    __syncthreads();
+    return sqrtf(sred[32]) * 1.000001f;
 }
 
 // ---------------------------------------------------------------------------
@@ -482,7 +632,7 @@ __host__ __device__ inline size_t gather_smem_bytes(size_t table_bytes, int tx, 
 template <typename T, int SH>
 __device__ __forceinline__ void density_shells(const ShellInfo &shc, const float4 *__restrict__ po,
                                                const Vec4<T> *__restrict__ su, int slot, const Vec4<T> &ui, T lim2, T S,
-                                               int nseg1, const Vec4<T> *__restrict__ tabf, Acc<T> &rho)
+                                               int seglo, int nseg1, const Vec4<T> *__restrict__ tabf, Acc<T> &rho)
 {
     if constexpr (SH < kLVec.nshell) {
         constexpr int KB = kLVec.shell_begin[SH], KE = kLVec.shell_begin[SH + 1];
@@ -499,26 +649,26 @@ __device__ __forceinline__ void density_shells(const ShellInfo &shc, const float
             const T qq = (dx + (T)o.y) * dx + (dy + (T)o.z) * dy + (dz + (T)o.w) * dz;
             if (dense) {
                 T t, rinv;
-                const int seg = shell_arg<T>(sh, qq, S, nseg1, t, rinv);
+                const int seg = shell_arg<T>(sh, qq, S, seglo, nseg1, t, rinv);
                 const Vec4<T> c = tabf[seg];
                 const T v = ((c.x * t + c.y) * t + c.z) * t + c.w;
                 part += qq < sh.thr ? v : (T)0;
             } else if (qq < sh.thr) {
                 T t, rinv;
-                const int seg = shell_arg<T>(sh, qq, S, nseg1, t, rinv);
+                const int seg = shell_arg<T>(sh, qq, S, seglo, nseg1, t, rinv);
                 const Vec4<T> c = tabf[seg];
                 part += ((c.x * t + c.y) * t + c.z) * t + c.w;
             }
         }
         rho.add(part);
-        density_shells<T, SH + 1>(shc, po, su, slot, ui, lim2, S, nseg1, tabf, rho);
+        density_shells<T, SH + 1>(shc, po, su, slot, ui, lim2, S, seglo, nseg1, tabf, rho);
     }
 }
 
 template <typename T, int SH, bool ENERGY>
 __device__ __forceinline__ void force_shells(const ShellInfo &shc, const float4 *__restrict__ po,
                                              const Vec4<T> *__restrict__ su, int slot, const Vec4<T> &ui, T lim2, T S,
-                                             int nseg1, const Vec4<T> *__restrict__ tab0, const Vec2<T> *__restrict__ tab1,
+                                             int seglo, int nseg1, const Vec4<T> *__restrict__ tab0, const Vec2<T> *__restrict__ tab1,
                                              const Vec4<T> *__restrict__ tabphi, Acc<T> &fx, Acc<T> &fy, Acc<T> &fz,
                                              double &ephi)
 {
@@ -537,7 +687,7 @@ __device__ __forceinline__ void force_shells(const ShellInfo &shc, const float4 
             const T qq = (dx + (T)o.y) * dx + (dy + (T)o.z) * dy + (dz + (T)o.w) * dz;
             if (dense || qq < sh.thr) {
                 T t, rinv;
-                const int seg = shell_arg<T>(sh, qq, S, nseg1, t, rinv);
+                const int seg = shell_arg<T>(sh, qq, S, seglo, nseg1, t, rinv);
                 const Vec4<T> c0 = tab0[seg];
                 const Vec2<T> c1 = tab1[seg];
                 const T dfr = (c0.x * t + c0.y) * t + c0.z;
@@ -557,30 +707,79 @@ __device__ __forceinline__ void force_shells(const ShellInfo &shc, const float4 
         fx.add(px);
         fy.add(py);
         fz.add(pz);
-        force_shells<T, SH + 1, ENERGY>(shc, po, su, slot, ui, lim2, S, nseg1, tab0, tab1, tabphi, fx, fy, fz, ephi);
+        force_shells<T, SH + 1, ENERGY>(shc, po, su, slot, ui, lim2, S, seglo, nseg1, tab0, tab1, tabphi, fx, fy, fz, ephi);
     }
+}
+
+// ---------------------------------------------------------------------------
+// run-away pairs inside a tile kernel (Alg. 1 parts 2-3, array side)
+// ---------------------------------------------------------------------------
+// Geometry from the home lattice vector (exact integers, minimum image) plus
+// the two displacements; r is floored at r_floor.  Uses the full global
+// tables (run-away pairs can come closer than any array pair).
+
+template <typename T>
+struct RaPair {
+    bool in;
+    int seg;
+    T t, rinv, rx, ry, rz;
+    bool floor_hit;
+};
+
+template <typename T>
+__device__ __forceinline__ RaPair<T> ra_pair(const GatherArgs<T> &a, const RepDesc &rd, int4 h, const Vec4<T> &uj,
+                                             const Vec4<T> &ui, int sx, int sy, int sz)
+{
+    RaPair<T> P;
+    int nx_ = h.x - sx, ny_ = h.y - sy, nz_ = h.z - sz;
+    const int Lx = 2 * rd.nx, Ly = 2 * rd.ny, Lz = 2 * rd.nz;
+    nx_ -= (nx_ > rd.nx) ? Lx : 0;
+    nx_ += (nx_ < -rd.nx) ? Lx : 0;
+    ny_ -= (ny_ > rd.ny) ? Ly : 0;
+    ny_ += (ny_ < -rd.ny) ? Ly : 0;
+    nz_ -= (nz_ > rd.nz) ? Lz : 0;
+    nz_ += (nz_ < -rd.nz) ? Lz : 0;
+    const T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
+    const T qq = (dx + (T)(2 * nx_)) * dx + (dy + (T)(2 * ny_)) * dy + (dz + (T)(2 * nz_)) * dz;
+    const T r2 = (T)(nx_ * nx_ + ny_ * ny_ + nz_ * nz_) + qq;
+    P.in = r2 < a.rc2;
+    P.rx = dx + (T)nx_;
+    P.ry = dy + (T)ny_;
+    P.rz = dz + (T)nz_;
+    if (P.in) {
+        direct_arg<T>(r2, a.S, a.rfloor2, P.seg, P.t, P.rinv, P.floor_hit);
+        P.seg = clamp_seg<T>(P.seg, a.nseg, P.t);
+    }
+    return P;
 }
 
 // ---------------------------------------------------------------------------
 // density pass: rho_i, F'(rho_i)  (Sec. 2.2 steps 1-2)
 // ---------------------------------------------------------------------------
 // Each shell's terms are summed plainly (at most 24, similar magnitudes)
-// and the shell sums are added with Kahan compensation.
+// and the shell sums are added with Kahan compensation.  One persistent CTA
+// per SM walks the global tile list of all replicas.
 
 template <typename T, int TX, int TY, int TZ, bool ENERGY>
 __global__ void __launch_bounds__(2 * TX * TY * TZ, 1) k_density(const __grid_constant__ GatherArgs<T> a)
 {
     using G = Tile<TX, TY, TZ>;
+    constexpr bool DB = tile_buffers<T>() == 2;
     extern __shared__ __align__(32) unsigned char smem[];
-    const bool tsm = sizeof(T) == 4;
+    // FP32: the part of the f table that array pairs can reach, in shared memory
     const Vec4<T> *tabf = a.tab_f;
-    if (tsm) {
+    size_t tbytes = 0;
+    if constexpr (DB) {
         Vec4<T> *t = reinterpret_cast<Vec4<T> *>(smem);
-        for (int k = threadIdx.x; k < a.nseg; k += G::NT) t[k] = a.tab_f[k];
-        tabf = t;
+        const int nwin = a.nseg - a.seg_lo;
+        for (int k = threadIdx.x; k < nwin; k += G::NT) t[k] = a.tab_f[a.seg_lo + k];
+        tabf = t - a.seg_lo;  // indexed by segment; segments >= seg_lo only
+        tbytes = sizeof(Vec4<T>) * (size_t)nwin;
     }
-    const GatherSmem<T> sm = carve<T, TX, TY, TZ>(smem, tsm ? sizeof(Vec4<T>) * (size_t)a.nseg : 0);
+    const GatherSmem<T> sm = carve<T, TX, TY, TZ>(smem, tbytes, tile_buffers<T>());
     for (int k = threadIdx.x; k < 2 * kNVec; k += G::NT) sm.off[k] = (&a.off[0][0])[k];
+    fill_rep_cache<T>(a, sm.rep);
+    __syncthreads();
 
     // this thread's site within a tile: parity-major, then (z, y, x)
     const int q = threadIdx.x;
@@ -590,55 +789,54 @@ __global__ void __launch_bounds__(2 * TX * TY * TZ, 1) k_density(const __grid_co
     const int slot = p * G::PLANE + ((lz + 2) * G::SY + (ly + 2)) * G::SX + (lx + 2);
     const float4 *po = sm.off + p * kNVec;
     const int nseg1 = a.nseg - 1;
+    const int seglo = DB ? a.seg_lo : 0;
     unsigned st = 0;
-    const int nra = a.sc->n_ra;
+    int buf = 0;
+    if constexpr (DB) {
+        if ((int)blockIdx.x < a.ntiles) issue_tile<TX, TY, TZ, false>(a, sm.rep, sm.u, blockIdx.x);
+        cp_async_commit();
+    }
 
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        const int tix = tile % a.ntx, tiy = (tile / a.ntx) % a.nty, tiz = tile / (a.ntx * a.nty);
-        const int c0x = tix * TX, c0y = tiy * TY, c0z = tiz * TZ;
-        __syncthreads();
-        const T U = stage_tile<T, TX, TY, TZ, false>(a, sm.u, c0x, c0y, c0z, sm.red);
+        double dt_rep;
+        int nra;
+        const TileLoc L = locate_cached(a, sm.rep, tile, TX, TY, TZ, dt_rep, nra);
+        Vec4<T> *cur = sm.u + buf * 2 * G::PLANE;
+        T U;
+        if constexpr (DB) {
+            const int nxt = tile + gridDim.x;
+            if (nxt < a.ntiles) issue_tile<TX, TY, TZ, false>(a, sm.rep, sm.u + (buf ^ 1) * 2 * G::PLANE, nxt);
+            cp_async_commit();
+            cp_async_wait<1>();
+            __syncthreads();
+            U = tile_umax<TX, TY, TZ>(cur, sm.red);
+        } else {
+            __syncthreads();
+            U = stage_tile<T, TX, TY, TZ, false>(a, L, cur, sm.red);
+        }
         const bool has_ra = a.tile_flag[tile] != 0 && nra > 0;
-        const bool inbox = (c0x + lx < a.nx) && (c0y + ly < a.ny) && (c0z + lz < a.nz);
-        const Vec4<T> ui = sm.u[slot];
+        const bool inbox = (L.c0x + lx < L.rd.nx) && (L.c0y + ly < L.rd.ny) && (L.c0z + lz < L.rd.nz);
+        const Vec4<T> ui = cur[slot];
         const bool live = inbox && ui.x < (T)(0.5f * kVacant);
         Acc<T> rho;
         if (live) {
             const T lim = a.rc_lat + sqrt(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + U;
-            const T lim2 = lim * lim;
-            density_shells<T, 0>(a.sh, po, sm.u, slot, ui, lim2, a.S, nseg1, tabf, rho);
+            density_shells<T, 0>(a.sh, po, cur, slot, ui, lim * lim, a.S, seglo, nseg1, tabf, rho);
         }
         if (has_ra) {
             int pos = 0;
             const int sx = 2 * lx + p, sy = 2 * ly + p, sz = 2 * lz + p;
-            const int Lx = 2 * a.nx, Ly = 2 * a.ny, Lz = 2 * a.nz;
             while (true) {
                 __syncthreads();
-                const int cnt = stage_runaways<T, TX, TY, TZ, false>(a, nra, pos, c0x, c0y, c0z, sm.rh, sm.ru, sm.st);
+                const int cnt = stage_runaways<T, TX, TY, TZ, false>(a, L, nra, pos, sm.rh, sm.ru, sm.st);
                 if (cnt == 0) break;
                 if (live) {
                     for (int j = 0; j < cnt; ++j) {
-                        const int4 h = sm.rh[j];
-                        const Vec4<T> uj = sm.ru[j];
-                        int nx_ = h.x - sx, ny_ = h.y - sy, nz_ = h.z - sz;
-                        nx_ -= (nx_ > a.nx) ? Lx : 0;
-                        nx_ += (nx_ < -a.nx) ? Lx : 0;
-                        ny_ -= (ny_ > a.ny) ? Ly : 0;
-                        ny_ += (ny_ < -a.ny) ? Ly : 0;
-                        nz_ -= (nz_ > a.nz) ? Lz : 0;
-                        nz_ += (nz_ < -a.nz) ? Lz : 0;
-                        const T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
-                        const T qq = (dx + (T)(2 * nx_)) * dx + (dy + (T)(2 * ny_)) * dy + (dz + (T)(2 * nz_)) * dz;
-                        const T r2 = (T)(nx_ * nx_ + ny_ * ny_ + nz_ * nz_) + qq;
-                        if (r2 < a.rc2) {
-                            int seg;
-                            T t, rinv;
-                            bool fh;
-                            direct_arg<T>(r2, a.S, a.rfloor2, seg, t, rinv, fh);
-                            seg = clamp_seg<T>(seg, a.nseg, t);
-                            if (fh) st |= kStRfloor;
-                            const Vec4<T> c = tabf[seg];
-                            rho.add(((c.x * t + c.y) * t + c.z) * t + c.w);
+                        const RaPair<T> P = ra_pair<T>(a, L.rd, sm.rh[j], sm.ru[j], ui, sx, sy, sz);
+                        if (P.in) {
+                            if (P.floor_hit) st |= kStRfloor;
+                            const Vec4<T> c = a.tab_f[P.seg];
+                            rho.add(((c.x * P.t + c.y) * P.t + c.z) * P.t + c.w);
                         }
                     }
                 }
@@ -646,7 +844,8 @@ __global__ void __launch_bounds__(2 * TX * TY * TZ, 1) k_density(const __grid_co
             }
         }
         if (live) {
-            const long long sid = (((long long)(c0z + lz) * a.ny + (c0y + ly)) * a.nx + (c0x + lx)) * 2 + p;
+            const long long sid =
+                L.rd.site_base + (((long long)(L.c0z + lz) * L.rd.ny + (L.c0y + ly)) * L.rd.nx + (L.c0x + lx)) * 2 + p;
             const T rh = rho.value();
             T dF;
             const T Fv = embed<T>(a.tab_F, a.nseg, a.Srho, a.rho_max, rh, dF, st);
@@ -656,8 +855,31 @@ __global__ void __launch_bounds__(2 * TX * TY * TZ, 1) k_density(const __grid_co
                 a.e_out[sid] = (double)Fv;
             }
         }
+        if constexpr (DB) {
+            buf ^= 1;
+            __syncthreads();  // every read of cur is done before it is refilled
+        }
     }
-    if (st) atomicOr(&a.sc->status, st);
+    if constexpr (DB) cp_async_wait<0>();
+    if (st) atomicOr(&a.sc[0].status, st);
+}
+
+// Block max of |v|^2 -> one atomicMax of |v| on the replica's accumulator
+// (non-negative doubles order like their bit patterns).  Block-uniform call.
+template <int NT>
+__device__ __forceinline__ void flush_vmax(double vmax2, float *sred, DevScalars *sc)
+{
+    double m = vmax2;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    double *smd = reinterpret_cast<double *>(sred) + 24;  // clear of the floats stage_tile uses
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) smd[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double w = 0.0;
+        for (int k = 0; k < NT / 32; ++k) w = fmax(w, smd[k]);
+        if (w > 0.0) atomicMax(&sc->vacc_bits, (unsigned long long)__double_as_longlong(sqrt(w)));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -668,23 +890,29 @@ template <typename T, int TX, int TY, int TZ, bool ENERGY>
 __global__ void __launch_bounds__(2 * TX * TY * TZ, 1) k_force(const __grid_constant__ GatherArgs<T> a)
 {
     using G = Tile<TX, TY, TZ>;
+    constexpr bool DB = kForceBuffers == 2 && tile_buffers<T>() == 2;
+    constexpr bool TSM = sizeof(T) == 4;  // tables in shared memory
     extern __shared__ __align__(32) unsigned char smem[];
-    const bool tsm = sizeof(T) == 4;
+    // FP32: the part of the f', phi' tables that array pairs can reach
     const Vec4<T> *tab0 = a.tab_d0;
     const Vec2<T> *tab1 = a.tab_d1;
-    if (tsm) {
+    size_t tbytes = 0;
+    if constexpr (TSM) {
+        const int nwin = a.nseg - a.seg_lo;
         Vec4<T> *t0 = reinterpret_cast<Vec4<T> *>(smem);
-        Vec2<T> *t1 = reinterpret_cast<Vec2<T> *>(smem + sizeof(Vec4<T>) * (size_t)a.nseg);
-        for (int k = threadIdx.x; k < a.nseg; k += G::NT) {
-            t0[k] = a.tab_d0[k];
-            t1[k] = a.tab_d1[k];
+        Vec2<T> *t1 = reinterpret_cast<Vec2<T> *>(smem + sizeof(Vec4<T>) * (size_t)nwin);
+        for (int k = threadIdx.x; k < nwin; k += G::NT) {
+            t0[k] = a.tab_d0[a.seg_lo + k];
+            t1[k] = a.tab_d1[a.seg_lo + k];
         }
-        tab0 = t0;
-        tab1 = t1;
+        tab0 = t0 - a.seg_lo;
+        tab1 = t1 - a.seg_lo;
+        tbytes = (sizeof(Vec4<T>) + sizeof(Vec2<T>)) * (size_t)nwin;
     }
-    const GatherSmem<T> sm =
-        carve<T, TX, TY, TZ>(smem, tsm ? (sizeof(Vec4<T>) + sizeof(Vec2<T>)) * (size_t)a.nseg : 0);
+    const GatherSmem<T> sm = carve<T, TX, TY, TZ>(smem, tbytes, DB ? 2 : 1);
     for (int k = threadIdx.x; k < 2 * kNVec; k += G::NT) sm.off[k] = (&a.off[0][0])[k];
+    fill_rep_cache<T>(a, sm.rep);
+    __syncthreads();
 
     const int q = threadIdx.x;
     const int p = q / G::PER_PAR;
@@ -693,69 +921,78 @@ __global__ void __launch_bounds__(2 * TX * TY * TZ, 1) k_force(const __grid_cons
     const int slot = p * G::PLANE + ((lz + 2) * G::SY + (ly + 2)) * G::SX + (lx + 2);
     const float4 *po = sm.off + p * kNVec;
     const int nseg1 = a.nseg - 1;
+    const int seglo = TSM ? a.seg_lo : 0;
     unsigned st = 0;
-    const int nra = a.sc->n_ra;
-    const double hdt = 0.5 * a.sc->dt;
     const T conv = (T)a.acc_conv;
-    double vmax2 = 0.0;
+    int buf = 0;
+    if constexpr (DB) {
+        if ((int)blockIdx.x < a.ntiles) issue_tile<TX, TY, TZ, true>(a, sm.rep, sm.u, blockIdx.x);
+        cp_async_commit();
+    }
 
+    int cur_rep = -1;
+    double vmax2 = 0.0;
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        const int tix = tile % a.ntx, tiy = (tile / a.ntx) % a.nty, tiz = tile / (a.ntx * a.nty);
-        const int c0x = tix * TX, c0y = tiy * TY, c0z = tiz * TZ;
-        __syncthreads();
-        const T U = stage_tile<T, TX, TY, TZ, true>(a, sm.u, c0x, c0y, c0z, sm.red);
+        double dt_rep;
+        int nra;
+        const TileLoc L = locate_cached(a, sm.rep, tile, TX, TY, TZ, dt_rep, nra);
+        if (a.kick && L.rep != cur_rep) {
+            // the block's tiles moved on to another replica: fold the max |v|
+            // gathered so far into the previous one (block-uniform branch)
+            if (cur_rep >= 0) flush_vmax<G::NT>(vmax2, sm.red, a.sc + cur_rep);
+            cur_rep = L.rep;
+            vmax2 = 0.0;
+        }
+        Vec4<T> *cur = sm.u + buf * 2 * G::PLANE;
+        T U;
+        if constexpr (DB) {
+            const int nxt = tile + gridDim.x;
+            if (nxt < a.ntiles) issue_tile<TX, TY, TZ, true>(a, sm.rep, sm.u + (buf ^ 1) * 2 * G::PLANE, nxt);
+            cp_async_commit();
+            cp_async_wait<1>();
+            __syncthreads();
+            U = tile_umax<TX, TY, TZ>(cur, sm.red);
+        } else {
+            __syncthreads();
+            U = stage_tile<T, TX, TY, TZ, true>(a, L, cur, sm.red);
+        }
+        const double hdt = 0.5 * dt_rep;
         const bool has_ra = a.tile_flag[tile] != 0 && nra > 0;
-        const bool inbox = (c0x + lx < a.nx) && (c0y + ly < a.ny) && (c0z + lz < a.nz);
-        const Vec4<T> ui = sm.u[slot];
+        const bool inbox = (L.c0x + lx < L.rd.nx) && (L.c0y + ly < L.rd.ny) && (L.c0z + lz < L.rd.nz);
+        const Vec4<T> ui = cur[slot];
         const bool live = inbox && ui.x < (T)(0.5f * kVacant);
         Acc<T> fx, fy, fz;
         double ephi = 0.0;
         if (live) {
             const T lim = a.rc_lat + sqrt(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + U;
-            const T lim2 = lim * lim;
-            force_shells<T, 0, ENERGY>(a.sh, po, sm.u, slot, ui, lim2, a.S, nseg1, tab0, tab1, a.tab_phi, fx, fy, fz, ephi);
+            force_shells<T, 0, ENERGY>(a.sh, po, cur, slot, ui, lim * lim, a.S, seglo, nseg1, tab0, tab1, a.tab_phi, fx,
+                                       fy, fz, ephi);
         }
         if (has_ra) {
             int pos = 0;
             const int sx = 2 * lx + p, sy = 2 * ly + p, sz = 2 * lz + p;
-            const int Lx = 2 * a.nx, Ly = 2 * a.ny, Lz = 2 * a.nz;
             while (true) {
                 __syncthreads();
-                const int cnt = stage_runaways<T, TX, TY, TZ, true>(a, nra, pos, c0x, c0y, c0z, sm.rh, sm.ru, sm.st);
+                const int cnt = stage_runaways<T, TX, TY, TZ, true>(a, L, nra, pos, sm.rh, sm.ru, sm.st);
                 if (cnt == 0) break;
                 if (live) {
                     for (int j = 0; j < cnt; ++j) {
-                        const int4 h = sm.rh[j];
                         const Vec4<T> uj = sm.ru[j];
-                        int nx_ = h.x - sx, ny_ = h.y - sy, nz_ = h.z - sz;
-                        nx_ -= (nx_ > a.nx) ? Lx : 0;
-                        nx_ += (nx_ < -a.nx) ? Lx : 0;
-                        ny_ -= (ny_ > a.ny) ? Ly : 0;
-                        ny_ += (ny_ < -a.ny) ? Ly : 0;
-                        nz_ -= (nz_ > a.nz) ? Lz : 0;
-                        nz_ += (nz_ < -a.nz) ? Lz : 0;
-                        const T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
-                        const T qq = (dx + (T)(2 * nx_)) * dx + (dy + (T)(2 * ny_)) * dy + (dz + (T)(2 * nz_)) * dz;
-                        const T r2 = (T)(nx_ * nx_ + ny_ * ny_ + nz_ * nz_) + qq;
-                        if (r2 < a.rc2) {
-                            int seg;
-                            T t, rinv;
-                            bool fh;
-                            direct_arg<T>(r2, a.S, a.rfloor2, seg, t, rinv, fh);
-                            seg = clamp_seg<T>(seg, a.nseg, t);
-                            const Vec4<T> c0 = tab0[seg];
-                            const Vec2<T> c1 = tab1[seg];
-                            const T dfr = (c0.x * t + c0.y) * t + c0.z;
-                            const T dph = (c0.w * t + c1.x) * t + c1.y;
+                        const RaPair<T> P = ra_pair<T>(a, L.rd, sm.rh[j], uj, ui, sx, sy, sz);
+                        if (P.in) {
+                            const Vec4<T> c0 = a.tab_d0[P.seg];
+                            const Vec2<T> c1 = a.tab_d1[P.seg];
+                            const T dfr = (c0.x * P.t + c0.y) * P.t + c0.z;
+                            const T dph = (c0.w * P.t + c1.x) * P.t + c1.y;
                             const T coef = (ui.w + uj.w) * dfr + dph;
-                            const T sc_ = fh ? (T)0 : coef * rinv;
-                            if (fh) st |= kStRfloor;
-                            fx.add(sc_ * (dx + (T)nx_));
-                            fy.add(sc_ * (dy + (T)ny_));
-                            fz.add(sc_ * (dz + (T)nz_));
+                            const T sc_ = P.floor_hit ? (T)0 : coef * P.rinv;
+                            if (P.floor_hit) st |= kStRfloor;
+                            fx.add(sc_ * P.rx);
+                            fy.add(sc_ * P.ry);
+                            fz.add(sc_ * P.rz);
                             if (ENERGY) {
-                                const Vec4<T> cp = a.tab_phi[seg];
-                                ephi += 0.5 * (double)(((cp.x * t + cp.y) * t + cp.z) * t + cp.w);
+                                const Vec4<T> cp = a.tab_phi[P.seg];
+                                ephi += 0.5 * (double)(((cp.x * P.t + cp.y) * P.t + cp.z) * P.t + cp.w);
                             }
                         }
                     }
@@ -764,7 +1001,8 @@ __global__ void __launch_bounds__(2 * TX * TY * TZ, 1) k_force(const __grid_cons
             }
         }
         if (live) {
-            const long long sid = (((long long)(c0z + lz) * a.ny + (c0y + ly)) * a.nx + (c0x + lx)) * 2 + p;
+            const long long sid =
+                L.rd.site_base + (((long long)(L.c0z + lz) * L.rd.ny + (L.c0y + ly)) * L.rd.nx + (L.c0x + lx)) * 2 + p;
             T gx, gy, gz;
             if constexpr (sizeof(T) == 4) {
                 gx = fx.value() * conv;
@@ -791,22 +1029,14 @@ __global__ void __launch_bounds__(2 * TX * TY * TZ, 1) k_force(const __grid_cons
             }
             if (ENERGY) a.e_out[sid] += ephi;
         }
-    }
-    if (st) atomicOr(&a.sc->status, st);
-    if (a.kick) {
-        // block max of |v| -> one atomicMax on the (non-negative) double bits
-        double m = vmax2;
-        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        __syncthreads();
-        double *smd = reinterpret_cast<double *>(sm.red);
-        if ((threadIdx.x & 31) == 0) smd[threadIdx.x >> 5] = m;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double w = 0.0;
-            for (int k = 0; k < G::NT / 32; ++k) w = fmax(w, smd[k]);
-            atomicMax(&a.sc->vacc_bits, (unsigned long long)__double_as_longlong(sqrt(w)));
+        if constexpr (DB) {
+            buf ^= 1;
+            __syncthreads();
         }
     }
+    if (a.kick && cur_rep >= 0) flush_vmax<G::NT>(vmax2, sm.red, a.sc + cur_rep);
+    if constexpr (DB) cp_async_wait<0>();
+    if (st) atomicOr(&a.sc[0].status, st);
 }
 
 }  // namespace misa

@@ -7,19 +7,23 @@
 // reassign period, lowest atom id first), the run-away part of Alg. 1 (each
 // run-away gathers over array sites around it and over the other
 // run-aways), PKA insertion (Sec. 5.1), and per-atom read-out.
+//
+// Every kernel serves a whole batch of independent replicas: the replica is
+// blockIdx.y (or one thread / one block per replica for the scalar and list
+// kernels), and each replica has its own timestep, time and run-away list.
 #pragma once
 
 #include "misa_kernels.cuh"
 
 namespace misa {
 
-constexpr int kSortMax = 16384;  // run-away list capacity limit (single-CTA sort)
+constexpr int kSortMax = 16384;  // run-away list capacity limit per replica (single-CTA sort)
 
 template <typename T>
 struct MdArgs {
-    int nx, ny, nz;
-    long long ns;
-    int *sid;                      // atom id per site, -1 vacant
+    const RepDesc *reps;
+    int nrep;
+    int *sid;                      // atom id per site (pooled), -1 vacant
     double *ux, *uy, *uz;          // displacement (lattice units); vacant: kVacant
     T *sx, *sy, *sz;               // precision-T shadow of u read by the gather (aliases u in FP64)
     double *vx, *vy, *vz;
@@ -27,8 +31,8 @@ struct MdArgs {
     T *fp, *rho;
     double *esite;
     int *claim;
-    // run-away list (capacity cap); tmp arrays are the permutation scratch
-    int cap;
+    // run-away lists (pooled; replica r owns [ra_base, ra_base + cap)); the
+    // home site is local to the replica; t_* is the permutation scratch
     int *ra_home, *ra_id;
     double *ra_ux, *ra_uy, *ra_uz;
     T *ra_sx, *ra_sy, *ra_sz;
@@ -40,8 +44,8 @@ struct MdArgs {
     double *t_u[3], *t_v[3];
     T *t_s[3], *t_a[3];
     int *tile_flag;
-    int tx, ty, tz, ntx, nty, ntz;
-    DevScalars *sc;
+    int tx, ty, tz;
+    DevScalars *sc;   // per replica; sc[0].status holds the batch's status bits
     double half;      // a0/2 (A per lattice unit)
     double inv_half;
     double skin2;     // skin^2, lattice units
@@ -51,7 +55,7 @@ struct MdArgs {
     double mass;
 };
 
-// site id <-> lattice coordinates (lattice units: (2cx + p, 2cy + p, 2cz + p))
+// local site id <-> lattice coordinates (lattice units: (2cx + p, 2cy + p, 2cz + p))
 __device__ __forceinline__ void site_lat(long long s, int nx, int ny, int &X, int &Y, int &Z)
 {
     int x2 = (int)(s % (2 * nx));
@@ -72,7 +76,7 @@ __device__ __forceinline__ int wrapi(int a, int n)
 // The hash function of Sec. 3 in lattice units: nearest site of the point
 // P (unwrapped lattice coords).  Candidates: nearest corner (all coords even)
 // and nearest centre (all odd); the closer wins, a tie goes to the lower id.
-// Returns the site id and writes the displacement P - site (lattice units).
+// Returns the (replica-local) site id and writes P - site (lattice units).
 __device__ __forceinline__ long long nearest_site(double Px, double Py, double Pz, int nx, int ny, int nz, double &ux,
                                                   double &uy, double &uz)
 {
@@ -95,14 +99,21 @@ __device__ __forceinline__ long long nearest_site(double Px, double Py, double P
     return ide;
 }
 
+// grid-stride loop over the replica-local sites of replica rd
+#define MISA_SITE_LOOP(rd, s)                                                                     \
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < (rd).ns;            \
+         s += (long long)gridDim.x * blockDim.x)
+
 // ---------------------------------------------------------------------------
-// step bookkeeping
+// step bookkeeping (one thread per replica)
 // ---------------------------------------------------------------------------
 
 template <typename T>
 __global__ void k_begin_step(MdArgs<T> m)
 {
-    DevScalars *sc = m.sc;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m.nrep) return;
+    DevScalars *sc = m.sc + r;
     double vmax = __longlong_as_double((long long)sc->vmax_bits);
     double dt = m.dt_max;
     if (m.dx_max > 0.0 && vmax > 0.0) dt = fmin(m.dt_max, m.dx_max / vmax);
@@ -113,12 +124,14 @@ __global__ void k_begin_step(MdArgs<T> m)
     sc->dirty = 0;
 }
 
-// Empties the run-away list bookkeeping before an explicit state is loaded
-// (step count and time are kept).
+// Empties the run-away bookkeeping before an explicit state is loaded (step
+// count and time are kept).
 template <typename T>
 __global__ void k_reset_list(MdArgs<T> m)
 {
-    DevScalars *sc = m.sc;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m.nrep) return;
+    DevScalars *sc = m.sc + r;
     sc->n_ra = 0;
     sc->n_ra_old = 0;
     sc->n_new = 0;
@@ -131,22 +144,27 @@ __global__ void k_reset_list(MdArgs<T> m)
 template <typename T>
 __global__ void k_end_step(MdArgs<T> m)
 {
-    DevScalars *sc = m.sc;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m.nrep) return;
+    DevScalars *sc = m.sc + r;
     sc->t += sc->dt;
     sc->step += 1;
     sc->vmax_bits = sc->vacc_bits;
 }
 
 // Opening half kick + drift of array atoms (FP64).  An atom leaving its
-// skin is demoted to the run-away list (Alg. 2 part 1, skin reading).
+// skin is demoted to its replica's run-away list (Alg. 2 part 1, skin reading).
 template <typename T>
 __global__ void k_kick_drift(MdArgs<T> m)
 {
-    DevScalars *sc = m.sc;
+    const int r = blockIdx.y;
+    const RepDesc rd = m.reps[r];
+    DevScalars *sc = m.sc + r;
     const double dt = sc->dt, hdt = 0.5 * dt, dtl = dt * m.inv_half;
     const int base = sc->n_ra_old;
     const float skin2f = (float)m.skin2;
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < m.ns; s += (long long)gridDim.x * blockDim.x) {
+    MISA_SITE_LOOP(rd, ls) {
+        const long long s = rd.site_base + ls;
         int id = m.sid[s];
         if (id < 0) continue;
         // FP64 integration; the skin test (a storage decision) in FP32
@@ -163,25 +181,26 @@ __global__ void k_kick_drift(MdArgs<T> m)
         if (out) {
             int slot = atomicAdd(&sc->n_new, 1);
             int j = base + slot;
-            if (j < m.cap) {
+            if (j < rd.cap) {
+                const int g = rd.ra_base + j;
                 int X, Y, Z;
-                site_lat(s, m.nx, m.ny, X, Y, Z);
+                site_lat(ls, rd.nx, rd.ny, X, Y, Z);
                 double rx, ry, rz;
-                long long h = nearest_site(X + ux, Y + uy, Z + uz, m.nx, m.ny, m.nz, rx, ry, rz);
-                m.ra_home[j] = (int)h;
-                m.ra_id[j] = id;
-                m.ra_ux[j] = rx; m.ra_uy[j] = ry; m.ra_uz[j] = rz;
-                m.ra_sx[j] = (T)rx; m.ra_sy[j] = (T)ry; m.ra_sz[j] = (T)rz;
-                m.ra_vx[j] = vx; m.ra_vy[j] = vy; m.ra_vz[j] = vz;
-                m.ra_ax[j] = m.ax[s]; m.ra_ay[j] = m.ay[s]; m.ra_az[j] = m.az[s];
+                long long h = nearest_site(X + ux, Y + uy, Z + uz, rd.nx, rd.ny, rd.nz, rx, ry, rz);
+                m.ra_home[g] = (int)h;
+                m.ra_id[g] = id;
+                m.ra_ux[g] = rx; m.ra_uy[g] = ry; m.ra_uz[g] = rz;
+                m.ra_sx[g] = (T)rx; m.ra_sy[g] = (T)ry; m.ra_sz[g] = (T)rz;
+                m.ra_vx[g] = vx; m.ra_vy[g] = vy; m.ra_vz[g] = vz;
+                m.ra_ax[g] = m.ax[s]; m.ra_ay[g] = m.ay[s]; m.ra_az[g] = m.az[s];
                 m.sid[s] = -1;
                 m.ux[s] = kVacant; m.uy[s] = kVacant; m.uz[s] = kVacant;
-                if ((void *)m.sx != (void *)m.ux) {
-                    m.sx[s] = (T)kVacant; m.sy[s] = (T)kVacant; m.sz[s] = (T)kVacant;
+                if constexpr (sizeof(T) == 4) {
+                    m.sx[s] = kVacant; m.sy[s] = kVacant; m.sz[s] = kVacant;
                 }
                 continue;
             }
-            atomicOr(&sc->status, kStRunawayOverflow);
+            atomicOr(&m.sc[0].status, kStRunawayOverflow);
         }
         m.vx[s] = vx; m.vy[s] = vy; m.vz[s] = vz;
         m.ux[s] = ux; m.uy[s] = uy; m.uz[s] = uz;
@@ -196,24 +215,27 @@ __global__ void k_kick_drift(MdArgs<T> m)
 template <typename T>
 __global__ void k_ra_kick_drift(MdArgs<T> m)
 {
-    DevScalars *sc = m.sc;
+    const int r = blockIdx.y;
+    const RepDesc rd = m.reps[r];
+    DevScalars *sc = m.sc + r;
     const double dt = sc->dt, hdt = 0.5 * dt;
     const int n = sc->n_ra_old;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        double vx = m.ra_vx[j] + hdt * (double)m.ra_ax[j];
-        double vy = m.ra_vy[j] + hdt * (double)m.ra_ay[j];
-        double vz = m.ra_vz[j] + hdt * (double)m.ra_az[j];
+        const int g = rd.ra_base + j;
+        double vx = m.ra_vx[g] + hdt * (double)m.ra_ax[g];
+        double vy = m.ra_vy[g] + hdt * (double)m.ra_ay[g];
+        double vz = m.ra_vz[g] + hdt * (double)m.ra_az[g];
         int X, Y, Z;
-        site_lat(m.ra_home[j], m.nx, m.ny, X, Y, Z);
-        double Px = X + m.ra_ux[j] + dt * vx * m.inv_half;
-        double Py = Y + m.ra_uy[j] + dt * vy * m.inv_half;
-        double Pz = Z + m.ra_uz[j] + dt * vz * m.inv_half;
+        site_lat(m.ra_home[g], rd.nx, rd.ny, X, Y, Z);
+        double Px = X + m.ra_ux[g] + dt * vx * m.inv_half;
+        double Py = Y + m.ra_uy[g] + dt * vy * m.inv_half;
+        double Pz = Z + m.ra_uz[g] + dt * vz * m.inv_half;
         double rx, ry, rz;
-        long long h = nearest_site(Px, Py, Pz, m.nx, m.ny, m.nz, rx, ry, rz);
-        m.ra_home[j] = (int)h;
-        m.ra_ux[j] = rx; m.ra_uy[j] = ry; m.ra_uz[j] = rz;
-        m.ra_sx[j] = (T)rx; m.ra_sy[j] = (T)ry; m.ra_sz[j] = (T)rz;
-        m.ra_vx[j] = vx; m.ra_vy[j] = vy; m.ra_vz[j] = vz;
+        long long h = nearest_site(Px, Py, Pz, rd.nx, rd.ny, rd.nz, rx, ry, rz);
+        m.ra_home[g] = (int)h;
+        m.ra_ux[g] = rx; m.ra_uy[g] = ry; m.ra_uz[g] = rz;
+        m.ra_sx[g] = (T)rx; m.ra_sy[g] = (T)ry; m.ra_sz[g] = (T)rz;
+        m.ra_vx[g] = vx; m.ra_vy[g] = vy; m.ra_vz[g] = vz;
     }
 }
 
@@ -222,14 +244,17 @@ __global__ void k_ra_kick_drift(MdArgs<T> m)
 template <typename T>
 __global__ void k_reassign_claim(MdArgs<T> m, int force)
 {
-    DevScalars *sc = m.sc;
+    const int r = blockIdx.y;
+    const RepDesc rd = m.reps[r];
+    DevScalars *sc = m.sc + r;
     if (!force && (sc->step + 1) % m.reassign_period != 0) return;
-    int n = sc->n_ra_old + min(sc->n_new, m.cap - sc->n_ra_old);
+    int n = sc->n_ra_old + min(sc->n_new, rd.cap - sc->n_ra_old);
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        int h = m.ra_home[j];
-        double u2 = m.ra_ux[j] * m.ra_ux[j] + m.ra_uy[j] * m.ra_uy[j] + m.ra_uz[j] * m.ra_uz[j];
+        const int g = rd.ra_base + j;
+        const long long h = rd.site_base + m.ra_home[g];
+        double u2 = m.ra_ux[g] * m.ra_ux[g] + m.ra_uy[g] * m.ra_uy[g] + m.ra_uz[g] * m.ra_uz[g];
         if (m.sid[h] < 0 && u2 <= m.skin2) {
-            atomicMin(&m.claim[h], m.ra_id[j]);
+            atomicMin(&m.claim[h], m.ra_id[g]);
             sc->dirty = 1;
         }
     }
@@ -238,44 +263,52 @@ __global__ void k_reassign_claim(MdArgs<T> m, int force)
 template <typename T>
 __global__ void k_reassign_promote(MdArgs<T> m, int force)
 {
-    DevScalars *sc = m.sc;
+    const int r = blockIdx.y;
+    const RepDesc rd = m.reps[r];
+    DevScalars *sc = m.sc + r;
     if (!force && (sc->step + 1) % m.reassign_period != 0) return;
-    int n = sc->n_ra_old + min(sc->n_new, m.cap - sc->n_ra_old);
+    int n = sc->n_ra_old + min(sc->n_new, rd.cap - sc->n_ra_old);
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        int h = m.ra_home[j];
-        int id = m.ra_id[j];
+        const int g = rd.ra_base + j;
+        const long long h = rd.site_base + m.ra_home[g];
+        int id = m.ra_id[g];
         if (m.claim[h] == id && m.sid[h] < 0) {
             m.sid[h] = id;
-            m.ux[h] = m.ra_ux[j]; m.uy[h] = m.ra_uy[j]; m.uz[h] = m.ra_uz[j];
-            if ((void *)m.sx != (void *)m.ux) {
-                m.sx[h] = (T)m.ra_ux[j]; m.sy[h] = (T)m.ra_uy[j]; m.sz[h] = (T)m.ra_uz[j];
+            m.ux[h] = m.ra_ux[g]; m.uy[h] = m.ra_uy[g]; m.uz[h] = m.ra_uz[g];
+            if constexpr (sizeof(T) == 4) {
+                m.sx[h] = (T)m.ra_ux[g]; m.sy[h] = (T)m.ra_uy[g]; m.sz[h] = (T)m.ra_uz[g];
             }
-            m.vx[h] = m.ra_vx[j]; m.vy[h] = m.ra_vy[j]; m.vz[h] = m.ra_vz[j];
-            m.ax[h] = m.ra_ax[j]; m.ay[h] = m.ra_ay[j]; m.az[h] = m.ra_az[j];
-            m.ra_id[j] = -1;  // removed from the list by k_ra_sort
+            m.vx[h] = m.ra_vx[g]; m.vy[h] = m.ra_vy[g]; m.vz[h] = m.ra_vz[g];
+            m.ax[h] = m.ra_ax[g]; m.ay[h] = m.ra_ay[g]; m.az[h] = m.ra_az[g];
+            m.ra_id[g] = -1;  // removed from the list by k_ra_sort
         }
     }
 }
 
-// Rebuilds the run-away list in ascending atom id (deterministic order for
-// every gather that scans it), dropping promoted entries; resets the site
-// claims.  One CTA, bitonic sort of (id, index) keys in shared memory.
+// Rebuilds each replica's run-away list in ascending atom id (deterministic
+// order for every gather that scans it), dropping promoted entries; resets
+// the site claims.  One CTA per replica, bitonic sort of (id, index) keys in
+// shared memory.
 template <typename T>
 __global__ void __launch_bounds__(1024) k_ra_sort(MdArgs<T> m)
 {
     extern __shared__ unsigned long long skey[];
-    DevScalars *sc = m.sc;
-    int nnew = sc->n_new;
-    int n = sc->n_ra_old + min(nnew, m.cap - sc->n_ra_old);
+    __shared__ int s_cnt;
+    const int r = blockIdx.x;
+    const RepDesc rd = m.reps[r];
+    DevScalars *sc = m.sc + r;
+    const int nnew = sc->n_new;
+    const int n = sc->n_ra_old + min(nnew, rd.cap - sc->n_ra_old);
     if (nnew == 0 && sc->dirty == 0) return;
+    const int B = rd.ra_base;
     int P = 1;
     while (P < n) P <<= 1;
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         unsigned long long key = ~0ull;
         if (i < n) {
-            int id = m.ra_id[i];
+            int id = m.ra_id[B + i];
             key = ((unsigned long long)(id < 0 ? 0xFFFFFFFFu : (unsigned)id) << 32) | (unsigned)i;
-            m.claim[m.ra_home[i]] = 0x7FFFFFFF;
+            m.claim[rd.site_base + m.ra_home[B + i]] = 0x7FFFFFFF;
         }
         skey[i] = key;
     }
@@ -296,7 +329,6 @@ __global__ void __launch_bounds__(1024) k_ra_sort(MdArgs<T> m)
             __syncthreads();
         }
     }
-    __shared__ int s_cnt;
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
     int local = 0;
@@ -304,28 +336,29 @@ __global__ void __launch_bounds__(1024) k_ra_sort(MdArgs<T> m)
         if ((skey[i] >> 32) != 0xFFFFFFFFull) ++local;
     atomicAdd(&s_cnt, local);
     __syncthreads();
-    int cnt = s_cnt;
+    const int cnt = s_cnt;
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        int src = (int)(skey[i] & 0xFFFFFFFFu);
-        m.t_home[i] = m.ra_home[src];
-        m.t_id[i] = m.ra_id[src];
-        m.t_u[0][i] = m.ra_ux[src]; m.t_u[1][i] = m.ra_uy[src]; m.t_u[2][i] = m.ra_uz[src];
-        m.t_v[0][i] = m.ra_vx[src]; m.t_v[1][i] = m.ra_vy[src]; m.t_v[2][i] = m.ra_vz[src];
-        m.t_s[0][i] = m.ra_sx[src]; m.t_s[1][i] = m.ra_sy[src]; m.t_s[2][i] = m.ra_sz[src];
-        m.t_a[0][i] = m.ra_ax[src]; m.t_a[1][i] = m.ra_ay[src]; m.t_a[2][i] = m.ra_az[src];
+        const int src = B + (int)(skey[i] & 0xFFFFFFFFu), d = B + i;
+        m.t_home[d] = m.ra_home[src];
+        m.t_id[d] = m.ra_id[src];
+        m.t_u[0][d] = m.ra_ux[src]; m.t_u[1][d] = m.ra_uy[src]; m.t_u[2][d] = m.ra_uz[src];
+        m.t_v[0][d] = m.ra_vx[src]; m.t_v[1][d] = m.ra_vy[src]; m.t_v[2][d] = m.ra_vz[src];
+        m.t_s[0][d] = m.ra_sx[src]; m.t_s[1][d] = m.ra_sy[src]; m.t_s[2][d] = m.ra_sz[src];
+        m.t_a[0][d] = m.ra_ax[src]; m.t_a[1][d] = m.ra_ay[src]; m.t_a[2][d] = m.ra_az[src];
     }
     __syncthreads();
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        m.ra_home[i] = m.t_home[i];
-        m.ra_id[i] = m.t_id[i];
-        m.ra_ux[i] = m.t_u[0][i]; m.ra_uy[i] = m.t_u[1][i]; m.ra_uz[i] = m.t_u[2][i];
-        m.ra_vx[i] = m.t_v[0][i]; m.ra_vy[i] = m.t_v[1][i]; m.ra_vz[i] = m.t_v[2][i];
-        m.ra_sx[i] = m.t_s[0][i]; m.ra_sy[i] = m.t_s[1][i]; m.ra_sz[i] = m.t_s[2][i];
-        m.ra_ax[i] = m.t_a[0][i]; m.ra_ay[i] = m.t_a[1][i]; m.ra_az[i] = m.t_a[2][i];
+        const int d = B + i;
+        m.ra_home[d] = m.t_home[d];
+        m.ra_id[d] = m.t_id[d];
+        m.ra_ux[d] = m.t_u[0][d]; m.ra_uy[d] = m.t_u[1][d]; m.ra_uz[d] = m.t_u[2][d];
+        m.ra_vx[d] = m.t_v[0][d]; m.ra_vy[d] = m.t_v[1][d]; m.ra_vz[d] = m.t_v[2][d];
+        m.ra_sx[d] = m.t_s[0][d]; m.ra_sy[d] = m.t_s[1][d]; m.ra_sz[d] = m.t_s[2][d];
+        m.ra_ax[d] = m.t_a[0][d]; m.ra_ay[d] = m.t_a[1][d]; m.ra_az[d] = m.t_a[2][d];
     }
     if (threadIdx.x == 0) {
         sc->n_ra = cnt;
-        if (sc->n_ra_old + nnew > m.cap) atomicOr(&sc->status, kStRunawayOverflow);
+        if (sc->n_ra_old + nnew > rd.cap) atomicOr(&m.sc[0].status, kStRunawayOverflow);
     }
 }
 
@@ -334,13 +367,15 @@ __global__ void __launch_bounds__(1024) k_ra_sort(MdArgs<T> m)
 template <typename T>
 __global__ void k_mark_tiles(MdArgs<T> m)
 {
-    int n = m.sc->n_ra;
+    const int r = blockIdx.y;
+    const RepDesc rd = m.reps[r];
+    const int n = m.sc[r].n_ra;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        int h = m.ra_home[j];
-        int x2 = h % (2 * m.nx);
-        int r = h / (2 * m.nx);
-        int c[3] = {x2 >> 1, r % m.ny, r / m.ny};
-        int nn[3] = {m.nx, m.ny, m.nz};
+        int h = m.ra_home[rd.ra_base + j];
+        int x2 = h % (2 * rd.nx);
+        int q = h / (2 * rd.nx);
+        int c[3] = {x2 >> 1, q % rd.ny, q / rd.ny};
+        int nn[3] = {rd.nx, rd.ny, rd.nz};
         int tt[3] = {m.tx, m.ty, m.tz};
         int tl[3][8], nt[3];
         for (int d = 0; d < 3; ++d) {
@@ -350,13 +385,14 @@ __global__ void k_mark_tiles(MdArgs<T> m)
                 int cc = wrapi(c[d] - 3 + o, nn[d]);
                 int t = cc / tt[d];
                 bool seen = false;
-                for (int q = 0; q < nt[d]; ++q) seen |= (tl[d][q] == t);
+                for (int k = 0; k < nt[d]; ++k) seen |= (tl[d][k] == t);
                 if (!seen) tl[d][nt[d]++] = t;
             }
         }
         for (int a = 0; a < nt[2]; ++a)
             for (int b = 0; b < nt[1]; ++b)
-                for (int e = 0; e < nt[0]; ++e) m.tile_flag[(tl[2][a] * m.nty + tl[1][b]) * m.ntx + tl[0][e]] = 1;
+                for (int e = 0; e < nt[0]; ++e)
+                    m.tile_flag[rd.tile_base + (tl[2][a] * rd.nty + tl[1][b]) * rd.ntx + tl[0][e]] = 1;
     }
 }
 
@@ -366,7 +402,7 @@ __global__ void k_mark_tiles(MdArgs<T> m)
 
 template <typename T>
 struct RaGatherArgs {
-    GatherArgs<T> g;  // tables, box, site arrays
+    GatherArgs<T> g;  // tables, replica table, site arrays
     const int *sid;
     const T *ra_sx, *ra_sy, *ra_sz;
     T *ra_fp, *ra_rho;
@@ -383,37 +419,41 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
-// mode 0: density (+F, F'), mode 1: force (+kick)
+// mode 0: density (+F, F'), mode 1: force (+kick); grid.y = replica
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_ra_gather(const __grid_constant__ RaGatherArgs<T> ra)
 {
     const GatherArgs<T> &a = ra.g;
-    const int n = a.sc->n_ra;
+    const int rep = blockIdx.y;
+    const RepDesc rd = a.reps[rep];
+    DevScalars *scr = a.sc + rep;
+    const int n = scr->n_ra;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const double hdt = 0.5 * a.sc->dt;
+    const double hdt = 0.5 * scr->dt;
+    const int B = rd.ra_base;
     unsigned st = 0;
     double vmax2 = 0.0;
-    const int Lx = 2 * a.nx, Ly = 2 * a.ny, Lz = 2 * a.nz;
+    const int Lx = 2 * rd.nx, Ly = 2 * rd.ny, Lz = 2 * rd.nz;
     for (int j = warp; j < n; j += nwarps) {
-        int h = a.ra_home[j];
+        int h = a.ra_home[B + j];
         int X, Y, Z;
-        site_lat(h, a.nx, a.ny, X, Y, Z);
+        site_lat(h, rd.nx, rd.ny, X, Y, Z);
         const int hp = X & 1;
         const int hcx = X >> 1, hcy = (Y - hp) >> 1, hcz = (Z - hp) >> 1;
-        T ujx = ra.ra_sx[j], ujy = ra.ra_sy[j], ujz = ra.ra_sz[j];
-        T fpj = MODE == 1 ? ra.ra_fp[j] : (T)0;
+        T ujx = ra.ra_sx[B + j], ujy = ra.ra_sy[B + j], ujz = ra.ra_sz[B + j];
+        T fpj = MODE == 1 ? ra.ra_fp[B + j] : (T)0;
         Acc<T> s0, s1, s2;
         double ephi = 0.0;
-        const int wx = a.nx < 7 ? a.nx : 7, wy = a.ny < 7 ? a.ny : 7, wz = a.nz < 7 ? a.nz : 7;
+        const int wx = rd.nx < 7 ? rd.nx : 7, wy = rd.ny < 7 ? rd.ny : 7, wz = rd.nz < 7 ? rd.nz : 7;
         const int W = wx * wy * wz * 2;
         for (int c = lane; c < W; c += 32) {
             int q = c & 1;
-            int r = c >> 1;
-            int ox = r % wx, oy = (r / wx) % wy, oz = r / (wx * wy);
+            int rr = c >> 1;
+            int ox = rr % wx, oy = (rr / wx) % wy, oz = rr / (wx * wy);
             int cx = hcx - 3 + ox, cy = hcy - 3 + oy, cz = hcz - 3 + oz;
-            long long s = (((long long)wrapi(cz, a.nz) * a.ny + wrapi(cy, a.ny)) * a.nx + wrapi(cx, a.nx)) * 2 + q;
+            long long s = rd.site_base + (((long long)wrapi(cz, rd.nz) * rd.ny + wrapi(cy, rd.ny)) * rd.nx + wrapi(cx, rd.nx)) * 2 + q;
             if (ra.sid[s] < 0) continue;
             int nx_ = 2 * cx + q - X, ny_ = 2 * cy + q - Y, nz_ = 2 * cz + q - Z;
             T dx = a.ux[s] - ujx, dy = a.uy[s] - ujy, dz = a.uz[s] - ujz;
@@ -449,15 +489,15 @@ __global__ void __launch_bounds__(256) k_ra_gather(const __grid_constant__ RaGat
         for (int k = lane; k < n; k += 32) {
             if (k == j) continue;
             int Xk, Yk, Zk;
-            site_lat(a.ra_home[k], a.nx, a.ny, Xk, Yk, Zk);
+            site_lat(a.ra_home[B + k], rd.nx, rd.ny, Xk, Yk, Zk);
             int nx_ = Xk - X, ny_ = Yk - Y, nz_ = Zk - Z;
-            nx_ -= (nx_ > a.nx) ? Lx : 0;
-            nx_ += (nx_ < -a.nx) ? Lx : 0;
-            ny_ -= (ny_ > a.ny) ? Ly : 0;
-            ny_ += (ny_ < -a.ny) ? Ly : 0;
-            nz_ -= (nz_ > a.nz) ? Lz : 0;
-            nz_ += (nz_ < -a.nz) ? Lz : 0;
-            T dx = ra.ra_sx[k] - ujx, dy = ra.ra_sy[k] - ujy, dz = ra.ra_sz[k] - ujz;
+            nx_ -= (nx_ > rd.nx) ? Lx : 0;
+            nx_ += (nx_ < -rd.nx) ? Lx : 0;
+            ny_ -= (ny_ > rd.ny) ? Ly : 0;
+            ny_ += (ny_ < -rd.ny) ? Ly : 0;
+            nz_ -= (nz_ > rd.nz) ? Lz : 0;
+            nz_ += (nz_ < -rd.nz) ? Lz : 0;
+            T dx = ra.ra_sx[B + k] - ujx, dy = ra.ra_sy[B + k] - ujy, dz = ra.ra_sz[B + k] - ujz;
             T qq = (dx + (T)(2 * nx_)) * dx + (dy + (T)(2 * ny_)) * dy + (dz + (T)(2 * nz_)) * dz;
             T r2 = (T)(nx_ * nx_ + ny_ * ny_ + nz_ * nz_) + qq;
             if (r2 < a.rc2) {
@@ -475,7 +515,7 @@ __global__ void __launch_bounds__(256) k_ra_gather(const __grid_constant__ RaGat
                     Vec2<T> c1 = a.tab_d1[seg];
                     T dfr = (c0.x * t + c0.y) * t + c0.z;
                     T dph = (c0.w * t + c1.x) * t + c1.y;
-                    T coef = (fpj + ra.ra_fp[k]) * dfr + dph;
+                    T coef = (fpj + ra.ra_fp[B + k]) * dfr + dph;
                     T sc = fh ? (T)0 : coef * rinv;
                     s0.add(sc * (dx + (T)nx_));
                     s1.add(sc * (dy + (T)ny_));
@@ -492,10 +532,10 @@ __global__ void __launch_bounds__(256) k_ra_gather(const __grid_constant__ RaGat
             if (lane == 0) {
                 T dF;
                 T Fv = embed<T>(a.tab_F, a.nseg, a.Srho, a.rho_max, rh, dF, st);
-                ra.ra_fp[j] = dF;
+                ra.ra_fp[B + j] = dF;
                 if (ra.energy) {
-                    ra.ra_rho[j] = rh;
-                    ra.ra_e[j] = (double)Fv;
+                    ra.ra_rho[B + j] = rh;
+                    ra.ra_e[B + j] = (double)Fv;
                 }
             }
         } else {
@@ -504,41 +544,43 @@ __global__ void __launch_bounds__(256) k_ra_gather(const __grid_constant__ RaGat
             if (lane == 0) {
                 double conv = a.acc_conv;
                 double gx = (double)fx * conv, gy = (double)fy * conv, gz = (double)fz * conv;
-                ra.ra_ax[j] = (T)gx;
-                ra.ra_ay[j] = (T)gy;
-                ra.ra_az[j] = (T)gz;
+                ra.ra_ax[B + j] = (T)gx;
+                ra.ra_ay[B + j] = (T)gy;
+                ra.ra_az[B + j] = (T)gz;
                 if (!isfinite(gx) || !isfinite(gy) || !isfinite(gz)) st |= kStNonfinite;
                 if (a.kick) {
-                    double vx = ra.ra_vx[j] + hdt * (double)(T)gx;
-                    double vy = ra.ra_vy[j] + hdt * (double)(T)gy;
-                    double vz = ra.ra_vz[j] + hdt * (double)(T)gz;
-                    ra.ra_vx[j] = vx;
-                    ra.ra_vy[j] = vy;
-                    ra.ra_vz[j] = vz;
+                    double vx = ra.ra_vx[B + j] + hdt * (double)(T)gx;
+                    double vy = ra.ra_vy[B + j] + hdt * (double)(T)gy;
+                    double vz = ra.ra_vz[B + j] + hdt * (double)(T)gz;
+                    ra.ra_vx[B + j] = vx;
+                    ra.ra_vy[B + j] = vy;
+                    ra.ra_vz[B + j] = vz;
                     double v2 = vx * vx + vy * vy + vz * vz;
                     vmax2 = v2 > vmax2 ? v2 : vmax2;
                 }
-                if (ra.energy) ra.ra_e[j] += eph;
+                if (ra.energy) ra.ra_e[B + j] += eph;
             }
         }
     }
-    if (st) atomicOr(&a.sc->status, st);
+    if (st) atomicOr(&a.sc[0].status, st);
     if (MODE == 1 && a.kick && lane == 0 && vmax2 > 0.0)
-        atomicMax(&a.sc->vacc_bits, (unsigned long long)__double_as_longlong(sqrt(vmax2)));
+        atomicMax(&scr->vacc_bits, (unsigned long long)__double_as_longlong(sqrt(vmax2)));
 }
 
 // ---------------------------------------------------------------------------
-// state set-up and read-out
+// state set-up and read-out (grid.y = replica)
 // ---------------------------------------------------------------------------
 
 template <typename T>
 __global__ void k_init_crystal(MdArgs<T> m)
 {
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < m.ns; s += (long long)gridDim.x * blockDim.x) {
+    const RepDesc rd = m.reps[blockIdx.y];
+    MISA_SITE_LOOP(rd, ls) {
+        const long long s = rd.site_base + ls;
         m.sid[s] = (int)s;
         m.ux[s] = 0.0; m.uy[s] = 0.0; m.uz[s] = 0.0;
-        if ((void *)m.sx != (void *)m.ux) {
-            m.sx[s] = (T)0; m.sy[s] = (T)0; m.sz[s] = (T)0;
+        if constexpr (sizeof(T) == 4) {
+            m.sx[s] = 0.f; m.sy[s] = 0.f; m.sz[s] = 0.f;
         }
         m.vx[s] = 0.0; m.vy[s] = 0.0; m.vz[s] = 0.0;
         m.ax[s] = (T)0; m.ay[s] = (T)0; m.az[s] = (T)0;
@@ -549,62 +591,72 @@ __global__ void k_init_crystal(MdArgs<T> m)
 template <typename T>
 __global__ void k_clear_sites(MdArgs<T> m)
 {
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < m.ns; s += (long long)gridDim.x * blockDim.x) {
+    const RepDesc rd = m.reps[blockIdx.y];
+    MISA_SITE_LOOP(rd, ls) {
+        const long long s = rd.site_base + ls;
         m.sid[s] = -1;
         m.ux[s] = kVacant; m.uy[s] = kVacant; m.uz[s] = kVacant;
-        if ((void *)m.sx != (void *)m.ux) {
-            m.sx[s] = (T)kVacant; m.sy[s] = (T)kVacant; m.sz[s] = (T)kVacant;
+        if constexpr (sizeof(T) == 4) {
+            m.sx[s] = kVacant; m.sy[s] = kVacant; m.sz[s] = kVacant;
         }
         m.ax[s] = (T)0; m.ay[s] = (T)0; m.az[s] = (T)0;
         m.claim[s] = 0x7FFFFFFF;
     }
 }
 
-// Hash every atom of an explicit configuration (x: 3 natoms, A) to its
-// nearest site; atoms within the skin claim the site (lowest id wins).
+// Hash every atom of an explicit configuration (x: 3 natoms, A) to the
+// nearest site of its replica's box; atoms within the skin claim the site
+// (lowest id wins).  Atom i of replica r is i in [site_base, site_base + ns).
 template <typename T>
-__global__ void k_state_claim(MdArgs<T> m, const double *x, long long natoms, double Lx, double Ly, double Lz,
-                              int *home, double *rel)
+__global__ void k_state_claim(MdArgs<T> m, const double *x, int *home, double *rel)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < natoms; i += (long long)gridDim.x * blockDim.x) {
+    const RepDesc rd = m.reps[blockIdx.y];
+    const double L[3] = {rd.nx * 2.0 * m.half, rd.ny * 2.0 * m.half, rd.nz * 2.0 * m.half};
+    MISA_SITE_LOOP(rd, li) {
+        const long long i = rd.site_base + li;
         double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
-        px -= Lx * floor(px / Lx);
-        py -= Ly * floor(py / Ly);
-        pz -= Lz * floor(pz / Lz);
+        px -= L[0] * floor(px / L[0]);
+        py -= L[1] * floor(py / L[1]);
+        pz -= L[2] * floor(pz / L[2]);
         double rx, ry, rz;
-        long long h = nearest_site(px * m.inv_half, py * m.inv_half, pz * m.inv_half, m.nx, m.ny, m.nz, rx, ry, rz);
+        long long h = nearest_site(px * m.inv_half, py * m.inv_half, pz * m.inv_half, rd.nx, rd.ny, rd.nz, rx, ry, rz);
         home[i] = (int)h;
         rel[3 * i] = rx; rel[3 * i + 1] = ry; rel[3 * i + 2] = rz;
-        if (rx * rx + ry * ry + rz * rz <= m.skin2) atomicMin(&m.claim[h], (int)i);
+        if (rx * rx + ry * ry + rz * rz <= m.skin2) atomicMin(&m.claim[rd.site_base + h], (int)i);
     }
 }
 
 template <typename T>
-__global__ void k_state_place(MdArgs<T> m, const double *v, long long natoms, const int *home, const double *rel)
+__global__ void k_state_place(MdArgs<T> m, const double *v, const int *home, const double *rel)
 {
-    DevScalars *sc = m.sc;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < natoms; i += (long long)gridDim.x * blockDim.x) {
-        int h = home[i];
+    const int r = blockIdx.y;
+    const RepDesc rd = m.reps[r];
+    DevScalars *sc = m.sc + r;
+    MISA_SITE_LOOP(rd, li) {
+        const long long i = rd.site_base + li;
+        const int h = home[i];
+        const long long hs = rd.site_base + h;
         double rx = rel[3 * i], ry = rel[3 * i + 1], rz = rel[3 * i + 2];
         double vx = v ? v[3 * i] : 0.0, vy = v ? v[3 * i + 1] : 0.0, vz = v ? v[3 * i + 2] : 0.0;
-        if (m.claim[h] == (int)i) {
-            m.sid[h] = (int)i;
-            m.ux[h] = rx; m.uy[h] = ry; m.uz[h] = rz;
-            if ((void *)m.sx != (void *)m.ux) {
-                m.sx[h] = (T)rx; m.sy[h] = (T)ry; m.sz[h] = (T)rz;
+        if (m.claim[hs] == (int)i) {
+            m.sid[hs] = (int)i;
+            m.ux[hs] = rx; m.uy[hs] = ry; m.uz[hs] = rz;
+            if constexpr (sizeof(T) == 4) {
+                m.sx[hs] = (T)rx; m.sy[hs] = (T)ry; m.sz[hs] = (T)rz;
             }
-            m.vx[h] = vx; m.vy[h] = vy; m.vz[h] = vz;
+            m.vx[hs] = vx; m.vy[hs] = vy; m.vz[hs] = vz;
         } else {
             int j = atomicAdd(&sc->n_new, 1);
-            if (j < m.cap) {
-                m.ra_home[j] = h;
-                m.ra_id[j] = (int)i;
-                m.ra_ux[j] = rx; m.ra_uy[j] = ry; m.ra_uz[j] = rz;
-                m.ra_sx[j] = (T)rx; m.ra_sy[j] = (T)ry; m.ra_sz[j] = (T)rz;
-                m.ra_vx[j] = vx; m.ra_vy[j] = vy; m.ra_vz[j] = vz;
-                m.ra_ax[j] = (T)0; m.ra_ay[j] = (T)0; m.ra_az[j] = (T)0;
+            if (j < rd.cap) {
+                const int g = rd.ra_base + j;
+                m.ra_home[g] = h;
+                m.ra_id[g] = (int)i;
+                m.ra_ux[g] = rx; m.ra_uy[g] = ry; m.ra_uz[g] = rz;
+                m.ra_sx[g] = (T)rx; m.ra_sy[g] = (T)ry; m.ra_sz[g] = (T)rz;
+                m.ra_vx[g] = vx; m.ra_vy[g] = vy; m.ra_vz[g] = vz;
+                m.ra_ax[g] = (T)0; m.ra_ay[g] = (T)0; m.ra_az[g] = (T)0;
             } else {
-                atomicOr(&sc->status, kStRunawayOverflow);
+                atomicOr(&m.sc[0].status, kStRunawayOverflow);
             }
         }
     }
@@ -613,16 +665,19 @@ __global__ void k_state_place(MdArgs<T> m, const double *v, long long natoms, co
 template <typename T>
 __global__ void k_set_velocities(MdArgs<T> m, const double *v)
 {
-    long long n = m.ns;
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+    const int r = blockIdx.y;
+    const RepDesc rd = m.reps[r];
+    MISA_SITE_LOOP(rd, ls) {
+        const long long s = rd.site_base + ls;
         int id = m.sid[s];
         if (id < 0) continue;
         m.vx[s] = v[3LL * id]; m.vy[s] = v[3LL * id + 1]; m.vz[s] = v[3LL * id + 2];
     }
-    int nra = m.sc->n_ra;
+    int nra = m.sc[r].n_ra;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nra; j += gridDim.x * blockDim.x) {
-        int id = m.ra_id[j];
-        m.ra_vx[j] = v[3LL * id]; m.ra_vy[j] = v[3LL * id + 1]; m.ra_vz[j] = v[3LL * id + 2];
+        const int g = rd.ra_base + j;
+        int id = m.ra_id[g];
+        m.ra_vx[g] = v[3LL * id]; m.ra_vy[g] = v[3LL * id + 1]; m.ra_vz[g] = v[3LL * id + 2];
     }
 }
 
@@ -630,51 +685,63 @@ __global__ void k_set_velocities(MdArgs<T> m, const double *v)
 template <typename T>
 __global__ void k_pka(MdArgs<T> m, int id, double vx, double vy, double vz)
 {
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < m.ns; s += (long long)gridDim.x * blockDim.x) {
+    const int r = blockIdx.y;
+    const RepDesc rd = m.reps[r];
+    MISA_SITE_LOOP(rd, ls) {
+        const long long s = rd.site_base + ls;
         if (m.sid[s] == id) {
             m.vx[s] = vx; m.vy[s] = vy; m.vz[s] = vz;
         }
     }
-    int nra = m.sc->n_ra;
+    int nra = m.sc[r].n_ra;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nra; j += gridDim.x * blockDim.x) {
-        if (m.ra_id[j] == id) {
-            m.ra_vx[j] = vx; m.ra_vy[j] = vy; m.ra_vz[j] = vz;
+        const int g = rd.ra_base + j;
+        if (m.ra_id[g] == id) {
+            m.ra_vx[g] = vx; m.ra_vy[g] = vy; m.ra_vz[g] = vz;
         }
     }
 }
 
-// max |v| over all atoms into vmax_bits (used after state changes).
+// max |v| of every replica into its vmax_bits (used after state changes).
 template <typename T>
 __global__ void k_vmax(MdArgs<T> m)
 {
+    const int r = blockIdx.y;
+    const RepDesc rd = m.reps[r];
     double w = 0.0;
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < m.ns; s += (long long)gridDim.x * blockDim.x) {
+    MISA_SITE_LOOP(rd, ls) {
+        const long long s = rd.site_base + ls;
         if (m.sid[s] < 0) continue;
         double v2 = m.vx[s] * m.vx[s] + m.vy[s] * m.vy[s] + m.vz[s] * m.vz[s];
         w = v2 > w ? v2 : w;
     }
-    int nra = m.sc->n_ra;
+    int nra = m.sc[r].n_ra;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nra; j += gridDim.x * blockDim.x) {
-        double v2 = m.ra_vx[j] * m.ra_vx[j] + m.ra_vy[j] * m.ra_vy[j] + m.ra_vz[j] * m.ra_vz[j];
+        const int g = rd.ra_base + j;
+        double v2 = m.ra_vx[g] * m.ra_vx[g] + m.ra_vy[g] * m.ra_vy[g] + m.ra_vz[g] * m.ra_vz[g];
         w = v2 > w ? v2 : w;
     }
     for (int o = 16; o > 0; o >>= 1) w = fmax(w, __shfl_xor_sync(0xffffffffu, w, o));
     if ((threadIdx.x & 31) == 0 && w > 0.0)
-        atomicMax(&m.sc->vmax_bits, (unsigned long long)__double_as_longlong(sqrt(w)));
+        atomicMax(&m.sc[r].vmax_bits, (unsigned long long)__double_as_longlong(sqrt(w)));
 }
 
-// Per-atom read-out: kind 0 positions (A, wrapped), 1 velocities, 2 forces
-// (eV/A), 3 density, 4 per-atom energy.  out is indexed by atom id.
+// Per-atom read-out: kind 0 positions (A, wrapped into the replica's box),
+// 1 velocities, 2 forces (eV/A), 3 density, 4 per-atom energy.  out is
+// indexed by atom id.
 template <typename T>
-__global__ void k_scatter(MdArgs<T> m, int kind, double *out, double Lx, double Ly, double Lz)
+__global__ void k_scatter(MdArgs<T> m, int kind, double *out)
 {
-    const double L[3] = {Lx, Ly, Lz};
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < m.ns; s += (long long)gridDim.x * blockDim.x) {
+    const int r = blockIdx.y;
+    const RepDesc rd = m.reps[r];
+    const double L[3] = {rd.nx * 2.0 * m.half, rd.ny * 2.0 * m.half, rd.nz * 2.0 * m.half};
+    MISA_SITE_LOOP(rd, ls) {
+        const long long s = rd.site_base + ls;
         int id = m.sid[s];
         if (id < 0) continue;
         if (kind == 0) {
             int X, Y, Z;
-            site_lat(s, m.nx, m.ny, X, Y, Z);
+            site_lat(ls, rd.nx, rd.ny, X, Y, Z);
             double P[3] = {(X + m.ux[s]) * m.half, (Y + m.uy[s]) * m.half, (Z + m.uz[s]) * m.half};
             for (int d = 0; d < 3; ++d) out[3LL * id + d] = P[d] - L[d] * floor(P[d] / L[d]);
         } else if (kind == 1) {
@@ -689,42 +756,48 @@ __global__ void k_scatter(MdArgs<T> m, int kind, double *out, double Lx, double 
             out[id] = m.esite[s];
         }
     }
-    int nra = m.sc->n_ra;
+    int nra = m.sc[r].n_ra;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nra; j += gridDim.x * blockDim.x) {
-        int id = m.ra_id[j];
+        const int g = rd.ra_base + j;
+        int id = m.ra_id[g];
         if (kind == 0) {
             int X, Y, Z;
-            site_lat(m.ra_home[j], m.nx, m.ny, X, Y, Z);
-            double P[3] = {(X + m.ra_ux[j]) * m.half, (Y + m.ra_uy[j]) * m.half, (Z + m.ra_uz[j]) * m.half};
+            site_lat(m.ra_home[g], rd.nx, rd.ny, X, Y, Z);
+            double P[3] = {(X + m.ra_ux[g]) * m.half, (Y + m.ra_uy[g]) * m.half, (Z + m.ra_uz[g]) * m.half};
             for (int d = 0; d < 3; ++d) out[3LL * id + d] = P[d] - L[d] * floor(P[d] / L[d]);
         } else if (kind == 1) {
-            out[3LL * id] = m.ra_vx[j]; out[3LL * id + 1] = m.ra_vy[j]; out[3LL * id + 2] = m.ra_vz[j];
+            out[3LL * id] = m.ra_vx[g]; out[3LL * id + 1] = m.ra_vy[g]; out[3LL * id + 2] = m.ra_vz[g];
         } else if (kind == 2) {
-            out[3LL * id] = (double)m.ra_ax[j] / m.acc_conv;
-            out[3LL * id + 1] = (double)m.ra_ay[j] / m.acc_conv;
-            out[3LL * id + 2] = (double)m.ra_az[j] / m.acc_conv;
+            out[3LL * id] = (double)m.ra_ax[g] / m.acc_conv;
+            out[3LL * id + 1] = (double)m.ra_ay[g] / m.acc_conv;
+            out[3LL * id + 2] = (double)m.ra_az[g] / m.acc_conv;
         } else if (kind == 3) {
-            out[id] = (double)m.ra_rho[j];
+            out[id] = (double)m.ra_rho[g];
         } else {
-            out[id] = m.ra_e[j];
+            out[id] = m.ra_e[g];
         }
     }
 }
 
-// Deterministic FP64 sums: potential energy (kind 0) or kinetic energy in
-// amu A^2/fs^2 (kind 1) over sites and run-aways.  Stage 1 writes one
-// partial per block; stage 2 (one block) adds the partials in order.
+// Deterministic FP64 sums per replica: potential energy (kind 0) or sum of
+// |v|^2 (kind 1) over sites and run-aways.  Stage 1 writes one partial per
+// (replica, block); stage 2 (one block per replica) adds them in order.
 template <typename T>
 __global__ void k_sum_stage1(MdArgs<T> m, int kind, double *partial)
 {
+    const int r = blockIdx.y;
+    const RepDesc rd = m.reps[r];
     double acc = 0.0;
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < m.ns; s += (long long)gridDim.x * blockDim.x) {
+    MISA_SITE_LOOP(rd, ls) {
+        const long long s = rd.site_base + ls;
         if (m.sid[s] < 0) continue;
         acc += kind == 0 ? m.esite[s] : (m.vx[s] * m.vx[s] + m.vy[s] * m.vy[s] + m.vz[s] * m.vz[s]);
     }
-    int nra = m.sc->n_ra;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nra; j += gridDim.x * blockDim.x)
-        acc += kind == 0 ? m.ra_e[j] : (m.ra_vx[j] * m.ra_vx[j] + m.ra_vy[j] * m.ra_vy[j] + m.ra_vz[j] * m.ra_vz[j]);
+    int nra = m.sc[r].n_ra;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nra; j += gridDim.x * blockDim.x) {
+        const int g = rd.ra_base + j;
+        acc += kind == 0 ? m.ra_e[g] : (m.ra_vx[g] * m.ra_vx[g] + m.ra_vy[g] * m.ra_vy[g] + m.ra_vz[g] * m.ra_vz[g]);
+    }
     __shared__ double sw[32];
     acc = warp_sum<double>(acc);
     if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
@@ -732,33 +805,37 @@ __global__ void k_sum_stage1(MdArgs<T> m, int kind, double *partial)
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sw[k];
-        partial[blockIdx.x] = t;
+        partial[(size_t)r * gridDim.x + blockIdx.x] = t;
     }
 }
 
 __global__ void k_sum_stage2(const double *partial, int n, double *out)
 {
     __shared__ double sw[32];
+    const double *pr = partial + (size_t)blockIdx.x * n;
     double acc = 0.0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partial[k];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) acc += pr[k];
     acc = warp_sum<double>(acc);
     if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sw[k];
-        *out = t;
+        out[blockIdx.x] = t;
     }
 }
 
-// Site map read-out (storage check).
+// Site map read-out (storage check): atom per site; run-away ids at their
+// pooled slots.
 template <typename T>
 __global__ void k_site_map(MdArgs<T> m, long long *site_atom, long long *ra_ids)
 {
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < m.ns; s += (long long)gridDim.x * blockDim.x)
-        site_atom[s] = m.sid[s];
-    int nra = m.sc->n_ra;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nra; j += gridDim.x * blockDim.x) ra_ids[j] = m.ra_id[j];
+    const int r = blockIdx.y;
+    const RepDesc rd = m.reps[r];
+    MISA_SITE_LOOP(rd, ls) site_atom[rd.site_base + ls] = m.sid[rd.site_base + ls];
+    int nra = m.sc[r].n_ra;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nra; j += gridDim.x * blockDim.x)
+        ra_ids[rd.ra_base + j] = m.ra_id[rd.ra_base + j];
 }
 
 }  // namespace misa

@@ -97,6 +97,18 @@ def lib():
         L.misa_load.argtypes = [C.c_void_p, C.c_char_p]
         L.misa_timing_enable.argtypes = [C.c_void_p, C.c_int]
         L.misa_timing_get.argtypes = [C.c_void_p, _D, _I64]
+        L.misa_create_batch.argtypes = [C.POINTER(Params), C.c_int32, C.POINTER(C.c_int32), C.c_void_p,
+                                        C.POINTER(C.c_void_p)]
+        L.misa_replica_count.argtypes = [C.c_void_p]
+        L.misa_replica_info.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), _I64, _I64]
+        L.misa_insert_pka_replica.argtypes = [C.c_void_p, C.c_int32, C.c_double, _D]
+        L.misa_replica_stats.argtypes = [C.c_void_p, C.c_int32, C.POINTER(Stats)]
+        L.misa_replica_energies.argtypes = [C.c_void_p, _D, _D]
+        L.misa_set_graphs.argtypes = [C.c_void_p, C.c_int]
+        L.misa_tile_current.argtypes = [C.c_void_p]
+        L.misa_eam_forces_static.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                             C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
+                                             C.c_void_p, C.c_void_p]
         L.misa_tile_count.restype = C.c_int
         L.misa_tile_shape.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         _lib = L
@@ -148,13 +160,19 @@ class _TorchAllocator:
 
 
 class Sim:
-    """One periodic bcc crystal on the GPU (a misa_sim handle)."""
+    """Periodic bcc crystals on the GPU (a misa_sim handle): one box of
+    nx x ny x nz cells, or a batch of independent replicas when ``replicas``
+    lists their (nx, ny, nz)."""
 
-    def __init__(self, pot: synth.Potential, nx, ny=None, nz=None, precision="fp32", a0=synth.A0_FE,
+    def __init__(self, pot: synth.Potential, nx=None, ny=None, nz=None, precision="fp32", a0=synth.A0_FE,
                  mass=synth.MASS_FE, skin=0.6, reassign_period=10, dt_max=1.0, dx_max=0.0,
-                 runaway_capacity=0, tile=0, stream=None, torch_memory=True):
-        ny = nx if ny is None else ny
-        nz = nx if nz is None else nz
+                 runaway_capacity=0, tile=0, stream=None, torch_memory=True, replicas=None):
+        if replicas is None:
+            ny = nx if ny is None else ny
+            nz = nx if nz is None else nz
+            replicas = [(nx, ny, nz)]
+        else:
+            nx, ny, nz = replicas[0]
         L = lib()
         p = Params()
         L.misa_default_params(C.byref(p))
@@ -187,13 +205,16 @@ class Sim:
             st = stream
         self.stream = st
         h = C.c_void_p()
-        rc = L.misa_create(C.byref(p), C.c_void_p(st) if st else None, C.byref(h))
+        dims = (C.c_int32 * (3 * len(replicas)))(*[int(v) for d in replicas for v in d])
+        rc = L.misa_create_batch(C.byref(p), len(replicas), dims, C.c_void_p(st) if st else None, C.byref(h))
         if rc != MISA_OK:
             raise MisaError(rc, L.misa_last_error(None).decode())
         self.h = h
+        self.replicas = [tuple(d) for d in replicas]
         self.nx, self.ny, self.nz = nx, ny, nz
-        self.natoms = 2 * nx * ny * nz
+        self.natoms = sum(2 * a * b * c for a, b, c in replicas)
         self.box = np.array([nx * a0, ny * a0, nz * a0])
+        self.a0 = a0
         self.precision = p.precision
 
     # -- plumbing -----------------------------------------------------------
@@ -282,6 +303,36 @@ class Sim:
         n = C.c_int64()
         self._check(lib().misa_timing_get(self.h, ms, C.byref(n)))
         return dict(zip(PHASES, list(ms))), n.value
+
+    # -- batches --------------------------------------------------------------
+    def replica_info(self, r):
+        """(dims, first atom id, atom count) of replica r."""
+        d = (C.c_int32 * 3)()
+        b, n = C.c_int64(), C.c_int64()
+        self._check(lib().misa_replica_info(self.h, int(r), d, C.byref(b), C.byref(n)))
+        return tuple(d), b.value, n.value
+
+    def insert_pka_replica(self, r, energy, direction):
+        d = (C.c_double * 3)(*[float(t) for t in direction])
+        self._check(lib().misa_insert_pka_replica(self.h, int(r), float(energy), d))
+
+    def replica_stats(self, r) -> dict:
+        s = Stats()
+        self._check(lib().misa_replica_stats(self.h, int(r), C.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def replica_energies(self):
+        n = len(self.replicas)
+        pe, ke = np.empty(n), np.empty(n)
+        self._check(lib().misa_replica_energies(self.h, pe.ctypes.data_as(_D), ke.ctypes.data_as(_D)))
+        return pe, ke
+
+    def set_graphs(self, enable=True):
+        self._check(lib().misa_set_graphs(self.h, 1 if enable else 0))
+
+    def tile(self):
+        """Tile shape in use (cells)."""
+        return tile_shapes()[lib().misa_tile_current(self.h) - 1]
 
     def clear_status(self):
         self._check(lib().misa_clear_status(self.h))

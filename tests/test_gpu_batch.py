@@ -1,0 +1,97 @@
+"""Batched replicas (Sec. 1 feature list: batch execution of simulations):
+several uneven boxes in one handle, every step kernel launched once for all
+of them.  A replica of a batch must evolve exactly as the same box alone
+(same kernels, same per-site sum order), and the captured step graph must
+reproduce the directly launched step."""
+import numpy as np
+import pytest
+
+from paper_2107_07866_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+M = synth.MASS_FE
+
+
+@pytest.fixture(scope="module")
+def misa():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2107_07866_gb300 import build
+    build.build()
+    from paper_2107_07866_gb300 import misa as M_
+    return M_
+
+
+def _inputs(dims, seed, pka_eV):
+    x = synth.cascade_snapshot(*dims, 0.1, 3, 1, seed)
+    v = synth.maxwell_velocities(len(x), 300.0 + 100 * seed, M, seed)
+    if pka_eV:
+        a = synth.pka_atom(*dims)
+        d = synth.random_direction(seed + 5)
+        v[a] = np.sqrt(2 * pka_eV / M / synth.EV_PER_AMU_A2_FS2) * d
+    return x, v
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_replicas_evolve_as_single_boxes(misa, pot, prec):
+    reps = [(6, 7, 8), (9, 6, 6), (8, 8, 7)]
+    ins = [_inputs(d, k, 200.0 * (k + 1)) for k, d in enumerate(reps)]
+    kw = dict(precision=prec, dx_max=0.02, reassign_period=2, tile=2)
+    with misa.Sim(pot, replicas=reps, **kw) as b:
+        assert b.natoms == sum(2 * a * c * e for a, c, e in reps)
+        b.set_state(np.concatenate([x for x, _ in ins]), np.concatenate([v for _, v in ins]))
+        b.step(25)
+        xb, fb = b.positions(), b.forces()
+        stb = [b.replica_stats(r) for r in range(len(reps))]
+        peb, keb = b.replica_energies()
+    off = 0
+    for r, (d, (x, v)) in enumerate(zip(reps, ins)):
+        n = 2 * d[0] * d[1] * d[2]
+        with misa.Sim(pot, *d, **kw) as s:
+            s.set_state(x, v)
+            s.step(25)
+            np.testing.assert_array_equal(xb[off:off + n], s.positions())
+            np.testing.assert_array_equal(fb[off:off + n], s.forces())
+            st = s.stats()
+            pe, ke = s.energies()
+        # each replica has its own adaptive timestep and run-away list
+        assert stb[r]["time"] == st["time"] and stb[r]["n_runaway"] == st["n_runaway"]
+        assert peb[r] == pytest.approx(pe, rel=1e-12) and keb[r] == pytest.approx(ke, rel=1e-12)
+        off += n
+    assert len({s_["time"] for s_ in stb}) == len(reps)
+
+
+def test_graph_replay_equals_direct_launches(misa, pot):
+    x, v = _inputs((8, 8, 8), 3, 400.0)
+    out = []
+    for graphs in (True, False):
+        with misa.Sim(pot, 8, precision="fp32", dx_max=0.02, reassign_period=3) as s:
+            s.set_graphs(graphs)
+            s.set_state(x, v)
+            s.step(15)
+            s.step(15)
+            out.append((s.positions(), s.velocities(), s.stats()["step"]))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2] == 30
+
+
+def test_autotuner_picks_a_built_tile(misa, pot):
+    with misa.Sim(pot, 12, precision="fp32", tile=0) as s:
+        assert s.tile() in misa.tile_shapes()
+
+
+def test_batch_pka_per_replica(misa, pot):
+    reps = [(6, 6, 6), (7, 6, 8)]
+    with misa.Sim(pot, replicas=reps, precision="fp64", dx_max=0.02) as b:
+        d = np.array([0.0, 0.6, 0.8])
+        b.insert_pka_replica(1, 1000.0, d)
+        v = b.velocities()
+        _, base, n = b.replica_info(1)
+        a = base + synth.pka_atom(*reps[1])
+        assert 0.5 * M * np.dot(v[a], v[a]) * synth.EV_PER_AMU_A2_FS2 == pytest.approx(1000.0, rel=1e-12)
+        assert np.count_nonzero(np.linalg.norm(v, axis=1)) == 1
+        b.step(4)
+        t0, t1 = b.replica_stats(0)["time"], b.replica_stats(1)["time"]
+        assert t0 == pytest.approx(4.0) and t1 < 0.5
