@@ -218,6 +218,23 @@ int misa_clear_status(misa_sim *s);
 int misa_save(misa_sim *s, const char *path);
 int misa_load(misa_sim *s, const char *path);
 
+/* Replaces the knot values of the three tables (same count and grids as at
+ * create; host or device pointers), rebuilds the spline coefficients on the
+ * device (Sec. 4.1) and re-evaluates the forces of the current positions. */
+int misa_set_tables(misa_sim *s, const double *f_knots, const double *phi_knots, const double *F_knots);
+
+/* Potential fitting (no counterpart in the paper): loss and its gradient
+ * with respect to the 3 n_knots knot values, for the current positions of
+ * every replica against target forces Fref (3 natoms doubles, eV/A, by atom
+ * id) and target energies Eref (nrep doubles, eV):
+ *   loss = sum_r [ (1/(3 N_r)) sum_i |F_i - Fref_i|^2 + ((E_r - Eref_r)/N_r)^2 ]
+ * (Eq. eam_base for E, Eq. eam_force_ij for F).  grad (3 n_knots doubles,
+ * host or device; may be NULL) receives d loss / d knot in the order f knots,
+ * phi knots, F knots.  Pair arithmetic in the handle's precision,
+ * accumulation in FP64 (per-CTA shared-memory bins, one ordered reduction).
+ * Synchronises. */
+int misa_loss_grad(misa_sim *s, const double *Fref, const double *Eref, double *loss, double *grad);
+
 /* Number of built gather tile shapes, and the shape of each (cells). */
 int misa_tile_count(void);
 int misa_tile_shape(int index, int *tx, int *ty, int *tz);

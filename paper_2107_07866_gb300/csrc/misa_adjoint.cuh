@@ -1,0 +1,458 @@
+// misa_adjoint.cuh -- gradient of a force-matching + energy loss with respect
+// to the knot values of the three spline tables (no counterpart in the
+// paper; used to fit potentials).
+//
+// Per replica r with N_r atoms, forces F_i, energy E_r and targets:
+//   L_r = (1/(3 N_r)) sum_i |F_i - Fref_i|^2 + ((E_r - Eref_r)/N_r)^2.
+// With lambda_i = 2 (F_i - Fref_i)/(3 N_r), sum_i lambda_i . F_i is minus
+// the derivative of E along the displacement field lambda, so the knot
+// gradient of the force term is minus that directional derivative of
+// dE/d(knot); the energy term adds c_e dE/d(knot), c_e = 2 (E_r - Eref_r)/N_r^2.
+// The spline is linear in its knots (S(x) = sum_k w_k(x) y_k), so
+//   phi knots: sum over ordered pairs of  c_e w_k/2 - dw_k D/2
+//   f knots:   sum over ordered pairs of  c_e F'_i w_k - (F''_i Dl_i w_k + F'_i dw_k D)
+//   F knots:   sum over atoms of          c_e w_k(rho_i) - dw_k(rho_i) Dl_i
+// where D = d r_ij / d eps along lambda and Dl_i = sum_j f'(r_ij) D.
+// Kernels: lambda (+ force-loss sums), Dl gather, gradient scatter into
+// per-CTA FP64 bins in shared memory, one ordered reduction over CTAs.
+// Pair arithmetic in the precision T of the handle, accumulation in FP64.
+#pragma once
+
+#include "misa_md.cuh"
+
+namespace misa {
+
+// the bcc lattice vectors for runtime-indexed device loops
+static __constant__ LVecTable c_lvec = kLVec;
+
+template <typename T>
+struct AdjArgs {
+    const RepDesc *reps;
+    int nrep;
+    const int *sid;
+    const T *ux, *uy, *uz;
+    const T *fp, *rho;
+    const T *ax, *ay, *az;
+    const int *ra_home, *ra_id;
+    const T *ra_ux, *ra_uy, *ra_uz;
+    const T *ra_fp, *ra_rho;
+    const T *ra_ax, *ra_ay, *ra_az;
+    const DevScalars *sc;
+    const Vec4<T> *tab_d0, *tab_F;  // f' coefficients (x, y, z of d0), F value coefficients
+    int n;                          // knots per table
+    T S;                            // knot index per lattice unit of r
+    T hr, hrho, rho_max, rc2, rfloor2, half;
+    double acc_conv;
+    const double *Fref;   // 3 per atom id
+    const double *Eref;   // per replica
+    const double *Etot;   // per replica
+    T *lam_x, *lam_y, *lam_z;        // per site (pooled)
+    T *ra_lx, *ra_ly, *ra_lz;        // per run-away slot
+    T *dl, *ra_dl;                   // D_lambda rho per site / run-away slot
+    int nvec;                        // offsets within rc + 2 skin (prefix of kLVec)
+};
+
+// one pair seen from atom i: |r| in lattice units, unit vector i -> j, the
+// spline segment and t of r, and where atom j lives (array site or run-away
+// slot, pooled indices)
+template <typename T>
+struct AdjPair {
+    T r, ex, ey, ez;
+    bool ra;
+    long long j;
+    int seg;
+    T t;
+    bool floor_hit;
+};
+
+// Pair geometry from the integer lattice vector n between the two sites and
+// d = u_j - u_i.  The spline argument x = r S is formed as |n| S (FP64,
+// split into integer and fraction) plus (r - |n|) S with
+// r - |n| = q / (r + |n|), q = (2n + d).d: full precision in t also in FP32
+// (x is near 2000, where a plain FP32 r S keeps only ~1e-4 of t).
+template <typename T>
+__device__ __forceinline__ bool adj_pair(const AdjArgs<T> &a, int nx, int ny, int nz, T dx, T dy, T dz, bool ra,
+                                         long long j, AdjPair<T> &P)
+{
+    const T q = ((T)(2 * nx) + dx) * dx + ((T)(2 * ny) + dy) * dy + ((T)(2 * nz) + dz) * dz;
+    const int n2 = nx * nx + ny * ny + nz * nz;
+    const T r2 = (T)n2 + q;
+    if (!(r2 < a.rc2)) return false;
+    const T rx = (T)nx + dx, ry = (T)ny + dy, rz = (T)nz + dz;
+    P.ra = ra;
+    P.j = j;
+    P.floor_hit = r2 < a.rfloor2;
+    const T r = sqrt(P.floor_hit ? a.rfloor2 : r2);
+    P.r = r;
+    const T inv = P.floor_hit ? (T)0 : (T)1 / r;
+    P.ex = rx * inv;
+    P.ey = ry * inv;
+    P.ez = rz * inv;
+    if (P.floor_hit || n2 == 0) {
+        const double x = (double)r * (double)a.S;
+        const double fl = floor(x);
+        P.seg = (int)fl;
+        P.t = (T)(x - fl);
+    } else {
+        const double nn = sqrt((double)n2);
+        const double x0 = nn * (double)a.S;
+        const double xi = floor(x0);
+        const T dr = q / (r + (T)nn);
+        const T x = (T)(x0 - xi) + dr * a.S;
+        const T fl = floor(x);
+        P.seg = (int)xi + (int)fl;
+        P.t = x - fl;
+    }
+    if (P.seg < 0) {
+        P.seg = 0;
+        P.t = 0;
+    }
+    if (P.seg > a.n - 2) {
+        P.seg = a.n - 2;
+        P.t = 1;
+    }
+    return true;
+}
+
+// Visits every neighbour j of array atom i (pooled site s, replica-local
+// site ls) inside rc: array atoms through the offset vectors, then the
+// replica's run-away list.
+template <typename T, typename Fn>
+__device__ __forceinline__ void visit_site(const AdjArgs<T> &a, const RepDesc &rd, int nra, long long ls, Fn &fn)
+{
+    const long long s = rd.site_base + ls;
+    const T uix = a.ux[s], uiy = a.uy[s], uiz = a.uz[s];
+    const int x2 = (int)(ls % (2 * rd.nx));
+    const long long q = ls / (2 * rd.nx);
+    const int cy = (int)(q % rd.ny), cz = (int)(q / rd.ny);
+    const int p = x2 & 1;
+    for (int k = 0; k < a.nvec; ++k) {
+        const LVec o = c_lvec.v[k];
+        const int tx = wrapi(x2 + o.x, 2 * rd.nx);
+        const int ty = wrapi(cy + cell_shift(p, o.y), rd.ny);
+        const int tz = wrapi(cz + cell_shift(p, o.z), rd.nz);
+        const long long t = rd.site_base + (((long long)tz * rd.ny + ty) * rd.nx) * 2 + tx;
+        if (a.sid[t] < 0) continue;
+        AdjPair<T> P;
+        if (adj_pair<T>(a, o.x, o.y, o.z, a.ux[t] - uix, a.uy[t] - uiy, a.uz[t] - uiz, false, t, P)) fn(P);
+    }
+    int X, Y, Z;
+    site_lat(ls, rd.nx, rd.ny, X, Y, Z);
+    const int Lx = 2 * rd.nx, Ly = 2 * rd.ny, Lz = 2 * rd.nz;
+    for (int j = 0; j < nra; ++j) {
+        const int g = rd.ra_base + j;
+        int Xj, Yj, Zj;
+        site_lat(a.ra_home[g], rd.nx, rd.ny, Xj, Yj, Zj);
+        int nx_ = Xj - X, ny_ = Yj - Y, nz_ = Zj - Z;
+        nx_ -= (nx_ > rd.nx) ? Lx : 0;
+        nx_ += (nx_ < -rd.nx) ? Lx : 0;
+        ny_ -= (ny_ > rd.ny) ? Ly : 0;
+        ny_ += (ny_ < -rd.ny) ? Ly : 0;
+        nz_ -= (nz_ > rd.nz) ? Lz : 0;
+        nz_ += (nz_ < -rd.nz) ? Lz : 0;
+        AdjPair<T> P;
+        if (adj_pair<T>(a, nx_, ny_, nz_, a.ra_ux[g] - uix, a.ra_uy[g] - uiy, a.ra_uz[g] - uiz, true, g, P)) fn(P);
+    }
+}
+
+// Visits every neighbour of run-away j (pooled slot g): array sites in a
+// 7-cell window around its home site, then the other run-aways.
+template <typename T, typename Fn>
+__device__ __forceinline__ void visit_ra(const AdjArgs<T> &a, const RepDesc &rd, int nra, int jl, Fn &fn)
+{
+    const int g = rd.ra_base + jl;
+    int X, Y, Z;
+    site_lat(a.ra_home[g], rd.nx, rd.ny, X, Y, Z);
+    const int hp = X & 1;
+    const int hcx = X >> 1, hcy = (Y - hp) >> 1, hcz = (Z - hp) >> 1;
+    const T ujx = a.ra_ux[g], ujy = a.ra_uy[g], ujz = a.ra_uz[g];
+    const int wx = rd.nx < 7 ? rd.nx : 7, wy = rd.ny < 7 ? rd.ny : 7, wz = rd.nz < 7 ? rd.nz : 7;
+    for (int c = 0; c < wx * wy * wz * 2; ++c) {
+        const int qq = c & 1, rr = c >> 1;
+        const int ox = rr % wx, oy = (rr / wx) % wy, oz = rr / (wx * wy);
+        const int cx = hcx - 3 + ox, cy = hcy - 3 + oy, cz = hcz - 3 + oz;
+        const long long t = rd.site_base + (((long long)wrapi(cz, rd.nz) * rd.ny + wrapi(cy, rd.ny)) * rd.nx + wrapi(cx, rd.nx)) * 2 + qq;
+        if (a.sid[t] < 0) continue;
+        AdjPair<T> P;
+        if (adj_pair<T>(a, 2 * cx + qq - X, 2 * cy + qq - Y, 2 * cz + qq - Z, a.ux[t] - ujx, a.uy[t] - ujy,
+                        a.uz[t] - ujz, false, t, P))
+            fn(P);
+    }
+    const int Lx = 2 * rd.nx, Ly = 2 * rd.ny, Lz = 2 * rd.nz;
+    for (int k = 0; k < nra; ++k) {
+        if (k == jl) continue;
+        const int gk = rd.ra_base + k;
+        int Xk, Yk, Zk;
+        site_lat(a.ra_home[gk], rd.nx, rd.ny, Xk, Yk, Zk);
+        int nx_ = Xk - X, ny_ = Yk - Y, nz_ = Zk - Z;
+        nx_ -= (nx_ > rd.nx) ? Lx : 0;
+        nx_ += (nx_ < -rd.nx) ? Lx : 0;
+        ny_ -= (ny_ > rd.ny) ? Ly : 0;
+        ny_ += (ny_ < -rd.ny) ? Ly : 0;
+        nz_ -= (nz_ > rd.nz) ? Lz : 0;
+        nz_ += (nz_ < -rd.nz) ? Lz : 0;
+        AdjPair<T> P;
+        if (adj_pair<T>(a, nx_, ny_, nz_, a.ra_ux[gk] - ujx, a.ra_uy[gk] - ujy, a.ra_uz[gk] - ujz, true, gk, P)) fn(P);
+    }
+}
+
+// Weights of knots s-2 .. s+3 in S(x) and dS/dx at x = (s + t) h for the
+// local Hermite spline (slopes: 4th-order central differences inside,
+// 2nd order at the two outer knots of each end).
+template <typename T>
+__device__ __forceinline__ void basis6(int s, T t, int n, T h, T w[6], T dw[6])
+{
+    const T t2 = t * t, t3 = t2 * t;
+    const T c0 = 2 * t3 - 3 * t2 + 1, c1 = t3 - 2 * t2 + t, c2 = -2 * t3 + 3 * t2, c3 = t3 - t2;
+    const T d0 = (6 * t2 - 6 * t) / h, d1 = (3 * t2 - 4 * t + 1) / h, d2 = (-6 * t2 + 6 * t) / h, d3 = (3 * t2 - 2 * t) / h;
+    for (int q = 0; q < 6; ++q) {
+        w[q] = 0;
+        dw[q] = 0;
+    }
+    w[2] += c0;
+    dw[2] += d0;
+    w[3] += c2;
+    dw[3] += d2;
+    // h * slope of knot k = sum_l st_l y_l (h cancels against the 1/h of the stencil)
+    for (int e = 0; e < 2; ++e) {
+        const int k = s + e;
+        const T cm = e == 0 ? c1 : c3, dm = e == 0 ? d1 : d3;
+        int ks[4];
+        T st[4];
+        int ns;
+        if (k == 0) {
+            ks[0] = 0; st[0] = (T)-1.5; ks[1] = 1; st[1] = (T)2; ks[2] = 2; st[2] = (T)-0.5; ns = 3;
+        } else if (k == n - 1) {
+            ks[0] = n - 1; st[0] = (T)1.5; ks[1] = n - 2; st[1] = (T)-2; ks[2] = n - 3; st[2] = (T)0.5; ns = 3;
+        } else if (k == 1 || k == n - 2) {
+            ks[0] = k + 1; st[0] = (T)0.5; ks[1] = k - 1; st[1] = (T)-0.5; ns = 2;
+        } else {
+            ks[0] = k - 2; st[0] = (T)(1.0 / 12.0); ks[1] = k - 1; st[1] = (T)(-8.0 / 12.0);
+            ks[2] = k + 1; st[2] = (T)(8.0 / 12.0); ks[3] = k + 2; st[3] = (T)(-1.0 / 12.0); ns = 4;
+        }
+        for (int q = 0; q < ns; ++q) {
+            const int j = ks[q] - (s - 2);
+            w[j] += cm * st[q];
+            dw[j] += dm * st[q];
+        }
+    }
+}
+
+// spline segment and t of x on a grid of spacing h (n knots)
+template <typename T>
+__device__ __forceinline__ int seg_t(T x, T inv_h, int n, T &t)
+{
+    const T u = x * inv_h;
+    int s = (int)floor(u);
+    s = s < 0 ? 0 : (s > n - 2 ? n - 2 : s);
+    t = u - (T)s;
+    return s;
+}
+
+// lambda_i = 2 (F_i - Fref_i)/(3 N_r) per site and run-away; per-(replica,
+// block) partial sums of |F_i - Fref_i|^2.  grid.y = replica.
+template <typename T>
+__global__ void k_adj_lambda(AdjArgs<T> a, double *partial)
+{
+    const int r = blockIdx.y;
+    const RepDesc rd = a.reps[r];
+    const double c = 2.0 / (3.0 * (double)rd.ns);
+    double acc = 0.0;
+    MISA_SITE_LOOP(rd, ls) {
+        const long long s = rd.site_base + ls;
+        const int id = a.sid[s];
+        if (id < 0) continue;
+        const double fx = (double)a.ax[s] / a.acc_conv - a.Fref[3LL * id];
+        const double fy = (double)a.ay[s] / a.acc_conv - a.Fref[3LL * id + 1];
+        const double fz = (double)a.az[s] / a.acc_conv - a.Fref[3LL * id + 2];
+        acc += fx * fx + fy * fy + fz * fz;
+        a.lam_x[s] = (T)(c * fx);
+        a.lam_y[s] = (T)(c * fy);
+        a.lam_z[s] = (T)(c * fz);
+    }
+    const int nra = a.sc[r].n_ra;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nra; j += gridDim.x * blockDim.x) {
+        const int g = rd.ra_base + j;
+        const int id = a.ra_id[g];
+        const double fx = (double)a.ra_ax[g] / a.acc_conv - a.Fref[3LL * id];
+        const double fy = (double)a.ra_ay[g] / a.acc_conv - a.Fref[3LL * id + 1];
+        const double fz = (double)a.ra_az[g] / a.acc_conv - a.Fref[3LL * id + 2];
+        acc += fx * fx + fy * fy + fz * fz;
+        a.ra_lx[g] = (T)(c * fx);
+        a.ra_ly[g] = (T)(c * fy);
+        a.ra_lz[g] = (T)(c * fz);
+    }
+    __shared__ double sw[32];
+    acc = warp_sum<double>(acc);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sw[k];
+        partial[(size_t)r * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+template <typename T>
+struct LamOf {
+    const AdjArgs<T> &a;
+    __device__ __forceinline__ void get(const AdjPair<T> &P, T &lx, T &ly, T &lz) const
+    {
+        if (P.ra) {
+            lx = a.ra_lx[P.j]; ly = a.ra_ly[P.j]; lz = a.ra_lz[P.j];
+        } else {
+            lx = a.lam_x[P.j]; ly = a.lam_y[P.j]; lz = a.lam_z[P.j];
+        }
+    }
+};
+
+// D_lambda r_ij = rhat_ij . (lambda_i - lambda_j) = e . (lambda_j - lambda_i)
+// with e the unit vector from i to j
+template <typename T>
+struct DlFn {
+    const AdjArgs<T> &a;
+    T lix, liy, liz;
+    double acc;
+    __device__ __forceinline__ void operator()(const AdjPair<T> &P)
+    {
+        if (P.floor_hit) return;  // direction undefined: no derivative
+        T ljx, ljy, ljz;
+        LamOf<T>{a}.get(P, ljx, ljy, ljz);
+        const T t = P.t;
+        const Vec4<T> c = a.tab_d0[P.seg];
+        const T dfr = (c.x * t + c.y) * t + c.z;
+        const T D = P.ex * (ljx - lix) + P.ey * (ljy - liy) + P.ez * (ljz - liz);
+        acc += (double)(dfr * D);
+    }
+};
+
+template <typename T>
+__global__ void k_adj_dl(AdjArgs<T> a)
+{
+    const int r = blockIdx.y;
+    const RepDesc rd = a.reps[r];
+    const int nra = a.sc[r].n_ra;
+    MISA_SITE_LOOP(rd, ls) {
+        const long long s = rd.site_base + ls;
+        if (a.sid[s] < 0) continue;
+        DlFn<T> fn{a, a.lam_x[s], a.lam_y[s], a.lam_z[s], 0.0};
+        visit_site<T>(a, rd, nra, ls, fn);
+        a.dl[s] = (T)fn.acc;
+    }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nra; j += gridDim.x * blockDim.x) {
+        const int g = rd.ra_base + j;
+        DlFn<T> fn{a, a.ra_lx[g], a.ra_ly[g], a.ra_lz[g], 0.0};
+        visit_ra<T>(a, rd, nra, j, fn);
+        a.ra_dl[g] = (T)fn.acc;
+    }
+}
+
+// per-pair scatter into the CTA's bins: bins[0, n) f knots, [n, 2n) phi
+// knots, [2n, 3n) F knots
+template <typename T>
+struct GradFn {
+    const AdjArgs<T> &a;
+    double *bins;
+    T lix, liy, liz;
+    T ce, Fpi, Fppi, dli;
+    __device__ __forceinline__ void operator()(const AdjPair<T> &P)
+    {
+        T ljx, ljy, ljz;
+        LamOf<T>{a}.get(P, ljx, ljy, ljz);
+        // unit vector is zero below r_floor: no derivative term there
+        const T D = P.ex * (ljx - lix) + P.ey * (ljy - liy) + P.ez * (ljz - liz);
+        const int sg = P.seg;
+        T w[6], dw[6];
+        basis6<T>(sg, P.t, a.n, a.hr, w, dw);
+        for (int q = 0; q < 6; ++q) {
+            const int k = sg - 2 + q;
+            if (k < 0 || k >= a.n) continue;
+            const T gphi = (T)0.5 * ce * w[q] - (T)0.5 * dw[q] * D;
+            const T gf = ce * Fpi * w[q] - (Fppi * dli * w[q] + Fpi * dw[q] * D);
+            if (gf != (T)0) atomicAdd(&bins[k], (double)gf);
+            if (gphi != (T)0) atomicAdd(&bins[a.n + k], (double)gphi);
+        }
+    }
+};
+
+// F'' of the embedding spline at rho (0 on the linear tail)
+template <typename T>
+__device__ __forceinline__ T embed_dd(const AdjArgs<T> &a, T rho)
+{
+    if (rho > a.rho_max) return 0;
+    if (rho < 0) rho = 0;
+    T t;
+    const int sg = seg_t<T>(rho, (T)1 / a.hrho, a.n, t);
+    const Vec4<T> c = a.tab_F[sg];
+    return (6 * c.x * t + 2 * c.y) / (a.hrho * a.hrho);
+}
+
+template <typename T>
+__device__ __forceinline__ void embed_bins(const AdjArgs<T> &a, double *bins, T rho, T ce, T dli)
+{
+    T w[6], dw[6];
+    int sg;
+    T ex = 0;
+    if (rho > a.rho_max) {
+        sg = a.n - 2;
+        basis6<T>(sg, (T)1, a.n, a.hrho, w, dw);
+        ex = rho - a.rho_max;
+    } else {
+        T t;
+        sg = seg_t<T>(rho < 0 ? (T)0 : rho, (T)1 / a.hrho, a.n, t);
+        basis6<T>(sg, t, a.n, a.hrho, w, dw);
+    }
+    for (int q = 0; q < 6; ++q) {
+        const int k = sg - 2 + q;
+        if (k < 0 || k >= a.n) continue;
+        const T g = ce * (w[q] + dw[q] * ex) - dw[q] * dli;
+        if (g != (T)0) atomicAdd(&bins[2 * a.n + k], (double)g);
+    }
+}
+
+// gradient scatter: grid (blocks, replica); each CTA zeroes its 3n FP64 bins
+// in shared memory, scatters its atoms' pair terms with shared-memory
+// atomics, then writes the bins to partial[cta][3n]
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_grad(AdjArgs<T> a, double *partial)
+{
+    extern __shared__ double bins[];
+    const int r = blockIdx.y;
+    const RepDesc rd = a.reps[r];
+    const int nra = a.sc[r].n_ra;
+    const int nb = 3 * a.n;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) bins[k] = 0.0;
+    __syncthreads();
+    const double Nr = (double)rd.ns;
+    const T ce = (T)(2.0 * (a.Etot[r] - a.Eref[r]) / (Nr * Nr));
+    MISA_SITE_LOOP(rd, ls) {
+        const long long s = rd.site_base + ls;
+        if (a.sid[s] < 0) continue;
+        const T rho = a.rho[s];
+        GradFn<T> fn{a, bins, a.lam_x[s], a.lam_y[s], a.lam_z[s], ce, a.fp[s], embed_dd<T>(a, rho), a.dl[s]};
+        visit_site<T>(a, rd, nra, ls, fn);
+        embed_bins<T>(a, bins, rho, ce, a.dl[s]);
+    }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nra; j += gridDim.x * blockDim.x) {
+        const int g = rd.ra_base + j;
+        const T rho = a.ra_rho[g];
+        GradFn<T> fn{a, bins, a.ra_lx[g], a.ra_ly[g], a.ra_lz[g], ce, a.ra_fp[g], embed_dd<T>(a, rho), a.ra_dl[g]};
+        visit_ra<T>(a, rd, nra, j, fn);
+        embed_bins<T>(a, bins, rho, ce, a.ra_dl[g]);
+    }
+    __syncthreads();
+    double *out = partial + ((size_t)r * gridDim.x + blockIdx.x) * nb;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) out[k] = bins[k];
+}
+
+// grad[k] = sum over CTAs of partial[cta][k], in CTA order
+__global__ void k_adj_reduce(const double *partial, int ncta, int nb, double *grad)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < ncta; ++c) s += partial[(size_t)c * nb + k];
+        grad[k] = s;
+    }
+}
+
+}  // namespace misa

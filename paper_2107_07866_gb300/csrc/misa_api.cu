@@ -12,7 +12,7 @@
 #include <vector>
 
 #include "misa.h"
-#include "misa_md.cuh"
+#include "misa_adjoint.cuh"
 
 using namespace misa;
 
@@ -79,6 +79,11 @@ struct misa_sim {
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
+    // adjoint work arrays (allocated on first use)
+    void *lam[3] = {}, *ra_lam[3] = {};
+    void *dl = nullptr, *ra_dl = nullptr;
+    double *adj_partial = nullptr, *adj_grad = nullptr, *adj_eref = nullptr, *adj_fref = nullptr;
+    int adj_cta = 0;
     // captured step graph
     bool use_graph = true;
     cudaGraphExec_t graph = nullptr;
@@ -738,6 +743,117 @@ int stats_of(misa_sim *s, int r, const DevScalars &h, unsigned status, misa_stat
     return MISA_OK;
 }
 
+// New knot values for the three tables (same n and grids); the forces of
+// the current positions are re-evaluated.
+template <typename T>
+int set_tables_impl(misa_sim *s, const double *f, const double *phi, const double *F)
+{
+    const int n = s->p.n_knots;
+    CK(cudaMemcpyAsync(s->knots, f, sizeof(double) * n, cudaMemcpyDefault, s->st));
+    CK(cudaMemcpyAsync(s->knots + n, phi, sizeof(double) * n, cudaMemcpyDefault, s->st));
+    CK(cudaMemcpyAsync(s->knots + 2 * n, F, sizeof(double) * n, cudaMemcpyDefault, s->st));
+    const double hr = s->p.rc / (n - 1), hrho = s->p.rho_max / (n - 1);
+    k_spline_tables<T><<<(n + 255) / 256, 256, 0, s->st>>>(s->knots, s->knots + n, s->knots + 2 * n, n, hr, hrho,
+                                                            (Vec4<T> *)s->tab_f, (Vec4<T> *)s->tab_phi,
+                                                            (Vec4<T> *)s->tab_F, (Vec4<T> *)s->tab_d0,
+                                                            (Vec2<T> *)s->tab_d1);
+    CK(cudaGetLastError());
+    return refresh<T>(s, true);
+}
+
+// Loss and knot gradient of the current state against target forces and
+// energies (Fref: 3 natoms, Eref: nrep); see misa_adjoint.cuh.
+template <typename T>
+int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *loss, double *grad)
+{
+    const int n = s->p.n_knots;
+    const size_t capt = (size_t)s->cap * s->nrep;
+    if (!s->dl) {
+        for (int d = 0; d < 3; ++d) {
+            s->lam[d] = dalloc(s, sizeof(T) * s->ns);
+            s->ra_lam[d] = dalloc(s, sizeof(T) * capt);
+            if (!s->lam[d] || !s->ra_lam[d]) return fail(s, MISA_EOOM, "adjoint work arrays");
+        }
+        s->dl = dalloc(s, sizeof(T) * s->ns);
+        s->ra_dl = dalloc(s, sizeof(T) * capt);
+        int gx = (s->nsm * 2 + s->nrep - 1) / s->nrep;
+        s->adj_cta = gx < 1 ? 1 : gx;
+        s->adj_partial = (double *)dalloc(s, sizeof(double) * 3 * n * (size_t)s->adj_cta * s->nrep);
+        s->adj_grad = (double *)dalloc(s, sizeof(double) * 3 * n);
+        s->adj_eref = (double *)dalloc(s, sizeof(double) * s->nrep * 2);
+        s->adj_fref = (double *)dalloc(s, sizeof(double) * 3 * s->ns);
+        if (!s->dl || !s->ra_dl || !s->adj_partial || !s->adj_grad || !s->adj_eref || !s->adj_fref)
+            return fail(s, MISA_EOOM, "adjoint work arrays");
+        CK(cudaFuncSetAttribute(k_adj_grad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * 3 * n)));
+    }
+    if ((size_t)3 * n * sizeof(double) > 227u * 1024u) return fail(s, MISA_EINVAL, "too many knots for the gradient bins");
+    // forward: rho, F', E_i, forces of the current positions
+    int rc = launch_forces<T>(s, 0, true);
+    if (rc) return rc;
+    MdArgs<T> m = md_args<T>(s);
+    const int nb = 512;
+    k_sum_stage1<T><<<dim3(nb, s->nrep), 256, 0, s->st>>>(m, 0, s->partial);
+    k_sum_stage2<<<s->nrep, 1024, 0, s->st>>>(s->partial, nb, s->red_out);  // E_r
+    CK(cudaMemcpyAsync(s->adj_fref, Fref, sizeof(double) * 3 * s->ns, cudaMemcpyDefault, s->st));
+    CK(cudaMemcpyAsync(s->adj_eref, Eref, sizeof(double) * s->nrep, cudaMemcpyDefault, s->st));
+    AdjArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.reps = s->reps_d;
+    a.nrep = s->nrep;
+    a.sid = s->sid;
+    a.ux = (const T *)s->s[0]; a.uy = (const T *)s->s[1]; a.uz = (const T *)s->s[2];
+    a.fp = (const T *)s->fp; a.rho = (const T *)s->rho;
+    a.ax = (const T *)s->a[0]; a.ay = (const T *)s->a[1]; a.az = (const T *)s->a[2];
+    a.ra_home = s->ra_home; a.ra_id = s->ra_id;
+    a.ra_ux = (const T *)s->ra_s[0]; a.ra_uy = (const T *)s->ra_s[1]; a.ra_uz = (const T *)s->ra_s[2];
+    a.ra_fp = (const T *)s->ra_fp; a.ra_rho = (const T *)s->ra_rho;
+    a.ra_ax = (const T *)s->ra_a[0]; a.ra_ay = (const T *)s->ra_a[1]; a.ra_az = (const T *)s->ra_a[2];
+    a.sc = s->sc;
+    a.tab_d0 = (const Vec4<T> *)s->tab_d0;
+    a.tab_F = (const Vec4<T> *)s->tab_F;
+    a.n = n;
+    const double half = 0.5 * s->p.a0;
+    a.half = (T)half;
+    a.hr = (T)(s->p.rc / (n - 1));
+    a.hrho = (T)(s->p.rho_max / (n - 1));
+    a.S = (T)(half / (s->p.rc / (n - 1)));
+    a.rho_max = (T)s->p.rho_max;
+    const double rcl = s->p.rc / half;
+    a.rc2 = (T)(rcl * rcl);
+    a.rfloor2 = (T)((kRfloor / half) * (kRfloor / half));
+    a.acc_conv = kAccUnit / s->p.mass;
+    a.Fref = s->adj_fref;
+    a.Eref = s->adj_eref;
+    a.Etot = s->red_out;
+    a.lam_x = (T *)s->lam[0]; a.lam_y = (T *)s->lam[1]; a.lam_z = (T *)s->lam[2];
+    a.ra_lx = (T *)s->ra_lam[0]; a.ra_ly = (T *)s->ra_lam[1]; a.ra_lz = (T *)s->ra_lam[2];
+    a.dl = (T *)s->dl; a.ra_dl = (T *)s->ra_dl;
+    const double roff = (s->p.rc + 2.0 * s->p.skin) / half;
+    int nsh = 0;
+    while (nsh < kLVec.nshell && kLVec.shell_n2[nsh] <= roff * roff) ++nsh;
+    a.nvec = kLVec.shell_begin[nsh];
+    k_adj_lambda<T><<<dim3(nb, s->nrep), 256, 0, s->st>>>(a, s->partial);
+    k_sum_stage2<<<s->nrep, 1024, 0, s->st>>>(s->partial, nb, s->red_out + s->nrep);  // sum |F - Fref|^2
+    k_adj_dl<T><<<site_grid(s), 256, 0, s->st>>>(a);
+    k_adj_grad<T><<<dim3(s->adj_cta, s->nrep), 256, sizeof(double) * 3 * n, s->st>>>(a, s->adj_partial);
+    k_adj_reduce<<<(3 * n + 255) / 256, 256, 0, s->st>>>(s->adj_partial, s->adj_cta * s->nrep, 3 * n, s->adj_grad);
+    s->launches += 8;
+    CK(cudaGetLastError());
+    if (grad) CK(cudaMemcpyAsync(grad, s->adj_grad, sizeof(double) * 3 * n, cudaMemcpyDefault, s->st));
+    std::vector<double> h(2 * s->nrep), er(s->nrep);
+    CK(cudaMemcpyAsync(h.data(), s->red_out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(er.data(), s->adj_eref, sizeof(double) * s->nrep, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    double L = 0.0;
+    for (int r = 0; r < s->nrep; ++r) {
+        const double N = (double)s->reps[r].ns;
+        const double de = (h[r] - er[r]) / N;
+        L += h[s->nrep + r] / (3.0 * N) + de * de;
+    }
+    if (loss) *loss = L;
+    return MISA_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1109,6 +1225,24 @@ static int ckpt_io(misa_sim *s, const char *path, bool save)
 
 int misa_save(misa_sim *s, const char *path) { return ckpt_io(s, path, true); }
 int misa_load(misa_sim *s, const char *path) { return ckpt_io(s, path, false); }
+
+int misa_set_tables(misa_sim *s, const double *f_knots, const double *phi_knots, const double *F_knots)
+{
+    if (!s) return MISA_EINVAL;
+    if (!f_knots || !phi_knots || !F_knots) return fail(s, MISA_EINVAL, "set_tables: three knot arrays required");
+    return s->prec == MISA_FP64 ? set_tables_impl<double>(s, f_knots, phi_knots, F_knots)
+                                : set_tables_impl<float>(s, f_knots, phi_knots, F_knots);
+}
+
+int misa_loss_grad(misa_sim *s, const double *Fref, const double *Eref, double *loss, double *grad)
+{
+    if (!s) return MISA_EINVAL;
+    if (!Fref || !Eref) return fail(s, MISA_EINVAL, "loss_grad: targets required");
+    int rc = s->prec == MISA_FP64 ? loss_grad_impl<double>(s, Fref, Eref, loss, grad)
+                                  : loss_grad_impl<float>(s, Fref, Eref, loss, grad);
+    if (rc) return rc;
+    return check_status(s);
+}
 
 int misa_tile_count(void) { return kNTiles; }
 

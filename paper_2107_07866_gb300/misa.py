@@ -109,6 +109,8 @@ def lib():
         L.misa_eam_forces_static.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
                                              C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
                                              C.c_void_p, C.c_void_p]
+        L.misa_set_tables.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.misa_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, _D, C.c_void_p]
         L.misa_tile_count.restype = C.c_int
         L.misa_tile_shape.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         _lib = L
@@ -215,6 +217,7 @@ class Sim:
         self.natoms = sum(2 * a * b * c for a, b, c in replicas)
         self.box = np.array([nx * a0, ny * a0, nz * a0])
         self.a0 = a0
+        self._n_knots = pot.n
         self.precision = p.precision
 
     # -- plumbing -----------------------------------------------------------
@@ -303,6 +306,25 @@ class Sim:
         n = C.c_int64()
         self._check(lib().misa_timing_get(self.h, ms, C.byref(n)))
         return dict(zip(PHASES, list(ms))), n.value
+
+    # -- potential fitting ----------------------------------------------------
+    def set_tables(self, f, phi, F):
+        """New knot values (numpy arrays or torch tensors, host or device)."""
+        f, phi, F = _f64(f), _f64(phi), _f64(F)
+        self._check(lib().misa_set_tables(self.h, _ptr(f), _ptr(phi), _ptr(F)))
+
+    def loss_grad(self, Fref, Eref, grad=None):
+        """Force-matching + energy loss of the current positions against
+        Fref (natoms x 3) and Eref (one per replica), and its gradient with
+        respect to the 3 x n knot values (f, phi, F).  grad may be a
+        preallocated numpy array or device tensor of 3n doubles."""
+        Fref = _f64(Fref)
+        Eref = _f64(np.atleast_1d(Eref)) if not hasattr(Eref, "data_ptr") else Eref
+        if grad is None:
+            grad = np.empty(3 * self._n_knots)
+        loss = C.c_double()
+        self._check(lib().misa_loss_grad(self.h, _ptr(Fref), _ptr(Eref), C.byref(loss), _ptr(grad)))
+        return loss.value, grad
 
     # -- batches --------------------------------------------------------------
     def replica_info(self, r):
