@@ -141,6 +141,11 @@ WORKLOADS = {
     "c4": dict(n=None, nrep=64, seed=4, dx_max=0.02, reassign=10,
                desc="64 batched replicas, dims ~ U{20..60}^3 cells (seeded), 300-900 K, 1-5 keV PKA each, "
                     "FP32 forces, adaptive dt per replica, steps captured in a CUDA graph, autotuned tile"),
+    # potential fitting: knot gradient of the force-matching + energy loss
+    "c5": dict(n=16, nrep=16, seed=5, sigma=0.02, adjoint=True,
+               desc="16 thermal snapshots of 16x16x16 cells (8,192 atoms each, 300-1500 K), targets from knots "
+                    "scaled by 1 + N(0, 0.02^2); one step = loss + gradient w.r.t. 3 x 5000 knots, FP32 pair "
+                    "arithmetic, FP64 bins"),
 }
 
 
@@ -221,15 +226,70 @@ def cpu_baseline(target_s=12.0, max_cells=100):
         n = min(max_cells, int(n * 1.6))
 
 
+def fitting_inputs(w, rank=0):
+    pot = synth.potential()
+    target = pot.scaled(*synth.knot_perturbation(pot.n, w["sigma"], w["seed"] + 1000 * rank))
+    _, snaps = synth.fitting_snapshots(w["nrep"], w["n"], w["seed"] + 1000 * rank)
+    return pot, target, snaps
+
+
+def oracle_grad_rate(w, n_snap=None, seconds=None):
+    """The oracle's loss gradient (target forces + gradient per snapshot) on
+    n_snap snapshots, or on as many as fit in ``seconds``; returns
+    (full-set gradient evaluations/s, snapshots done, seconds, cores).  The
+    oracle's gradient is a serial loop, so the whole sample runs on one core."""
+    from oracle import oracle as O
+    O.build()
+    pot, target, snaps = fitting_inputs(w)
+    op, ot = O.Pot(pot), O.Pot(target)
+    n = w["n"]
+    L = synth.box(n, n, n)
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        xs = snaps[k % len(snaps)]
+        _, _, e_, f_ = O.eam(ot, xs, L, mode=1, nthreads=1)
+        O.loss_grad(op, xs, L, f_, e_.sum(), mode=1)
+        k += 1
+        el = time.perf_counter() - t0
+        if (n_snap is not None and k >= n_snap) or (seconds is not None and el > seconds):
+            break
+    return k / len(snaps) / el, k, el, 1
+
+
+def run_reference_adjoint(args, ws):
+    w = WORKLOADS[args.workload]
+    oracle_grad_rate(w, n_snap=max(1, args.warmup // 3))
+    val, k, el, cores = oracle_grad_rate(w, n_snap=args.steps)
+    unit = "gradient evaluations/s"
+    line = {"impl": "reference", "metric": "gradient evaluations/s (loss + d loss / d knots over the snapshot set)",
+            "value": val, "unit": unit, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"oracle sample: one snapshot per step of the {args.workload} workload "
+                                   f"({w['desc']}), scaled to the {w['nrep']}-snapshot evaluation", "cache": "cpu"},
+            "cpu_baseline": {"value": val, "unit": unit, "cores": cores, "kind": "oracle",
+                             "sample": f"{k} snapshots (target forces + gradient each)"},
+            "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = init_dist()
     if rank != 0:
         return 0
     w = WORKLOADS[args.workload]
+    if w.get("adjoint"):
+        return run_reference_adjoint(args, ws)
     from oracle import oracle as O
     O.build()
     pot = synth.potential()
     op = O.Pot(pot)
+    if w.get("nrep"):
+        # batched workload: the oracle runs one replica-like box per sample
+        rep = synth.batch_replicas(w["nrep"], w["seed"])[0]
+        w = dict(w, T=rep.T, pka_eV=rep.pka_energy)
     # one bench step = one oracle MD step of a bounded sample of the workload:
     # a 24^3-cell box of the same crystal, potential, temperature and PKA
     n = args.ref_cells
@@ -252,6 +312,117 @@ def run_reference(args):
                              "sample": f"{args.steps} MD steps of a {n}^3-cell box per run"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+    return 0
+
+
+def run_adjoint(args):
+    """Gradient evaluations/s of misa_loss_grad on the fitting workload."""
+    import torch
+
+    ws, rank, local = init_dist()
+    torch.cuda.set_device(local)
+    from paper_2107_07866_gb300 import build
+    build.build()
+    from paper_2107_07866_gb300 import misa
+
+    w = WORKLOADS[args.workload]
+    n, nrep = w["n"], w["nrep"]
+    pot, target, snaps = fitting_inputs(w, rank)
+    x = np.concatenate(snaps)
+    natoms = len(x)
+    dims = [(n, n, n)] * nrep
+    N = 2 * n ** 3
+    with misa.Sim(target, replicas=dims, precision="fp64") as t:
+        t.set_state(x)
+        Fref = t.forces()
+        _, _, e = t.energies(per_atom=True)
+        Eref = np.array([e[k * N:(k + 1) * N].sum() for k in range(nrep)])
+    out = {}
+    for prec in ("fp32", "fp64"):
+        sim = misa.Sim(pot, replicas=dims, precision=prec)
+        sim.set_state(x)
+        Fd = torch.from_numpy(Fref).cuda()
+        Ed = torch.from_numpy(Eref).cuda()
+        gd = torch.empty(3 * pot.n, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            sim.loss_grad(Fd, Ed, grad=gd)
+        l0 = sim.stats()["launches"]
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clk = ClockSampler(local) if prec == "fp32" else None
+        if clk:
+            clk.__enter__()
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            loss, _ = sim.loss_grad(Fd, Ed, grad=gd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        if clk:
+            clk.__exit__(None, None, None)
+        el = barrier_max(ws, e0.elapsed_time(e1))
+        launches = sim.stats()["launches"] - l0
+        # e2e: knots, targets from host memory, gradient back to host
+        kh = [torch.from_numpy(a.copy()).pin_memory() for a in (pot.f, pot.phi, pot.F)]
+        Fh, Eh = torch.from_numpy(Fref).pin_memory(), torch.from_numpy(Eref).pin_memory()
+        gh = torch.empty(3 * pot.n, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sim.set_tables(*kh)
+            sim.loss_grad(Fh, Eh, grad=gh)
+        el2 = barrier_max(ws, time.perf_counter() - t0)
+        out[prec] = {"ms": el / args.steps, "value": ws * args.steps / (el / 1e3), "launches": launches,
+                     "loss": loss, "grad": gd.cpu().numpy(), "e2e": ws * args.steps / el2,
+                     "clocks": clk.summary() if clk else None}
+        # central differences of the loss on 8 seeded knots (FP64 handle)
+        if prec == "fp64":
+            g = out[prec]["grad"]
+            rng = np.random.default_rng(3)
+            hot = np.flatnonzero(np.abs(g) > 1e-3 * np.abs(g).max())
+            tabs = [pot.f.copy(), pot.phi.copy(), pot.F.copy()]
+            errs = []
+            for k in rng.choice(hot, 8, replace=False):
+                tb, j = divmod(int(k), pot.n)
+                h = 1e-6 * max(1.0, abs(tabs[tb][j]))
+                y0 = tabs[tb][j]
+                tabs[tb][j] = y0 + h
+                sim.set_tables(*tabs)
+                lp, _ = sim.loss_grad(Fref, Eref, grad=np.empty(3 * pot.n))
+                tabs[tb][j] = y0 - h
+                sim.set_tables(*tabs)
+                lm, _ = sim.loss_grad(Fref, Eref, grad=np.empty(3 * pot.n))
+                tabs[tb][j] = y0
+                errs.append(abs(g[k] - (lp - lm) / (2 * h)) / np.abs(g).max())
+            out[prec]["fd_err"] = max(errs)
+        sim.close()
+    g32, g64 = out["fp32"]["grad"], out["fp64"]["grad"]
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        val, k, _, cores = oracle_grad_rate(w, seconds=min(args.cpu_seconds, 20.0))
+        cpu = {"value": val, "unit": "gradient evaluations/s", "cores": cores, "kind": "oracle",
+               "sample": f"{k} snapshots of {N} atoms (target forces + loss gradient each), scaled to the "
+                         f"{nrep}-snapshot evaluation"}
+    if rank == 0:
+        r32 = out["fp32"]
+        line = {"metric": "gradient evaluations/s (loss + d loss / d knots over the snapshot set)",
+                "value": r32["value"], "unit": "gradient evaluations/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": r32["ms"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w["desc"], "atoms": natoms, "parallelism": f"replicas{ws}",
+                           "cache": "working set ~20 MB fits L2; each evaluation re-reads it (no flush)"},
+                "roofline": None, "cpu_baseline": cpu,
+                "e2e": {"value": r32["e2e"], "unit": "gradient evaluations/s",
+                        "h2d_bytes_per_step": 8 * (3 * pot.n + 3 * natoms + nrep),
+                        "d2h_bytes_per_step": 8 * (3 * pot.n + 1),
+                        "note": "knots, target forces and energies from pinned host memory; gradient and loss back"},
+                "gpu_launches": r32["launches"], "clocks": r32["clocks"],
+                "fp64_path": {"value": out["fp64"]["value"], "ms_per_step": out["fp64"]["ms"],
+                              "fd_rel_err": out["fp64"]["fd_err"]},
+                "fp32_vs_fp64_grad_rel": float(np.abs(g32 - g64).max() / np.abs(g64).max())}
+        print(json.dumps(line))
     return 0
 
 
@@ -436,6 +607,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if WORKLOADS[args.workload].get("adjoint"):
+        return run_adjoint(args)
     return run_gpu(args)
 
 
