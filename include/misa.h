@@ -239,6 +239,12 @@ int misa_loss_grad(misa_sim *s, const double *Fref, const double *Eref, double *
 int misa_tile_count(void);
 int misa_tile_shape(int index, int *tx, int *ty, int *tz);
 
+/* 1 if shape `index` (1-based) is built for `precision`, else 0.  The FP64
+ * gathers run one thread per site (2 tx ty tz <= 1024); the FP32 gathers run
+ * two sites per thread, the tile folded in z (tz even, tx ty tz <= 1024).
+ * Creating a handle with a shape its precision lacks returns MISA_EINVAL. */
+int misa_tile_valid(int precision, int index);
+
 /* Tile shape in use (1-based index; chosen by the autotuner when
  * misa_params.tile is 0: each shape's density + force passes are timed on
  * the initial crystal and the fastest kept). */

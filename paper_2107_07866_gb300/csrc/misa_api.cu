@@ -13,6 +13,7 @@
 
 #include "misa.h"
 #include "misa_adjoint.cuh"
+#include "misa_packed.cuh"
 
 using namespace misa;
 
@@ -24,8 +25,18 @@ constexpr double kRfloor = 1e-4;                      // A
 struct TileShape {
     int tx, ty, tz;
 };
-constexpr TileShape kTiles[] = {{8, 8, 8}, {8, 8, 4}, {8, 4, 4}, {16, 8, 4}};
+constexpr TileShape kTiles[] = {{8, 8, 8}, {8, 8, 4}, {8, 4, 4}, {16, 8, 4}, {8, 8, 16}};
 constexpr int kNTiles = sizeof(kTiles) / sizeof(kTiles[0]);
+
+// Shapes each precision's gathers are built for: FP64 runs one thread per
+// site (2 tx ty tz <= 1024); FP32 runs two sites per thread folded in z
+// (tz even, tx ty tz <= 1024); each parity fills whole warps.
+constexpr bool tile_ok(int prec, const TileShape &t)
+{
+    const int cells = t.tx * t.ty * t.tz;
+    if (prec == MISA_FP64) return 2 * cells <= 1024 && cells % 32 == 0;
+    return t.tz % 2 == 0 && cells <= 1024 && (cells / 2) % 32 == 0;
+}
 
 std::string g_create_error;
 
@@ -74,6 +85,7 @@ struct misa_sim {
     long long ntile_cap = 0;    // tile_flag / tile_rep capacity (smallest tile shape)
     int ntiles = 0;
     size_t smem_density = 0, smem_force = 0;
+    bool dens_db = false;  // FP32 density pass double-buffers its tiles
     long long launches = 0;
     // phase timing
     bool timing = false;
@@ -244,8 +256,9 @@ void fill_gather(misa_sim *s, GatherArgs<T> &g)
     g.acc_conv = kAccUnit / s->p.mass;
     g.kick = 1;
     // neighbour offset index for this tile shape (Sec. 3): per parity, the
-    // shared-memory slot displacement of every lattice vector
-    const int SX = ts.tx + 4, SY = ts.ty + 4, SZ = ts.tz + 4;
+    // shared-memory slot displacement of every lattice vector (FP32: in the
+    // tile folded in z, two sites per slot)
+    const int SX = ts.tx + 4, SY = ts.ty + 4, SZ = sizeof(T) == 4 ? ts.tz / 2 + 4 : ts.tz + 4;
     const int PLANE = SX * SY * SZ;
     for (int par = 0; par < 2; ++par)
         for (int k = 0; k < kNVec; ++k) {
@@ -274,12 +287,22 @@ void fill_gather(misa_sim *s, GatherArgs<T> &g)
     }
 }
 
+// FP32: the table window plus one zero segment, the folded tile (two
+// buffers for the density pass when they fit); FP64: tables in global memory.
 template <typename T>
-size_t smem_density_bytes(misa_sim *s)
+size_t smem_density_bytes(misa_sim *s, size_t optin)
 {
     const TileShape &ts = kTiles[s->tile];
     const size_t nwin = (size_t)(s->p.n_knots - 1 - seg_lo_of(s));
-    return gather_smem_bytes<T>(sizeof(T) == 4 ? sizeof(Vec4<T>) * nwin : 0, ts.tx, ts.ty, ts.tz, tile_buffers<T>());
+    if constexpr (sizeof(T) == 4) {
+        const size_t tb = sizeof(float4) * (nwin + 1);
+        const size_t two = packed_smem_bytes(tb, ts.tx, ts.ty, ts.tz, 2);
+        s->dens_db = two <= optin;
+        return s->dens_db ? two : packed_smem_bytes(tb, ts.tx, ts.ty, ts.tz, 1);
+    } else {
+        s->dens_db = false;
+        return gather_smem_bytes<T>(0, ts.tx, ts.ty, ts.tz, tile_buffers<T>());
+    }
 }
 
 template <typename T>
@@ -287,42 +310,83 @@ size_t smem_force_bytes(misa_sim *s)
 {
     const TileShape &ts = kTiles[s->tile];
     const size_t nwin = (size_t)(s->p.n_knots - 1 - seg_lo_of(s));
-    return gather_smem_bytes<T>(sizeof(T) == 4 ? (sizeof(Vec4<T>) + sizeof(Vec2<T>)) * nwin : 0, ts.tx, ts.ty, ts.tz,
-                                (kForceBuffers == 2 && tile_buffers<T>() == 2) ? 2 : 1);
+    if constexpr (sizeof(T) == 4)
+        return packed_smem_bytes((sizeof(float4) + sizeof(float2)) * (nwin + 1), ts.tx, ts.ty, ts.tz, 1);
+    else
+        return gather_smem_bytes<T>(0, ts.tx, ts.ty, ts.tz, 1);
 }
 
-// one instantiation of the tile kernels per tile shape
+// one instantiation of the tile kernels per tile shape: FP32 the packed
+// two-sites-per-thread gathers, FP64 one thread per site
 template <typename T, int TX, int TY, int TZ>
 struct TileKernels {
+    static constexpr bool kF32 = sizeof(T) == 4;
+    static constexpr bool kBuilt = kF32 ? (TZ % 2 == 0 && TX * TY * TZ <= 1024) : (2 * TX * TY * TZ <= 1024);
     static int attrs(misa_sim *s)
     {
-        CK(cudaFuncSetAttribute(k_density<T, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_density));
-        CK(cudaFuncSetAttribute(k_density<T, TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_density));
-        CK(cudaFuncSetAttribute(k_force<T, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_force));
-        CK(cudaFuncSetAttribute(k_force<T, TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_force));
-        return MISA_OK;
+        if constexpr (!kBuilt) {
+            return MISA_EINVAL;
+        } else if constexpr (kF32) {
+            const int d = (int)s->smem_density, f = (int)s->smem_force;
+            CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
+            CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
+            CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
+            CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
+            CK(cudaFuncSetAttribute(k_force_p<TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, f));
+            CK(cudaFuncSetAttribute(k_force_p<TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, f));
+            return MISA_OK;
+        } else {
+            CK(cudaFuncSetAttribute(k_density<T, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_density));
+            CK(cudaFuncSetAttribute(k_density<T, TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_density));
+            CK(cudaFuncSetAttribute(k_force<T, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_force));
+            CK(cudaFuncSetAttribute(k_force<T, TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_force));
+            return MISA_OK;
+        }
     }
     static void density(misa_sim *s, const GatherArgs<T> &g, int grid, bool energy)
     {
-        constexpr int nt = 2 * TX * TY * TZ;
-        if (energy) k_density<T, TX, TY, TZ, true><<<grid, nt, s->smem_density, s->st>>>(g);
-        else k_density<T, TX, TY, TZ, false><<<grid, nt, s->smem_density, s->st>>>(g);
+        if constexpr (!kBuilt) {
+            return;
+        } else if constexpr (kF32) {
+            constexpr int nt = TX * TY * TZ;
+            const size_t b = s->smem_density;
+            if (s->dens_db) {
+                if (energy) k_density_p<TX, TY, TZ, true, true><<<grid, nt, b, s->st>>>(g);
+                else k_density_p<TX, TY, TZ, false, true><<<grid, nt, b, s->st>>>(g);
+            } else {
+                if (energy) k_density_p<TX, TY, TZ, true, false><<<grid, nt, b, s->st>>>(g);
+                else k_density_p<TX, TY, TZ, false, false><<<grid, nt, b, s->st>>>(g);
+            }
+        } else {
+            constexpr int nt = 2 * TX * TY * TZ;
+            if (energy) k_density<T, TX, TY, TZ, true><<<grid, nt, s->smem_density, s->st>>>(g);
+            else k_density<T, TX, TY, TZ, false><<<grid, nt, s->smem_density, s->st>>>(g);
+        }
     }
     static void force(misa_sim *s, const GatherArgs<T> &g, int grid, bool energy)
     {
-        constexpr int nt = 2 * TX * TY * TZ;
-        if (energy) k_force<T, TX, TY, TZ, true><<<grid, nt, s->smem_force, s->st>>>(g);
-        else k_force<T, TX, TY, TZ, false><<<grid, nt, s->smem_force, s->st>>>(g);
+        if constexpr (!kBuilt) {
+            return;
+        } else if constexpr (kF32) {
+            constexpr int nt = TX * TY * TZ;
+            if (energy) k_force_p<TX, TY, TZ, true><<<grid, nt, s->smem_force, s->st>>>(g);
+            else k_force_p<TX, TY, TZ, false><<<grid, nt, s->smem_force, s->st>>>(g);
+        } else {
+            constexpr int nt = 2 * TX * TY * TZ;
+            if (energy) k_force<T, TX, TY, TZ, true><<<grid, nt, s->smem_force, s->st>>>(g);
+            else k_force<T, TX, TY, TZ, false><<<grid, nt, s->smem_force, s->st>>>(g);
+        }
     }
 };
 
-// kTiles order: {8,8,8}, {8,8,4}, {8,4,4}, {16,8,4}
+// kTiles order: {8,8,8}, {8,8,4}, {8,4,4}, {16,8,4}, {8,8,16}
 #define MISA_TILE_DISPATCH(T, idx, CALL)                      \
     switch (idx) {                                            \
     case 0: TileKernels<T, 8, 8, 8>::CALL; break;             \
     case 1: TileKernels<T, 8, 8, 4>::CALL; break;             \
     case 2: TileKernels<T, 8, 4, 4>::CALL; break;             \
-    default: TileKernels<T, 16, 8, 4>::CALL; break;           \
+    case 3: TileKernels<T, 16, 8, 4>::CALL; break;            \
+    default: TileKernels<T, 8, 8, 16>::CALL; break;           \
     }
 
 // Sets the tile shape: tile counts of every replica, the global tile ->
@@ -349,8 +413,14 @@ int configure(misa_sim *s, int tile)
     CK(cudaMemcpyAsync(s->reps_d, s->reps.data(), sizeof(RepDesc) * s->nrep, cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->tile_rep, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, s->st));
     CK(cudaStreamSynchronize(s->st));  // map is a host temporary
-    s->smem_density = smem_density_bytes<T>(s);
+    if (!tile_ok(s->prec, ts)) return fail(s, MISA_EINVAL, "tile shape not built for this precision");
+    int dev = 0, optin = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    s->smem_density = smem_density_bytes<T>(s, (size_t)optin);
     s->smem_force = smem_force_bytes<T>(s);
+    if (s->smem_density > (size_t)optin || s->smem_force > (size_t)optin)
+        return fail(s, MISA_EINVAL, "tile shape and table window exceed the shared memory of a block");
     int arc = MISA_OK;
     MISA_TILE_DISPATCH(T, s->tile, attrs(s) == MISA_OK ? (void)0 : (void)(arc = MISA_ECUDA));
     if (arc) return fail(s, arc, s->err.empty() ? "tile kernel attributes" : s->err);
@@ -480,6 +550,7 @@ int autotune(misa_sim *s)
     float best = 1e30f;
     int best_k = 0;
     for (int k = 0; k < kNTiles; ++k) {
+        if (!tile_ok(s->prec, kTiles[k])) continue;
         int rc = configure<T>(s, k);
         if (rc) return rc;
         rc = launch_forces<T>(s, 0, false);  // warm-up
@@ -669,6 +740,7 @@ int validate(const misa_params &p, misa_sim *s)
     if (!(p.dt_max > 0) || p.dx_max < 0) return fail(s, MISA_EINVAL, "dt_max > 0, dx_max >= 0");
     if (!!p.alloc != !!p.free) return fail(s, MISA_EINVAL, "alloc and free hooks come together");
     if (p.tile < 0 || p.tile > kNTiles) return fail(s, MISA_EINVAL, "tile index");
+    if (p.tile > 0 && !tile_ok(p.precision, kTiles[p.tile - 1])) return fail(s, MISA_EINVAL, "tile shape not built for this precision");
     return MISA_OK;
 }
 
@@ -1257,6 +1329,13 @@ int misa_tile_shape(int index, int *tx, int *ty, int *tz)
 }
 
 int misa_tile_current(const misa_sim *s) { return s ? s->tile + 1 : 0; }
+
+int misa_tile_valid(int precision, int index)
+{
+    if (index < 1 || index > kNTiles) return 0;
+    if (precision != MISA_FP64 && precision != MISA_FP32_FORCE) return 0;
+    return tile_ok(precision, kTiles[index - 1]) ? 1 : 0;
+}
 
 }  // extern "C"
 

@@ -112,6 +112,7 @@ def lib():
         L.misa_set_tables.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.misa_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, _D, C.c_void_p]
         L.misa_tile_count.restype = C.c_int
+        L.misa_tile_valid.argtypes = [C.c_int, C.c_int]
         L.misa_tile_shape.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         _lib = L
     return _lib
@@ -367,6 +368,7 @@ class Sim:
 
 
 def tile_shapes():
+    """All built tile shapes (cells), index k - 1 for misa tile index k."""
     L = lib()
     out = []
     for k in range(1, L.misa_tile_count() + 1):
@@ -374,3 +376,10 @@ def tile_shapes():
         L.misa_tile_shape(k, C.byref(a), C.byref(b), C.byref(c))
         out.append((a.value, b.value, c.value))
     return out
+
+
+def tile_indices(precision):
+    """1-based tile indices built for a precision ("fp32" or "fp64")."""
+    L = lib()
+    code = {"fp64": FP64, "fp32": FP32_FORCE}[precision] if isinstance(precision, str) else int(precision)
+    return [k for k in range(1, L.misa_tile_count() + 1) if L.misa_tile_valid(code, k)]

@@ -59,9 +59,16 @@ def test_tile_shapes_are_warp_parity_pure(libmisa):
     from paper_2107_07866_gb300 import misa
     shapes = misa.tile_shapes()
     assert shapes
-    for tx, ty, tz in shapes:
-        # one thread per site, 2 tx ty tz <= 1024; each parity fills whole warps
-        assert 2 * tx * ty * tz <= 1024 and (tx * ty * tz) % 32 == 0
+    fp64, fp32 = misa.tile_indices("fp64"), misa.tile_indices("fp32")
+    assert 1 in fp64 and 1 in fp32
+    for k, (tx, ty, tz) in enumerate(shapes, 1):
+        cells = tx * ty * tz
+        # FP64: one thread per site; FP32: two sites per thread, z folded in
+        # halves; each parity fills whole warps, at most 1024 threads
+        assert (k in fp64) == (2 * cells <= 1024 and cells % 32 == 0)
+        assert (k in fp32) == (tz % 2 == 0 and cells <= 1024 and (cells // 2) % 32 == 0)
+    assert libmisa.misa_tile_valid(0, 0) == 0 and libmisa.misa_tile_valid(0, len(shapes) + 1) == 0
+    assert libmisa.misa_tile_valid(7, 1) == 0
 
 
 def test_create_rejects_bad_parameters_without_a_gpu(libmisa):

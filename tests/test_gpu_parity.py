@@ -96,7 +96,7 @@ def test_perfect_crystal_zero_force(misa, pot, oracle, opot, prec):
 def test_tile_shapes_bitwise_equal(misa, pot, prec):
     x = synth.cascade_snapshot(12, 9, 10, 0.12, 24, 8, 2)
     ref = None
-    for t in range(1, len(misa.tile_shapes()) + 1):
+    for t in misa.tile_indices(prec):
         with misa.Sim(pot, 12, 9, 10, precision=prec, tile=t) as s:
             s.set_state(x)
             f = s.forces()
