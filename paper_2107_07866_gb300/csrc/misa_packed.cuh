@@ -467,6 +467,8 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_density_p(const __grid_consta
     const float2 S2 = p_dup(a.S);
     unsigned st = 0;
     int buf = 0;
+    // double-buffered: the next tile streams in (cp.async) during the whole
+    // tile; single buffer: plain loads at the top of each tile
     if constexpr (DB) {
         if ((int)blockIdx.x < a.ntiles) issue_tile_p<TX, TY, TZ, false>(a, sm.rep, sm.tA, blockIdx.x);
         cp_async_commit();
@@ -553,6 +555,9 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_density_p(const __grid_consta
 // force pass + closing half kick
 // ---------------------------------------------------------------------------
 
+// The tile loop overlaps the staging of the next tile with the FP64 kick
+// epilogue of the current one: once every thread has read the staged tile,
+// the next tile's copies are issued (cp.async) and fly while the kick runs.
 template <int TX, int TY, int TZ, bool ENERGY>
 __global__ void __launch_bounds__(TX *TY *TZ, 1) k_force_p(const __grid_constant__ GatherArgs<float> a)
 {
@@ -579,20 +584,23 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_force_p(const __grid_constant
     const float conv = (float)a.acc_conv;
     unsigned st = 0;
     int cur_rep = -1;
-    double vmax2 = 0.0;
+    unsigned long long vmax2 = 0;  // bits of a non-negative double: integer order = value order
+    float4 *cA = sm.tA;
+    const float4 *cB = cA + 2 * G::PLANE;
+    if ((int)blockIdx.x < a.ntiles) issue_tile_p<TX, TY, TZ, true>(a, sm.rep, cA, blockIdx.x);
+    cp_async_commit();
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         double dt_rep;
         int nra;
         const TileLoc L = locate_cached(a, sm.rep, tile, TX, TY, TZ, dt_rep, nra);
         if (a.kick && L.rep != cur_rep) {
-            if (cur_rep >= 0) flush_vmax<G::NT>(vmax2, sm.red, a.sc + cur_rep);
+            if (cur_rep >= 0) flush_vmax<G::NT>(__longlong_as_double((long long)vmax2), sm.red, a.sc + cur_rep);
             cur_rep = L.rep;
-            vmax2 = 0.0;
+            vmax2 = 0;
         }
-        float4 *cA = sm.tA;
-        const float4 *cB = cA + 2 * G::PLANE;
+        cp_async_wait<0>();
         __syncthreads();
-        const float U = stage_tile_p<TX, TY, TZ, true>(a, L, cA, sm.red);
+        const float U = tile_umax_p<TX, TY, TZ>(cA, sm.red);
         const double hdt = 0.5 * dt_rep;
         const bool has_ra = a.tile_flag[tile] != 0 && nra > 0;
         const bool in_xy = (L.c0x + th.lx < L.rd.nx) && (L.c0y + th.ly < L.rd.ny);
@@ -629,6 +637,11 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_force_p(const __grid_constant
                 if (pos >= nra) break;
             }
         }
+        // every read of the staged tile is done: stage the next one during the kick
+        __syncthreads();
+        const int nxt = tile + gridDim.x;
+        if (nxt < a.ntiles) issue_tile_p<TX, TY, TZ, true>(a, sm.rep, cA, nxt);
+        cp_async_commit();
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             if (!(h ? live_b : live_a)) continue;
@@ -647,12 +660,14 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_force_p(const __grid_constant
                 a.vy[sid] = vy;
                 a.vz[sid] = vz;
                 const double v2 = vx * vx + vy * vy + vz * vz;
-                vmax2 = v2 > vmax2 ? v2 : vmax2;
+                const unsigned long long b = (unsigned long long)__double_as_longlong(v2);
+                vmax2 = b > vmax2 ? b : vmax2;
             }
             if (ENERGY) a.e_out[sid] += h ? eb : ea;
         }
     }
-    if (a.kick && cur_rep >= 0) flush_vmax<G::NT>(vmax2, sm.red, a.sc + cur_rep);
+    cp_async_wait<0>();
+    if (a.kick && cur_rep >= 0) flush_vmax<G::NT>(__longlong_as_double((long long)vmax2), sm.red, a.sc + cur_rep);
     if (st) atomicOr(&a.sc[0].status, st);
 }
 
