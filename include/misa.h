@@ -239,6 +239,15 @@ int misa_loss_grad(misa_sim *s, const double *Fref, const double *Eref, double *
 int misa_tile_count(void);
 int misa_tile_shape(int index, int *tx, int *ty, int *tz);
 
+/* Self-test of the library's float <-> double conversions done with integer
+ * operations (used by the FP64 integration kernels; no counterpart in the
+ * paper) against the GPU's own conversions on n generated bit patterns.
+ * mismatches[0] counts double -> float, mismatches[1] float -> double
+ * disagreements (a subnormal result flushed to a signed zero is not one).
+ * Runs on the current device, synchronises; MISA_EINVAL for n <= 0 or a
+ * null pointer, MISA_ECUDA on a CUDA error. */
+int misa_selftest(long long n, long long *mismatches);
+
 /* 1 if shape `index` (1-based) is built for `precision`, else 0.  The FP64
  * gathers run one thread per site (2 tx ty tz <= 1024); the FP32 gathers run
  * two sites per thread, the tile folded in z (tz even, tx ty tz <= 1024).

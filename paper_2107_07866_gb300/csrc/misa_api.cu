@@ -19,6 +19,54 @@ using namespace misa;
 
 namespace {
 
+// Self-test of the integer-pipe conversions against the hardware ones on
+// generated bit patterns: [0] double -> float, [1] float -> double.  A
+// subnormal hardware result is matched by a zero of the same sign.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_selftest_conv(unsigned long long n, unsigned long long *bad)
+{
+    unsigned long long b0 = 0, b1 = 0;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long h = mix64(i);
+        unsigned long long bits = h;
+        const unsigned long long keep = 0x800fffffffffffffull;
+        switch (i % 4) {
+        case 0:  // binary32 normal range
+            bits = (h & keep) | ((897ull + (h >> 52) % 254ull) << 52);
+            break;
+        case 1:  // exact halfway between two binary32 values
+            bits = (((h & keep) | ((897ull + (h >> 52) % 254ull) << 52)) & ~0x1fffffffull) | 0x10000000ull;
+            break;
+        case 2:  // any exponent
+            break;
+        default:  // around the binary32 underflow and overflow thresholds
+            bits = (h & keep) | ((((h >> 52) & 1ull) ? 860ull + (h >> 53) % 40ull : 1140ull + (h >> 53) % 20ull) << 52);
+        }
+        const double d = __longlong_as_double((long long)bits);
+        const float want = __double2float_rn(d), got = d2f_bits(d);
+        const unsigned wb = __float_as_uint(want), gb = __float_as_uint(got);
+        const bool wsub = (wb & 0x7f800000u) == 0u && (wb & 0x7fffffu) != 0u;
+        if (!(wb == gb || (want != want && got != got) || (wsub && gb == (wb & 0x80000000u)))) ++b0;
+        const float f = __uint_as_float((unsigned)(h >> 32) ^ (unsigned)h);
+        const double wd = (double)f, gd = f2d_bits(f);
+        const unsigned long long wdb = (unsigned long long)__double_as_longlong(wd);
+        const unsigned long long gdb = (unsigned long long)__double_as_longlong(gd);
+        const unsigned fb = __float_as_uint(f);
+        const bool fsub = (fb & 0x7f800000u) == 0u && (fb & 0x7fffffu) != 0u;
+        if (!(wdb == gdb || (wd != wd && gd != gd) || (fsub && gdb == ((unsigned long long)(fb >> 31) << 63)))) ++b1;
+    }
+    if (b0) atomicAdd(bad, b0);
+    if (b1) atomicAdd(bad + 1, b1);
+}
+
 constexpr double kAccUnit = 9.6485332123310018e-3;  // 1 eV/(A amu) in A/fs^2 (CODATA 2018)
 constexpr double kRfloor = 1e-4;                      // A
 
@@ -1329,6 +1377,25 @@ int misa_tile_shape(int index, int *tx, int *ty, int *tz)
 }
 
 int misa_tile_current(const misa_sim *s) { return s ? s->tile + 1 : 0; }
+
+int misa_selftest(long long n, long long *mismatches)
+{
+    if (n <= 0 || !mismatches) return MISA_EINVAL;
+    unsigned long long *d = nullptr;
+    if (cudaMalloc(&d, 2 * sizeof(unsigned long long)) != cudaSuccess) return MISA_ECUDA;
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaMemset(d, 0, sizeof(h));
+    if (e == cudaSuccess) {
+        k_selftest_conv<<<1024, 256>>>((unsigned long long)n, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return MISA_ECUDA;
+    mismatches[0] = (long long)h[0];
+    mismatches[1] = (long long)h[1];
+    return MISA_OK;
+}
 
 int misa_tile_valid(int precision, int index)
 {

@@ -140,6 +140,40 @@ struct alignas(2 * sizeof(T)) Vec2 {
     T x, y;
 };
 
+// Float <-> double conversions on the integer pipe (IEEE-754 binary32 /
+// binary64 bit layouts).  GB300 runs FP64 (and its conversions) at a small
+// fraction of the FP32 rate, while the FP64-bound integration kernels leave
+// the integer pipe idle.  Both are exact for zero and every normal value
+// (round to nearest even for double -> float); subnormal results flush to a
+// signed zero; infinities and NaNs stay infinities and NaNs.
+__device__ __forceinline__ double f2d_bits(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    const unsigned long long mant = (unsigned long long)(b & 0x7fffffu) << 29;
+    const unsigned long long ex = e == 0xffu ? 0x7ffull << 52 : (unsigned long long)(e + 896u) << 52;
+    return __longlong_as_double((long long)(e == 0u ? sign : (sign | ex | mant)));
+}
+
+__device__ __forceinline__ float d2f_bits(double d)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const unsigned e11 = (hi >> 20) & 0x7ffu;
+    const int e = (int)e11 - 896;                                // binary32 biased exponent
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);       // top 23 mantissa bits
+    const unsigned g = (lo >> 28) & 1u;                           // first dropped bit
+    const unsigned sticky = (lo & 0x0fffffffu) != 0u ? 1u : 0u;   // any later dropped bit
+    unsigned r = ((unsigned)e << 23) + m;
+    r += g & (sticky | (m & 1u));  // a carry moves into the exponent (and to infinity at the top)
+    if (e <= 0) r = 0u;
+    if (e >= 255) r = 0x7f800000u;
+    if (e11 == 0x7ffu) r = ((hi & 0xfffffu) | lo) != 0u ? 0x7fc00000u : 0x7f800000u;
+    return __uint_as_float(sign | r);
+}
+
 template <typename T>
 __device__ __forceinline__ Vec4<T> ld4(const Vec4<T> *p)
 {

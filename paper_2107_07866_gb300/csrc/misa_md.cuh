@@ -154,8 +154,11 @@ __global__ void k_end_step(MdArgs<T> m)
 
 // Opening half kick + drift of array atoms (FP64).  An atom leaving its
 // skin is demoted to its replica's run-away list (Alg. 2 part 1, skin reading).
+__device__ __forceinline__ double f2d(float x) { return f2d_bits(x); }
+__device__ __forceinline__ double f2d(double x) { return x; }
+
 template <typename T>
-__global__ void k_kick_drift(MdArgs<T> m)
+__global__ void __launch_bounds__(256, 4) k_kick_drift(MdArgs<T> m)
 {
     const int r = blockIdx.y;
     const RepDesc rd = m.reps[r];
@@ -167,14 +170,15 @@ __global__ void k_kick_drift(MdArgs<T> m)
         const long long s = rd.site_base + ls;
         int id = m.sid[s];
         if (id < 0) continue;
-        // FP64 integration; the skin test (a storage decision) in FP32
-        const double vx = fma(hdt, (double)m.ax[s], m.vx[s]);
-        const double vy = fma(hdt, (double)m.ay[s], m.vy[s]);
-        const double vz = fma(hdt, (double)m.az[s], m.vz[s]);
+        // FP64 integration; the skin test (a storage decision) in FP32;
+        // FP32 <-> FP64 conversions on the integer pipe
+        const double vx = fma(hdt, f2d(m.ax[s]), m.vx[s]);
+        const double vy = fma(hdt, f2d(m.ay[s]), m.vy[s]);
+        const double vz = fma(hdt, f2d(m.az[s]), m.vz[s]);
         const double ux = fma(dtl, vx, m.ux[s]);
         const double uy = fma(dtl, vy, m.uy[s]);
         const double uz = fma(dtl, vz, m.uz[s]);
-        const float fx = (float)ux, fy = (float)uy, fz = (float)uz;
+        const float fx = d2f_bits(ux), fy = d2f_bits(uy), fz = d2f_bits(uz);
         bool out;
         if constexpr (sizeof(T) == 4) out = fx * fx + fy * fy + fz * fz > skin2f;
         else out = ux * ux + uy * uy + uz * uz > m.skin2;

@@ -653,9 +653,9 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_force_p(const __grid_constant
             a.az[sid] = gz;
             if (!isfinite(gx) || !isfinite(gy) || !isfinite(gz)) st |= kStNonfinite;
             if (a.kick) {
-                const double vx = fma(hdt, (double)gx, a.vx[sid]);
-                const double vy = fma(hdt, (double)gy, a.vy[sid]);
-                const double vz = fma(hdt, (double)gz, a.vz[sid]);
+                const double vx = fma(hdt, f2d_bits(gx), a.vx[sid]);
+                const double vy = fma(hdt, f2d_bits(gy), a.vy[sid]);
+                const double vz = fma(hdt, f2d_bits(gz), a.vz[sid]);
                 a.vx[sid] = vx;
                 a.vy[sid] = vy;
                 a.vz[sid] = vz;

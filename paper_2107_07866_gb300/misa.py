@@ -113,6 +113,7 @@ def lib():
         L.misa_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, _D, C.c_void_p]
         L.misa_tile_count.restype = C.c_int
         L.misa_tile_valid.argtypes = [C.c_int, C.c_int]
+        L.misa_selftest.argtypes = [C.c_longlong, C.POINTER(C.c_longlong)]
         L.misa_tile_shape.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         _lib = L
     return _lib
@@ -376,6 +377,16 @@ def tile_shapes():
         L.misa_tile_shape(k, C.byref(a), C.byref(b), C.byref(c))
         out.append((a.value, b.value, c.value))
     return out
+
+
+def selftest(n=1 << 22):
+    """Mismatch counts (double -> float, float -> double) of the library's
+    integer-pipe conversions against the GPU's own on n bit patterns."""
+    out = (C.c_longlong * 2)()
+    code = lib().misa_selftest(n, out)
+    if code != MISA_OK:
+        raise MisaError(code, "misa_selftest failed")
+    return int(out[0]), int(out[1])
 
 
 def tile_indices(precision):

@@ -252,3 +252,9 @@ def test_runaway_overflow_is_reported(misa, pot):
             s.forces()
         assert e.value.code == misa.MISA_ERUNAWAY_OVERFLOW
         assert s.stats()["status"] & misa.ST_RUNAWAY_OVERFLOW
+
+
+def test_integer_pipe_conversions_match_hardware(misa):
+    # the FP64 integration kernels convert float <-> double with integer
+    # operations; they must agree bit for bit with the GPU's conversions
+    assert misa.selftest(1 << 22) == (0, 0)
