@@ -3,8 +3,9 @@
 
 Workload (the roofline headline case): bcc Fe-like crystal of 300 x 300 x 300
 cells (54,000,000 atoms), Finnis-Sinclair/Morse EAM tabulated on 5000-knot
-splines, Maxwell velocities at 600 K (seed 2), a 10 keV knock-on atom along a
-seeded direction, adaptive timestep (1 fs cap, 0.02 A max displacement),
+splines, an equilibrated crystal at 600 K (Gaussian displacements of
+0.1 A sqrt(T / 600 K) per component, Maxwell velocities, seed 2), a 10 keV
+knock-on atom along a seeded direction, adaptive timestep (1 fs cap, 0.02 A max displacement),
 hash update every 10 steps, FP32 force path with FP64 integration.  A bench
 "step" is one full MD step (kick/drift, hash update, density, embedding,
 force, kick, next timestep).  The state (~8 GB) is far larger than L2, so no
@@ -132,14 +133,14 @@ class ClockSampler:
 WORKLOADS = {
     # headline: the 54M-atom FP32-force cascade
     "c3": dict(n=300, T=600.0, seed=2, pka_eV=10000.0, dx_max=0.02, reassign=10,
-               desc="300x300x300 cells (54,000,000 atoms), 600 K seed 2, 10 keV PKA, FP32 forces, "
+               desc="300x300x300 cells (54,000,000 atoms), equilibrated at 600 K (seed 2), 10 keV PKA, FP32 forces, "
                     "adaptive dt (1 fs, 0.02 A), hash update every 10 steps"),
     # smaller cascade (parity-size check of the bench path)
     "c2": dict(n=100, T=600.0, seed=1, pka_eV=5000.0, dx_max=0.02, reassign=1,
-               desc="100x100x100 cells (2,000,000 atoms), 600 K seed 1, 5 keV PKA, adaptive dt, hash update every step"),
+               desc="100x100x100 cells (2,000,000 atoms), equilibrated at 600 K (seed 1), 5 keV PKA, adaptive dt, hash update every step"),
     # batched cascades: 64 uneven replicas in one handle, one launch per pass
     "c4": dict(n=None, nrep=64, seed=4, dx_max=0.02, reassign=10,
-               desc="64 batched replicas, dims ~ U{20..60}^3 cells (seeded), 300-900 K, 1-5 keV PKA each, "
+               desc="64 batched replicas, dims ~ U{20..60}^3 cells (seeded), equilibrated at 300-900 K, 1-5 keV PKA each, "
                     "FP32 forces, adaptive dt per replica, steps captured in a CUDA graph, autotuned tile"),
     # potential fitting: knot gradient of the force-matching + energy loss
     "c5": dict(n=16, nrep=16, seed=5, sigma=0.02, adjoint=True,
@@ -149,11 +150,24 @@ WORKLOADS = {
 }
 
 
+def thermal_sigma(T):
+    """Displacement std (A per component) of the equilibrated crystal at T."""
+    return 0.1 * math.sqrt(T / 600.0)
+
+
+def equilibrated(nx, ny, nz, T, seed):
+    """Positions and velocities of a crystal at temperature T: a cascade run
+    starts from an equilibrated lattice, not from perfect sites."""
+    x = synth.thermal_snapshot(nx, ny, nz, thermal_sigma(T), seed + 500)
+    v = synth.maxwell_velocities(len(x), T, synth.MASS_FE, seed)
+    return x, v
+
+
 def batch_inputs(w):
     reps = synth.batch_replicas(w["nrep"], w["seed"])
     dims = [(r.nx, r.ny, r.nz) for r in reps]
-    vs = [synth.maxwell_velocities(2 * r.nx * r.ny * r.nz, r.T, synth.MASS_FE, r.seed) for r in reps]
-    return reps, dims, np.concatenate(vs)
+    xv = [equilibrated(r.nx, r.ny, r.nz, r.T, r.seed) for r in reps]
+    return reps, dims, np.concatenate([a for a, _ in xv]), np.concatenate([b for _, b in xv])
 
 
 def init_dist():
@@ -185,10 +199,9 @@ def barrier(ws):
 
 def make_inputs(w, rank):
     n = w["n"]
-    natoms = 2 * n ** 3
-    v = synth.maxwell_velocities(natoms, w["T"], synth.MASS_FE, w["seed"] + 1000 * rank)
+    x, v = equilibrated(n, n, n, w["T"], w["seed"] + 1000 * rank)
     d = synth.random_direction(w["seed"] + 17 + 1000 * rank)
-    return v, d
+    return x, v, d
 
 
 def cpu_baseline(target_s=12.0, max_cells=100):
@@ -201,8 +214,7 @@ def cpu_baseline(target_s=12.0, max_cells=100):
     op = O.Pot(pot)
     n = 20
     while True:
-        x = synth.bcc_positions(n, n, n)
-        v = synth.maxwell_velocities(len(x), 600.0, synth.MASS_FE, 2)
+        x, v = equilibrated(n, n, n, 600.0, 2)
         L = synth.box(n, n, n)
         t0 = time.perf_counter()
         _, _, a, _, _ = O.md_run(op, x, v, L, synth.MASS_FE, 1.0, 0.02, 1, mode=1)
@@ -293,8 +305,7 @@ def run_reference(args):
     # one bench step = one oracle MD step of a bounded sample of the workload:
     # a 24^3-cell box of the same crystal, potential, temperature and PKA
     n = args.ref_cells
-    x = synth.bcc_positions(n, n, n)
-    v = synth.maxwell_velocities(len(x), w["T"], synth.MASS_FE, w["seed"])
+    x, v = equilibrated(n, n, n, w["T"], w["seed"])
     O.insert_pka(v, synth.pka_atom(n, n, n), synth.MASS_FE, w["pka_eV"], synth.random_direction(w["seed"] + 17))
     L = synth.box(n, n, n)
     x, v, a, _, _ = O.md_run(op, x, v, L, synth.MASS_FE, 1.0, w["dx_max"], args.warmup, mode=1)
@@ -439,26 +450,26 @@ def run_gpu(args):
     pot = synth.potential()
     batched = w.get("nrep") is not None
     if batched:
-        reps, dims, v = batch_inputs(w)
+        reps, dims, x, v = batch_inputs(w)
         natoms = len(v)
         n = None
         args.no_e2e = True
     else:
         n = w["n"]
         natoms = 2 * n ** 3
-        v, d = make_inputs(w, rank)
+        x, v, d = make_inputs(w, rank)
 
     def fresh(prec):
         if batched:
             s = misa.Sim(pot, replicas=dims, precision=prec, dt_max=1.0, dx_max=w["dx_max"],
                          reassign_period=w["reassign"], tile=args.tile)
-            s.set_velocities(v)
+            s.set_state(x, v)
             for r, rep in enumerate(reps):
                 s.insert_pka_replica(r, rep.pka_energy, rep.pka_dir)
             return s
         s = misa.Sim(pot, n, precision=prec, dt_max=1.0, dx_max=w["dx_max"], reassign_period=w["reassign"],
                      tile=args.tile)
-        s.set_velocities(v)
+        s.set_state(x, v)
         s.insert_pka(-1, w["pka_eV"], d)
         return s
 
@@ -523,7 +534,7 @@ def run_gpu(args):
     if not args.no_e2e:
         s = misa.Sim(pot, n, precision="fp32", dt_max=1.0, dx_max=w["dx_max"], reassign_period=w["reassign"],
                      tile=args.tile)
-        x_host = torch.from_numpy(synth.bcc_positions(n, n, n)).pin_memory()
+        x_host = torch.from_numpy(x).pin_memory()
         v0 = v.copy()
         pka = synth.pka_atom(n, n, n)
         spd = math.sqrt(2.0 * w["pka_eV"] / synth.MASS_FE / synth.EV_PER_AMU_A2_FS2)

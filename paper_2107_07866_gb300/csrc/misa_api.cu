@@ -115,6 +115,7 @@ struct misa_sim {
     void *a[3] = {};
     void *fp = nullptr, *rho = nullptr;
     double *esite = nullptr;
+    unsigned long long *bmask = nullptr;  // FP32: sparse-shell candidates inside rc, per site
     int *ra_home = nullptr, *ra_id = nullptr;
     double *ra_u[3] = {}, *ra_v[3] = {};
     void *ra_s[3] = {}, *ra_a[3] = {};
@@ -333,6 +334,8 @@ void fill_gather(misa_sim *s, GatherArgs<T> &g)
         sh.xfrac[q] = (float)(x0 - xi);
         sh.nshell = q + 1;
     }
+    g.bmask = s->bmask;
+    g.mask_ok = s->bmask && kLVec.shell_begin[sh.nshell] - kSparseK0 <= 64 ? 1 : 0;
 }
 
 // FP32: the table window plus one zero segment, the folded tile (two
@@ -655,6 +658,7 @@ int create_impl(misa_sim *s)
     s->fp = dalloc(s, Tb * ns);
     s->rho = dalloc(s, Tb * ns);
     s->esite = (double *)dalloc(s, sizeof(double) * ns);
+    if (sizeof(T) == 4) s->bmask = (unsigned long long *)dalloc(s, sizeof(unsigned long long) * ns);
     s->ra_home = (int *)dalloc(s, sizeof(int) * capt);
     s->ra_id = (int *)dalloc(s, sizeof(int) * capt);
     s->t_home = (int *)dalloc(s, sizeof(int) * capt);
@@ -674,7 +678,7 @@ int create_impl(misa_sim *s)
     s->aux_int = (int *)dalloc(s, sizeof(int) * ns);
     s->aux_dbl = (double *)dalloc(s, sizeof(double) * 3 * ns);
     if (!s->reps_d || !s->sc || !s->tile_rep || !s->tile_flag || !s->sid || !s->claim || !s->fp || !s->rho ||
-        !s->esite || !s->ra_home || !s->ra_id || !s->t_home || !s->t_id || !s->ra_fp || !s->ra_rho || !s->ra_e ||
+        !s->esite || (sizeof(T) == 4 && !s->bmask) || !s->ra_home || !s->ra_id || !s->t_home || !s->t_id || !s->ra_fp || !s->ra_rho || !s->ra_e ||
         !s->knots || !s->tab_f || !s->tab_phi || !s->tab_F || !s->tab_d0 || !s->tab_d1 || !s->partial ||
         !s->red_out || !s->out_buf || !s->aux_int || !s->aux_dbl)
         return fail(s, MISA_EOOM, "device allocation failed");
@@ -1474,6 +1478,7 @@ size_t carve_static(misa_sim *s, unsigned char *base, int nk)
     s->fp = c.take<T>(ns);
     s->rho = c.take<T>(ns);
     s->esite = c.take<double>(ns);
+    if (sizeof(T) == 4) s->bmask = c.take<unsigned long long>(ns);
     s->ra_home = c.take<int>(cap);
     s->ra_id = c.take<int>(cap);
     s->t_home = c.take<int>(cap);

@@ -195,6 +195,11 @@ struct GatherArgs {
     DevScalars *sc;         // per replica
     double acc_conv;        // (eV/A) -> (A/fs^2): 9.6485e-3 / m
     int kick;
+    // FP32 gathers: per site, which candidates of the sparse shells (|n|^2 > 12)
+    // the density pass found inside rc (bit k - first sparse candidate); the
+    // force pass evaluates only those.  mask_ok = 0: evaluate all of them.
+    unsigned long long *bmask;
+    int mask_ok;
     // neighbour offset index for this tile shape: per parity, per lattice
     // vector: (shared-memory slot displacement as int bits, 2 n_x, 2 n_y, 2 n_z)
     float4 off[2][kNVec];

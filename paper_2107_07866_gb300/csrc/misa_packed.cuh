@@ -17,9 +17,16 @@
 // it, so candidates outside rc -- and vacant sites, whose displacement is
 // the 1e4 sentinel -- contribute exactly zero without a mask.
 //
-// Per-site arithmetic is independent of the partner site: shells are summed
-// per site and added (Kahan) only for sites whose own reach includes the
-// shell, so results do not depend on the tile shape.
+// Sparse shells (|n|^2 > 12: at most a few of their candidates fall inside
+// rc) are screened before any geometry: a pair can only be inside rc if
+// |u_i| + |u_j| >= |n| - rc, and the density pass keeps |u_j|^2 in the
+// fourth plane slot for that test.  It records, per site, a bit for every
+// sparse candidate it found inside rc; the force pass, which sees the same
+// FP32 displacements and makes the same decisions, evaluates only those.
+//
+// Per-site arithmetic is independent of the partner site and of the tile:
+// a shell's sum is added (Kahan) only when it is non-zero, so shells that a
+// wider or narrower visit bound includes or skips change nothing.
 #pragma once
 
 #include "misa_kernels.cuh"
@@ -180,7 +187,9 @@ __device__ __forceinline__ float stage_tile_p(const GatherArgs<float> &a, const 
         const float xa = a.ux[sa], xb = a.ux[sb];
         const float ya = a.uy[sa], yb = a.uy[sb];
         const float za = a.uz[sa], zb = a.uz[sb];
-        const float fa = WITH_FP ? a.fp[sa] : 0.f, fb = WITH_FP ? a.fp[sb] : 0.f;
+        // force pass: F' of both sites; density pass: |u|^2 of both sites
+        const float fa = WITH_FP ? a.fp[sa] : xa * xa + ya * ya + za * za;
+        const float fb = WITH_FP ? a.fp[sb] : xb * xb + yb * yb + zb * zb;
         umax2 = fmaxf(umax2, fmaxf(occ_u2(xa, ya, za), occ_u2(xb, yb, zb)));
         sA[p * G::PLANE + r] = make_float4(xa, xb, ya, yb);
         sB[p * G::PLANE + r] = make_float4(za, zb, fa, fb);
@@ -216,15 +225,24 @@ __device__ __forceinline__ void issue_tile_p(const GatherArgs<float> &a, const R
     }
 }
 
-template <int TX, int TY, int TZ>
-__device__ __forceinline__ float tile_umax_p(const float4 *sA, float *sred)
+// Max |u| over the occupied slots of a staged tile, block-wide; with
+// WRITE_U2 (density pass) each slot's |u|^2 pair goes to plane B's zw.
+template <int TX, int TY, int TZ, bool WRITE_U2>
+__device__ __forceinline__ float tile_umax_p(float4 *sA, float *sred)
 {
     using G = PTile<TX, TY, TZ>;
-    const float4 *sB = sA + 2 * G::PLANE;
+    float4 *sB = sA + 2 * G::PLANE;
     float umax2 = 0.f;
     for (int q = threadIdx.x; q < 2 * G::PLANE; q += G::NT) {
-        const float4 A = sA[q], B = sB[q];
-        umax2 = fmaxf(umax2, fmaxf(occ_u2(A.x, A.z, B.x), occ_u2(A.y, A.w, B.y)));
+        const float4 A = sA[q];
+        float4 B = sB[q];
+        const float ua = A.x * A.x + A.z * A.z + B.x * B.x, ub = A.y * A.y + A.w * A.w + B.y * B.y;
+        umax2 = fmaxf(umax2, fmaxf(A.x < 0.5f * kVacant ? ua : 0.f, A.y < 0.5f * kVacant ? ub : 0.f));
+        if (WRITE_U2) {
+            B.z = ua;
+            B.w = ub;
+            sB[q] = B;
+        }
     }
     return sqrtf(block_max<G::NT>(umax2, sred)) * 1.000001f;
 }
@@ -276,101 +294,184 @@ struct PairSites {
     float2 ux, uy, uz, fp;  // the thread's two sites
 };
 
+// first sparse shell and its first candidate
+constexpr int first_sparse_shell()
+{
+    int s = 0;
+    while (s < kLVec.nshell && kLVec.shell_n2[s] <= 12) ++s;
+    return s;
+}
+constexpr int kSparseShell = first_sparse_shell();
+constexpr int kSparseK0 = kLVec.shell_begin[kSparseShell];
+
+// both pairs of candidate k: d = u_j - u_i, 2n and q = (2n + d).d
+struct PGeom {
+    float2 dx, dy, dz, nx2, ny2, nz2, q;
+};
+
+__device__ __forceinline__ PGeom pair_geom(const float4 o0, const float4 o1, const float4 A, const float4 B,
+                                           const PairSites &ui)
+{
+    PGeom g;
+    g.dx = p_sub(make_float2(A.x, A.y), ui.ux);
+    g.dy = p_sub(make_float2(A.z, A.w), ui.uy);
+    g.dz = p_sub(make_float2(B.x, B.y), ui.uz);
+    g.nx2 = make_float2(o0.x, o0.y);
+    g.ny2 = make_float2(o0.z, o0.w);
+    g.nz2 = make_float2(o1.x, o1.y);
+    g.q = p_fma(p_add(g.dz, g.nz2), g.dz, p_fma(p_add(g.dy, g.ny2), g.dy, p_mul(p_add(g.dx, g.nx2), g.dx)));
+    return g;
+}
+
+__device__ __forceinline__ void kahan_nz(Acc<float> &acc, float v)
+{
+    if (v != 0.f) acc.add(v);
+}
+
+// Screening bound of a sparse shell for one site: a neighbour j can only be
+// inside rc if |u_j|^2 >= thr (lattice units; -1: always).  A margin of
+// 1e-4 lattice units keeps every pair the FP32 geometry would place inside rc.
+__device__ __forceinline__ float screen_thr(float nrm, float rc_lat, float ui_norm, bool need)
+{
+    if (!need) return 3.0e38f;
+    const float gap = nrm - rc_lat - 1.0e-4f - ui_norm;
+    return gap > 0.f ? gap * gap * 0.99999f : -1.f;
+}
+
 template <int SH>
 __device__ __forceinline__ void density_shells_p(const ShellInfo &shc, int seg_lo, const float4 *__restrict__ po,
                                                  const float4 *__restrict__ sA, const float4 *__restrict__ sB, int slot,
-                                                 const PairSites &ui, float2 lim2, float2 S2, unsigned nwin,
-                                                 const float4 *__restrict__ tab, Acc<float> &ra, Acc<float> &rb)
+                                                 const PairSites &ui, float2 unorm, float rc_lat, float2 lim2, float2 S2,
+                                                 unsigned nwin, const float4 *__restrict__ tab, Acc<float> &ra,
+                                                 Acc<float> &rb, unsigned long long &ma, unsigned long long &mb)
 {
     if constexpr (SH < kLVec.nshell) {
         constexpr int KB = kLVec.shell_begin[SH], KE = kLVec.shell_begin[SH + 1];
         constexpr int N2 = kLVec.shell_n2[SH];
-        constexpr bool dense = N2 <= 12;
+        constexpr bool dense = SH < kSparseShell;
         const bool na = (float)N2 <= lim2.x, nb = (float)N2 <= lim2.y;
         if (SH >= shc.nshell || !(na || nb)) return;
         const PShell sh = pshell<SH>(shc, seg_lo);
         float2 part = make_float2(0.f, 0.f);
+        if constexpr (dense) {
 #pragma unroll 2
-        for (int k = KB; k < KE; ++k) {
-            const float4 o0 = po[2 * k], o1 = po[2 * k + 1];
-            const int D = __float_as_int(o1.z);
-            const float4 A = sA[slot + D], B = sB[slot + D];
-            const float2 dx = p_sub(make_float2(A.x, A.y), ui.ux);
-            const float2 dy = p_sub(make_float2(A.z, A.w), ui.uy);
-            const float2 dz = p_sub(make_float2(B.x, B.y), ui.uz);
-            const float2 q = p_fma(p_add(dz, make_float2(o1.x, o1.y)), dz,
-                                   p_fma(p_add(dy, make_float2(o0.z, o0.w)), dy,
-                                         p_mul(p_add(dx, make_float2(o0.x, o0.y)), dx)));
-            if (dense || q.x < sh.thr || q.y < sh.thr) {
+            for (int k = KB; k < KE; ++k) {
+                const float4 o0 = po[2 * k], o1 = po[2 * k + 1];
+                const int D = __float_as_int(o1.z);
+                const PGeom g = pair_geom(o0, o1, sA[slot + D], sB[slot + D], ui);
                 float2 t, rs;
                 int ia, ib;
-                arg_p(sh, q, S2, nwin, t, rs, ia, ib);
+                arg_p(sh, g.q, S2, nwin, t, rs, ia, ib);
                 part = p_add(part, make_float2(cubic(tab[ia], t.x), cubic(tab[ib], t.y)));
             }
+        } else {
+            const float ta = screen_thr(shc.nrm[SH], rc_lat, unorm.x, na);
+            const float tb = screen_thr(shc.nrm[SH], rc_lat, unorm.y, nb);
+            for (int k = KB; k < KE; ++k) {
+                const float4 o1 = po[2 * k + 1];
+                const int D = __float_as_int(o1.z);
+                const float4 B = sB[slot + D];  // zw: |u_j|^2 of both neighbours
+                if (B.z >= ta || B.w >= tb) {
+                    const PGeom g = pair_geom(po[2 * k], o1, sA[slot + D], B, ui);
+                    float2 t, rs;
+                    int ia, ib;
+                    arg_p(sh, g.q, S2, nwin, t, rs, ia, ib);
+                    part = p_add(part, make_float2(cubic(tab[ia], t.x), cubic(tab[ib], t.y)));
+                    const int bi = k - kSparseK0;
+                    if (bi < 64) {  // configurations with more sparse candidates run unmasked
+                        const unsigned long long bit = 1ull << bi;
+                        if (ia < (int)nwin) ma |= bit;
+                        if (ib < (int)nwin) mb |= bit;
+                    }
+                }
+            }
         }
-        if (na) ra.add(part.x);
-        if (nb) rb.add(part.y);
-        density_shells_p<SH + 1>(shc, seg_lo, po, sA, sB, slot, ui, lim2, S2, nwin, tab, ra, rb);
+        kahan_nz(ra, part.x);
+        kahan_nz(rb, part.y);
+        density_shells_p<SH + 1>(shc, seg_lo, po, sA, sB, slot, ui, unorm, rc_lat, lim2, S2, nwin, tab, ra, rb, ma, mb);
     }
 }
 
+// one candidate of the force pass for both sites, accumulated into p*
+template <bool ENERGY>
+__device__ __forceinline__ void force_pair_p(const PShell &sh, const PGeom &g, const float4 B, const PairSites &ui,
+                                             float2 S2, unsigned nwin, int seg_lo, const float4 *__restrict__ tab0,
+                                             const float2 *__restrict__ tab1, const Vec4<float> *__restrict__ gphi,
+                                             float2 &px, float2 &py, float2 &pz, double &ea, double &eb)
+{
+    float2 t, rs;
+    int ia, ib;
+    arg_p(sh, g.q, S2, nwin, t, rs, ia, ib);
+    const float4 ca = tab0[ia], cb = tab0[ib];
+    const float2 da = tab1[ia], db = tab1[ib];
+    const float2 dfr = make_float2(fmaf(fmaf(ca.x, t.x, ca.y), t.x, ca.z), fmaf(fmaf(cb.x, t.y, cb.y), t.y, cb.z));
+    const float2 dph = make_float2(fmaf(fmaf(ca.w, t.x, da.x), t.x, da.y), fmaf(fmaf(cb.w, t.y, db.x), t.y, db.y));
+    const float2 sc = p_mul(p_fma(p_add(ui.fp, make_float2(B.z, B.w)), dfr, dph), rs);
+    // r_ij = n + d, with n = (2n)/2 exactly
+    px = p_fma(sc, p_fma(p_dup(0.5f), g.nx2, g.dx), px);
+    py = p_fma(sc, p_fma(p_dup(0.5f), g.ny2, g.dy), py);
+    pz = p_fma(sc, p_fma(p_dup(0.5f), g.nz2, g.dz), pz);
+    if (ENERGY) {
+        const int ua = (int)nwin;
+        if (ia < ua) ea += 0.5 * (double)cubic(*reinterpret_cast<const float4 *>(&gphi[seg_lo + ia]), t.x);
+        if (ib < ua) eb += 0.5 * (double)cubic(*reinterpret_cast<const float4 *>(&gphi[seg_lo + ib]), t.y);
+    }
+}
+
+__device__ __forceinline__ void kahan3_nz(Acc<float> (&f)[3], float x, float y, float z)
+{
+    kahan_nz(f[0], x);
+    kahan_nz(f[1], y);
+    kahan_nz(f[2], z);
+}
+
+// Shells SH.. of the force pass.  Dense shells evaluate every candidate;
+// sparse shells evaluate the candidates set in msk (the union of both
+// sites' density-pass bits) or, without masks, every candidate that the
+// visit bound admits.
 template <int SH, bool ENERGY>
 __device__ __forceinline__ void force_shells_p(const ShellInfo &shc, int seg_lo, const float4 *__restrict__ po,
                                                const float4 *__restrict__ sA, const float4 *__restrict__ sB, int slot,
                                                const PairSites &ui, float2 lim2, float2 S2, unsigned nwin,
                                                const float4 *__restrict__ tab0, const float2 *__restrict__ tab1,
-                                               const Vec4<float> *__restrict__ gphi, Acc<float> (&fa)[3],
-                                               Acc<float> (&fb)[3], double &ea, double &eb)
+                                               const Vec4<float> *__restrict__ gphi, bool use_mask,
+                                               unsigned long long msk, Acc<float> (&fa)[3], Acc<float> (&fb)[3],
+                                               double &ea, double &eb)
 {
     if constexpr (SH < kLVec.nshell) {
         constexpr int KB = kLVec.shell_begin[SH], KE = kLVec.shell_begin[SH + 1];
         constexpr int N2 = kLVec.shell_n2[SH];
-        constexpr bool dense = N2 <= 12;
+        constexpr bool dense = SH < kSparseShell;
         const bool na = (float)N2 <= lim2.x, nb = (float)N2 <= lim2.y;
         if (SH >= shc.nshell || !(na || nb)) return;
         const PShell sh = pshell<SH>(shc, seg_lo);
         float2 px = make_float2(0.f, 0.f), py = px, pz = px;
+        if (dense || !use_mask) {
 #pragma unroll 2
-        for (int k = KB; k < KE; ++k) {
-            const float4 o0 = po[2 * k], o1 = po[2 * k + 1];
-            const int D = __float_as_int(o1.z);
-            const float4 A = sA[slot + D], B = sB[slot + D];
-            const float2 dx = p_sub(make_float2(A.x, A.y), ui.ux);
-            const float2 dy = p_sub(make_float2(A.z, A.w), ui.uy);
-            const float2 dz = p_sub(make_float2(B.x, B.y), ui.uz);
-            const float2 nx2 = make_float2(o0.x, o0.y), ny2 = make_float2(o0.z, o0.w), nz2 = make_float2(o1.x, o1.y);
-            const float2 q = p_fma(p_add(dz, nz2), dz, p_fma(p_add(dy, ny2), dy, p_mul(p_add(dx, nx2), dx)));
-            if (dense || q.x < sh.thr || q.y < sh.thr) {
-                float2 t, rs;
-                int ia, ib;
-                arg_p(sh, q, S2, nwin, t, rs, ia, ib);
-                const float4 ca = tab0[ia], cb = tab0[ib];
-                const float2 da = tab1[ia], db = tab1[ib];
-                const float2 dfr = make_float2(fmaf(fmaf(ca.x, t.x, ca.y), t.x, ca.z), fmaf(fmaf(cb.x, t.y, cb.y), t.y, cb.z));
-                const float2 dph = make_float2(fmaf(fmaf(ca.w, t.x, da.x), t.x, da.y), fmaf(fmaf(cb.w, t.y, db.x), t.y, db.y));
-                const float2 sc = p_mul(p_fma(p_add(ui.fp, make_float2(B.z, B.w)), dfr, dph), rs);
-                // r_ij = n + d, with n = (2n)/2 exactly
-                px = p_fma(sc, p_fma(p_dup(0.5f), nx2, dx), px);
-                py = p_fma(sc, p_fma(p_dup(0.5f), ny2, dy), py);
-                pz = p_fma(sc, p_fma(p_dup(0.5f), nz2, dz), pz);
-                if (ENERGY) {
-                    const int ua = (int)nwin;
-                    if (ia < ua) ea += 0.5 * (double)cubic(*reinterpret_cast<const float4 *>(&gphi[seg_lo + ia]), t.x);
-                    if (ib < ua) eb += 0.5 * (double)cubic(*reinterpret_cast<const float4 *>(&gphi[seg_lo + ib]), t.y);
-                }
+            for (int k = KB; k < KE; ++k) {
+                const float4 o0 = po[2 * k], o1 = po[2 * k + 1];
+                const int D = __float_as_int(o1.z);
+                const float4 B = sB[slot + D];
+                const PGeom g = pair_geom(o0, o1, sA[slot + D], B, ui);
+                if (dense || g.q.x < sh.thr || g.q.y < sh.thr)
+                    force_pair_p<ENERGY>(sh, g, B, ui, S2, nwin, seg_lo, tab0, tab1, gphi, px, py, pz, ea, eb);
+            }
+        } else {
+            unsigned long long sub = (msk >> (KB - kSparseK0)) & ((1ull << (KE - KB)) - 1ull);
+            while (sub) {
+                const int k = KB + __ffsll((long long)sub) - 1;
+                sub &= sub - 1ull;
+                const float4 o0 = po[2 * k], o1 = po[2 * k + 1];
+                const int D = __float_as_int(o1.z);
+                const float4 B = sB[slot + D];
+                const PGeom g = pair_geom(o0, o1, sA[slot + D], B, ui);
+                force_pair_p<ENERGY>(sh, g, B, ui, S2, nwin, seg_lo, tab0, tab1, gphi, px, py, pz, ea, eb);
             }
         }
-        if (na) {
-            fa[0].add(px.x);
-            fa[1].add(py.x);
-            fa[2].add(pz.x);
-        }
-        if (nb) {
-            fb[0].add(px.y);
-            fb[1].add(py.y);
-            fb[2].add(pz.y);
-        }
-        force_shells_p<SH + 1, ENERGY>(shc, seg_lo, po, sA, sB, slot, ui, lim2, S2, nwin, tab0, tab1, gphi, fa, fb, ea, eb);
+        kahan3_nz(fa, px.x, py.x, pz.x);
+        kahan3_nz(fb, px.y, py.y, pz.y);
+        force_shells_p<SH + 1, ENERGY>(shc, seg_lo, po, sA, sB, slot, ui, lim2, S2, nwin, tab0, tab1, gphi, use_mask,
+                                       msk, fa, fb, ea, eb);
     }
 }
 
@@ -486,7 +587,7 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_density_p(const __grid_consta
             cp_async_commit();
             cp_async_wait<1>();
             __syncthreads();
-            U = tile_umax_p<TX, TY, TZ>(cA, sm.red);
+            U = tile_umax_p<TX, TY, TZ, true>(cA, sm.red);
         } else {
             __syncthreads();
             U = stage_tile_p<TX, TY, TZ, false>(a, L, cA, sm.red);
@@ -504,11 +605,13 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_density_p(const __grid_consta
         const bool live_a = in_a && A.x < 0.5f * kVacant;
         const bool live_b = in_b && A.y < 0.5f * kVacant;
         Acc<float> ra, rb;
+        unsigned long long ma = 0, mb = 0;
         if (live_a || live_b) {
-            const float la = a.rc_lat + sqrtf(A.x * A.x + A.z * A.z + B.x * B.x) + U;
-            const float lb = a.rc_lat + sqrtf(A.y * A.y + A.w * A.w + B.y * B.y) + U;
+            const float2 un = make_float2(sqrtf(A.x * A.x + A.z * A.z + B.x * B.x), sqrtf(A.y * A.y + A.w * A.w + B.y * B.y));
+            const float la = a.rc_lat + un.x + U, lb = a.rc_lat + un.y + U;
             const float2 lim2 = make_float2(live_a ? la * la : -1.f, live_b ? lb * lb : -1.f);
-            density_shells_p<0>(a.sh, a.seg_lo, po, cA, cB, th.slot, ui, lim2, S2, (unsigned)nwin, tab, ra, rb);
+            density_shells_p<0>(a.sh, a.seg_lo, po, cA, cB, th.slot, ui, un, a.rc_lat, lim2, S2, (unsigned)nwin, tab, ra,
+                                rb, ma, mb);
         }
         if (has_ra) {
             int pos = 0;
@@ -533,6 +636,7 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_density_p(const __grid_consta
                 a.fp_out[sid] = 0.f;  // vacant: F' = 0 keeps every product with it finite
                 continue;
             }
+            if (a.mask_ok) a.bmask[sid] = h ? mb : ma;
             const float rh = (h ? rb : ra).value();
             float dF;
             const float Fv = embed<float>(a.tab_F, a.nseg, a.Srho, a.rho_max, rh, dF, st);
@@ -600,7 +704,7 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_force_p(const __grid_constant
         }
         cp_async_wait<0>();
         __syncthreads();
-        const float U = tile_umax_p<TX, TY, TZ>(cA, sm.red);
+        const float U = tile_umax_p<TX, TY, TZ, false>(cA, sm.red);
         const double hdt = 0.5 * dt_rep;
         const bool has_ra = a.tile_flag[tile] != 0 && nra > 0;
         const bool in_xy = (L.c0x + th.lx < L.rd.nx) && (L.c0y + th.ly < L.rd.ny);
@@ -620,8 +724,13 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_force_p(const __grid_constant
             const float la = a.rc_lat + sqrtf(A.x * A.x + A.z * A.z + B.x * B.x) + U;
             const float lb = a.rc_lat + sqrtf(A.y * A.y + A.w * A.w + B.y * B.y) + U;
             const float2 lim2 = make_float2(live_a ? la * la : -1.f, live_b ? lb * lb : -1.f);
+            unsigned long long msk = 0;
+            if (a.mask_ok) {
+                if (live_a) msk |= a.bmask[site_of(L, th.lx, th.ly, th.lz, th.p)];
+                if (live_b) msk |= a.bmask[site_of(L, th.lx, th.ly, th.lz + G::HZ, th.p)];
+            }
             force_shells_p<0, ENERGY>(a.sh, a.seg_lo, po, cA, cB, th.slot, ui, lim2, S2, (unsigned)nwin, tab0, tab1,
-                                      a.tab_phi, fa, fb, ea, eb);
+                                      a.tab_phi, a.mask_ok != 0, msk, fa, fb, ea, eb);
         }
         if (has_ra) {
             int pos = 0;
