@@ -476,6 +476,7 @@ def run_gpu(args):
     # ---- FP32-force path: the timed value ---------------------------------
     sim = fresh("fp32")
     tile_used = sim.tile()
+    tile_force = sim.tile_force()
     sim.step(args.warmup)
     torch.cuda.synchronize()
     st0 = sim.stats()
@@ -589,7 +590,7 @@ def run_gpu(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": w["desc"], "atoms": natoms, "parallelism": f"replicas{ws}",
                            "cache": f"state ~{148 * natoms / 1e9:.1f} GB >> 129 MB L2 (no flush needed)",
-                           "tile": list(tile_used)},
+                           "tile": list(tile_used), "tile_force": list(tile_force)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "clocks": clocks, "fp64_path": fp64,
                 "end_state": {"step": stats_end["step"], "time_fs": stats_end["time"],

@@ -254,10 +254,12 @@ int misa_selftest(long long n, long long *mismatches);
  * Creating a handle with a shape its precision lacks returns MISA_EINVAL. */
 int misa_tile_valid(int precision, int index);
 
-/* Tile shape in use (1-based index; chosen by the autotuner when
- * misa_params.tile is 0: each shape's density + force passes are timed on
- * the initial crystal and the fastest kept). */
+/* Tile shapes in use (1-based indices) by the density pass and by the force
+ * pass.  With misa_params.tile = 0 the autotuner times both passes of the
+ * initial state for every shape built for the precision and keeps the
+ * fastest shape of each pass; otherwise both passes use misa_params.tile. */
 int misa_tile_current(const misa_sim *s);
+int misa_tile_current_force(const misa_sim *s);
 
 /* Allocation-free force evaluation (the paper has no counterpart; it exists
  * for callers that must not allocate device memory).

@@ -107,15 +107,20 @@ struct misa_sim {
     std::string err;
     std::vector<std::pair<void *, size_t>> allocs;
     // device buffers
-    RepDesc *reps_d = nullptr;
+    RepDesc *reps_d = nullptr;   // replica table with the density pass's tile counts
     int *tile_rep = nullptr;
     int *sid = nullptr, *claim = nullptr, *tile_flag = nullptr;
+    // the force pass's own tile shape: replica table, tile -> replica map, run-away tile flags
+    int tile_f = 0, ntiles_f = 0;
+    RepDesc *reps_fd = nullptr;
+    int *tile_rep_f = nullptr, *tile_flag_f = nullptr;
     double *u[3] = {}, *v[3] = {};
     void *s[3] = {};  // precision-T shadow of u (FP32 path) or alias of u
     void *a[3] = {};
     void *fp = nullptr, *rho = nullptr;
     double *esite = nullptr;
     unsigned long long *bmask = nullptr;  // FP32: sparse-shell candidates inside rc, per site
+    unsigned long long tex_f = 0, tex_d0 = 0, tex_d1 = 0;  // FP32: texture objects over the tables
     int *ra_home = nullptr, *ra_id = nullptr;
     double *ra_u[3] = {}, *ra_v[3] = {};
     void *ra_s[3] = {}, *ra_a[3] = {};
@@ -263,13 +268,13 @@ int seg_lo_of(const misa_sim *s)
 }
 
 template <typename T>
-void fill_gather(misa_sim *s, GatherArgs<T> &g)
+void fill_gather(misa_sim *s, GatherArgs<T> &g, bool force_pass = false)
 {
     std::memset(&g, 0, sizeof(g));
-    const TileShape &ts = kTiles[s->tile];
-    g.reps = s->reps_d;
-    g.tile_rep = s->tile_rep;
-    g.ntiles = s->ntiles;
+    const TileShape &ts = kTiles[force_pass ? s->tile_f : s->tile];
+    g.reps = force_pass ? s->reps_fd : s->reps_d;
+    g.tile_rep = force_pass ? s->tile_rep_f : s->tile_rep;
+    g.ntiles = force_pass ? s->ntiles_f : s->ntiles;
     g.nrep = s->nrep;
     g.ux = (const T *)s->s[0]; g.uy = (const T *)s->s[1]; g.uz = (const T *)s->s[2];
     g.fp = (const T *)s->fp;
@@ -300,7 +305,7 @@ void fill_gather(misa_sim *s, GatherArgs<T> &g)
     g.ra_home = s->ra_home;
     g.ra_ux = (const T *)s->ra_s[0]; g.ra_uy = (const T *)s->ra_s[1]; g.ra_uz = (const T *)s->ra_s[2];
     g.ra_fp = (const T *)s->ra_fp;
-    g.tile_flag = s->tile_flag;
+    g.tile_flag = force_pass ? s->tile_flag_f : s->tile_flag;
     g.sc = s->sc;
     g.acc_conv = kAccUnit / s->p.mass;
     g.kick = 1;
@@ -335,6 +340,9 @@ void fill_gather(misa_sim *s, GatherArgs<T> &g)
         sh.nshell = q + 1;
     }
     g.bmask = s->bmask;
+    g.tex_f = s->tex_f;
+    g.tex_d0 = s->tex_d0;
+    g.tex_d1 = s->tex_d1;
     g.mask_ok = s->bmask && kLVec.shell_begin[sh.nshell] - kSparseK0 <= 64 ? 1 : 0;
 }
 
@@ -359,10 +367,10 @@ size_t smem_density_bytes(misa_sim *s, size_t optin)
 template <typename T>
 size_t smem_force_bytes(misa_sim *s)
 {
-    const TileShape &ts = kTiles[s->tile];
+    const TileShape &ts = kTiles[s->tile_f];
     const size_t nwin = (size_t)(s->p.n_knots - 1 - seg_lo_of(s));
     if constexpr (sizeof(T) == 4)
-        return packed_smem_bytes((sizeof(float4) + sizeof(float2)) * (nwin + 1), ts.tx, ts.ty, ts.tz, 1);
+        return packed_smem_bytes(sizeof(float4) * (nwin + 1), ts.tx, ts.ty, ts.tz, 1);
     else
         return gather_smem_bytes<T>(0, ts.tx, ts.ty, ts.tz, 1);
 }
@@ -373,22 +381,33 @@ template <typename T, int TX, int TY, int TZ>
 struct TileKernels {
     static constexpr bool kF32 = sizeof(T) == 4;
     static constexpr bool kBuilt = kF32 ? (TZ % 2 == 0 && TX * TY * TZ <= 1024) : (2 * TX * TY * TZ <= 1024);
-    static int attrs(misa_sim *s)
+    static int attrs_density(misa_sim *s)
     {
         if constexpr (!kBuilt) {
             return MISA_EINVAL;
         } else if constexpr (kF32) {
-            const int d = (int)s->smem_density, f = (int)s->smem_force;
+            const int d = (int)s->smem_density;
             CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
             CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
             CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
             CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
-            CK(cudaFuncSetAttribute(k_force_p<TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, f));
-            CK(cudaFuncSetAttribute(k_force_p<TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, f));
             return MISA_OK;
         } else {
             CK(cudaFuncSetAttribute(k_density<T, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_density));
             CK(cudaFuncSetAttribute(k_density<T, TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_density));
+            return MISA_OK;
+        }
+    }
+    static int attrs_force(misa_sim *s)
+    {
+        if constexpr (!kBuilt) {
+            return MISA_EINVAL;
+        } else if constexpr (kF32) {
+            const int f = (int)s->smem_force;
+            CK(cudaFuncSetAttribute(k_force_p<TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, f));
+            CK(cudaFuncSetAttribute(k_force_p<TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, f));
+            return MISA_OK;
+        } else {
             CK(cudaFuncSetAttribute(k_force<T, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_force));
             CK(cudaFuncSetAttribute(k_force<T, TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_force));
             return MISA_OK;
@@ -440,17 +459,14 @@ struct TileKernels {
     default: TileKernels<T, 8, 8, 16>::CALL; break;           \
     }
 
-// Sets the tile shape: tile counts of every replica, the global tile ->
-// replica map, kernel attributes.  Drops a captured step graph.
-template <typename T>
-int configure(misa_sim *s, int tile)
+// Tile counts of every replica for one tile shape and the global tile ->
+// replica map; the tile fields of reps are overwritten.
+int build_tile_map(misa_sim *s, const TileShape &ts, std::vector<RepDesc> &reps, std::vector<int> &map)
 {
-    s->tile = tile;
-    const TileShape &ts = kTiles[tile];
     int base = 0;
-    std::vector<int> map;
+    map.clear();
     for (int r = 0; r < s->nrep; ++r) {
-        RepDesc &rd = s->reps[r];
+        RepDesc &rd = reps[r];
         rd.ntx = (rd.nx + ts.tx - 1) / ts.tx;
         rd.nty = (rd.ny + ts.ty - 1) / ts.ty;
         rd.ntz = (rd.nz + ts.tz - 1) / ts.tz;
@@ -459,12 +475,30 @@ int configure(misa_sim *s, int tile)
         base += rd.ntiles;
         map.insert(map.end(), rd.ntiles, r);
     }
-    s->ntiles = base;
-    if ((long long)base > s->ntile_cap) return fail(s, MISA_EINVAL, "tile map capacity");
+    return base;
+}
+
+// Sets the tile shapes of the density pass (td) and the force pass (tf):
+// tile counts of every replica, the global tile -> replica maps, kernel
+// attributes.  Drops a captured step graph.
+template <typename T>
+int configure(misa_sim *s, int td, int tf)
+{
+    if (!tile_ok(s->prec, kTiles[td]) || !tile_ok(s->prec, kTiles[tf]))
+        return fail(s, MISA_EINVAL, "tile shape not built for this precision");
+    s->tile = td;
+    s->tile_f = tf;
+    std::vector<int> map, map_f;
+    std::vector<RepDesc> reps_f = s->reps;
+    s->ntiles = build_tile_map(s, kTiles[td], s->reps, map);
+    s->ntiles_f = build_tile_map(s, kTiles[tf], reps_f, map_f);
+    if ((long long)s->ntiles > s->ntile_cap || (long long)s->ntiles_f > s->ntile_cap)
+        return fail(s, MISA_EINVAL, "tile map capacity");
     CK(cudaMemcpyAsync(s->reps_d, s->reps.data(), sizeof(RepDesc) * s->nrep, cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->tile_rep, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, s->st));
-    CK(cudaStreamSynchronize(s->st));  // map is a host temporary
-    if (!tile_ok(s->prec, ts)) return fail(s, MISA_EINVAL, "tile shape not built for this precision");
+    CK(cudaMemcpyAsync(s->reps_fd, reps_f.data(), sizeof(RepDesc) * s->nrep, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->tile_rep_f, map_f.data(), sizeof(int) * map_f.size(), cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));  // the maps are host temporaries
     int dev = 0, optin = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -473,7 +507,8 @@ int configure(misa_sim *s, int tile)
     if (s->smem_density > (size_t)optin || s->smem_force > (size_t)optin)
         return fail(s, MISA_EINVAL, "tile shape and table window exceed the shared memory of a block");
     int arc = MISA_OK;
-    MISA_TILE_DISPATCH(T, s->tile, attrs(s) == MISA_OK ? (void)0 : (void)(arc = MISA_ECUDA));
+    MISA_TILE_DISPATCH(T, td, attrs_density(s) == MISA_OK ? (void)0 : (void)(arc = MISA_ECUDA));
+    MISA_TILE_DISPATCH(T, tf, attrs_force(s) == MISA_OK ? (void)0 : (void)(arc = MISA_ECUDA));
     if (arc) return fail(s, arc, s->err.empty() ? "tile kernel attributes" : s->err);
     CK(cudaFuncSetAttribute(k_ra_sort<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)(sizeof(unsigned long long) * kSortMax)));
@@ -484,19 +519,49 @@ int configure(misa_sim *s, int tile)
     return MISA_OK;
 }
 
+// Run-away tile flags of both passes' tile shapes.
+template <typename T>
+int mark_tiles(misa_sim *s)
+{
+    MdArgs<T> m = md_args<T>(s);
+    CK(cudaMemsetAsync(s->tile_flag, 0, sizeof(int) * (size_t)s->ntiles, s->st));
+    CK(cudaMemsetAsync(s->tile_flag_f, 0, sizeof(int) * (size_t)s->ntiles_f, s->st));
+    k_mark_tiles<T><<<list_grid(s), 256, 0, s->st>>>(m);
+    const TileShape &tf = kTiles[s->tile_f];
+    m.reps = s->reps_fd;
+    m.tile_flag = s->tile_flag_f;
+    m.tx = tf.tx; m.ty = tf.ty; m.tz = tf.tz;
+    k_mark_tiles<T><<<list_grid(s), 256, 0, s->st>>>(m);
+    return MISA_OK;
+}
+
+template <typename T>
+void launch_density(misa_sim *s, const GatherArgs<T> &g, bool energy)
+{
+    const int grid = s->ntiles < s->nsm ? s->ntiles : s->nsm;
+    MISA_TILE_DISPATCH(T, s->tile, density(s, g, grid, energy));
+}
+
+template <typename T>
+void launch_force(misa_sim *s, const GatherArgs<T> &g, bool energy)
+{
+    const int grid = s->ntiles_f < s->nsm ? s->ntiles_f : s->nsm;
+    MISA_TILE_DISPATCH(T, s->tile_f, force(s, g, grid, energy));
+}
+
 template <typename T>
 int launch_forces(misa_sim *s, int kick, bool energy, bool step_marks = false)
 {
-    MdArgs<T> m = md_args<T>(s);
-    GatherArgs<T> g;
-    fill_gather<T>(s, g);
-    g.kick = kick;
-    const int grid = s->ntiles < s->nsm ? s->ntiles : s->nsm;
-    CK(cudaMemsetAsync(s->tile_flag, 0, sizeof(int) * (size_t)s->ntiles, s->st));
-    k_mark_tiles<T><<<list_grid(s), 256, 0, s->st>>>(m);
+    GatherArgs<T> gd, gf;
+    fill_gather<T>(s, gd, false);
+    fill_gather<T>(s, gf, true);
+    gd.kick = gf.kick = kick;
+    int rc = mark_tiles<T>(s);
+    if (rc) return rc;
     RaGatherArgs<T> ra;
     std::memset(&ra, 0, sizeof(ra));
-    ra.g = g;
+    ra.g = gd;
+    ra.g.kick = kick;
     ra.sid = s->sid;
     ra.ra_sx = (const T *)s->ra_s[0]; ra.ra_sy = (const T *)s->ra_s[1]; ra.ra_sz = (const T *)s->ra_s[2];
     ra.ra_fp = (T *)s->ra_fp; ra.ra_rho = (T *)s->ra_rho; ra.ra_e = s->ra_e;
@@ -504,15 +569,15 @@ int launch_forces(misa_sim *s, int kick, bool energy, bool step_marks = false)
     ra.ra_vx = s->ra_v[0]; ra.ra_vy = s->ra_v[1]; ra.ra_vz = s->ra_v[2];
     ra.energy = energy ? 1 : 0;
     if (step_marks) mark(s);  // end of the list phase
-    MISA_TILE_DISPATCH(T, s->tile, density(s, g, grid, energy));
+    launch_density<T>(s, gd, energy);
     if (step_marks) mark(s);
     k_ra_gather<T, 0><<<dim3(16, s->nrep), 256, 0, s->st>>>(ra);
     if (step_marks) mark(s);
-    MISA_TILE_DISPATCH(T, s->tile, force(s, g, grid, energy));
+    launch_force<T>(s, gf, energy);
     if (step_marks) mark(s);
     k_ra_gather<T, 1><<<dim3(16, s->nrep), 256, 0, s->st>>>(ra);
     if (step_marks) mark(s);
-    s->launches += 5;
+    s->launches += 6;
     CK(cudaGetLastError());
     return MISA_OK;
 }
@@ -590,39 +655,46 @@ int refresh(misa_sim *s, bool forces)
     return MISA_OK;
 }
 
-// Tile autotuner: times the density + force passes of the current state for
-// every tile shape and keeps the fastest.
+// Tile autotuner: times the density pass and the force pass of the current
+// state for every tile shape and keeps the fastest shape of each pass.
 template <typename T>
 int autotune(misa_sim *s)
 {
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_k = 0;
+    cudaEvent_t ev[3];
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    float best_d = 1e30f, best_f = 1e30f;
+    int kd = 0, kf = 0;
     for (int k = 0; k < kNTiles; ++k) {
         if (!tile_ok(s->prec, kTiles[k])) continue;
-        int rc = configure<T>(s, k);
+        int rc = configure<T>(s, k, k);
         if (rc) return rc;
         rc = launch_forces<T>(s, 0, false);  // warm-up
         if (rc) return rc;
-        CK(cudaEventRecord(e0, s->st));
-        for (int q = 0; q < 3; ++q) {
-            rc = launch_forces<T>(s, 0, false);
-            if (rc) return rc;
+        GatherArgs<T> gd, gf;
+        fill_gather<T>(s, gd, false);
+        fill_gather<T>(s, gf, true);
+        gd.kick = gf.kick = 0;
+        CK(cudaEventRecord(ev[0], s->st));
+        for (int q = 0; q < 3; ++q) launch_density<T>(s, gd, false);
+        CK(cudaEventRecord(ev[1], s->st));
+        for (int q = 0; q < 3; ++q) launch_force<T>(s, gf, false);
+        CK(cudaEventRecord(ev[2], s->st));
+        CK(cudaGetLastError());
+        CK(cudaEventSynchronize(ev[2]));
+        float md = 0.f, mf = 0.f;
+        CK(cudaEventElapsedTime(&md, ev[0], ev[1]));
+        CK(cudaEventElapsedTime(&mf, ev[1], ev[2]));
+        if (md < best_d) {
+            best_d = md;
+            kd = k;
         }
-        CK(cudaEventRecord(e1, s->st));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-            best = ms;
-            best_k = k;
+        if (mf < best_f) {
+            best_f = mf;
+            kf = k;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    return configure<T>(s, best_k);
+    for (auto e : ev) cudaEventDestroy(e);
+    return configure<T>(s, kd, kf);
 }
 
 template <typename T>
@@ -636,6 +708,9 @@ int create_impl(misa_sim *s)
     s->sc = (DevScalars *)dalloc(s, sizeof(DevScalars) * s->nrep);
     s->tile_rep = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap);
     s->tile_flag = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap);
+    s->reps_fd = (RepDesc *)dalloc(s, sizeof(RepDesc) * s->nrep);
+    s->tile_rep_f = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap);
+    s->tile_flag_f = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap);
     s->sid = (int *)dalloc(s, sizeof(int) * ns);
     s->claim = (int *)dalloc(s, sizeof(int) * ns);
     for (int d = 0; d < 3; ++d) {
@@ -677,7 +752,8 @@ int create_impl(misa_sim *s)
     s->out_buf = (double *)dalloc(s, sizeof(double) * 3 * ns);
     s->aux_int = (int *)dalloc(s, sizeof(int) * ns);
     s->aux_dbl = (double *)dalloc(s, sizeof(double) * 3 * ns);
-    if (!s->reps_d || !s->sc || !s->tile_rep || !s->tile_flag || !s->sid || !s->claim || !s->fp || !s->rho ||
+    if (!s->reps_d || !s->sc || !s->tile_rep || !s->tile_flag || !s->reps_fd || !s->tile_rep_f || !s->tile_flag_f ||
+        !s->sid || !s->claim || !s->fp || !s->rho ||
         !s->esite || (sizeof(T) == 4 && !s->bmask) || !s->ra_home || !s->ra_id || !s->t_home || !s->t_id || !s->ra_fp || !s->ra_rho || !s->ra_e ||
         !s->knots || !s->tab_f || !s->tab_phi || !s->tab_F || !s->tab_d0 || !s->tab_d1 || !s->partial ||
         !s->red_out || !s->out_buf || !s->aux_int || !s->aux_dbl)
@@ -690,7 +766,27 @@ int create_impl(misa_sim *s)
                                                             (Vec4<T> *)s->tab_f, (Vec4<T> *)s->tab_phi,
                                                             (Vec4<T> *)s->tab_F, (Vec4<T> *)s->tab_d0,
                                                             (Vec2<T> *)s->tab_d1);
-    int rc = configure<T>(s, s->p.tile > 0 ? s->p.tile - 1 : 0);
+    if (sizeof(T) == 4) {
+        void *ptrs[3] = {s->tab_f, s->tab_d0, s->tab_d1};
+        const cudaChannelFormatDesc cd[3] = {cudaCreateChannelDesc<float4>(), cudaCreateChannelDesc<float4>(),
+                                             cudaCreateChannelDesc<float2>()};
+        const size_t bytes[3] = {sizeof(Vec4<T>) * (size_t)n, sizeof(Vec4<T>) * (size_t)n, sizeof(Vec2<T>) * (size_t)n};
+        unsigned long long *out[3] = {&s->tex_f, &s->tex_d0, &s->tex_d1};
+        for (int q = 0; q < 3; ++q) {
+            cudaResourceDesc rd{};
+            rd.resType = cudaResourceTypeLinear;
+            rd.res.linear.devPtr = ptrs[q];
+            rd.res.linear.desc = cd[q];
+            rd.res.linear.sizeInBytes = bytes[q];
+            cudaTextureDesc td{};
+            td.readMode = cudaReadModeElementType;
+            cudaTextureObject_t to = 0;
+            CK(cudaCreateTextureObject(&to, &rd, &td, nullptr));
+            *out[q] = to;
+        }
+    }
+    const int t0 = s->p.tile > 0 ? s->p.tile - 1 : 0;
+    int rc = configure<T>(s, t0, t0);
     if (rc) return rc;
     MdArgs<T> m = md_args<T>(s);
     k_init_crystal<T><<<site_grid(s), 256, 0, s->st>>>(m);
@@ -1054,6 +1150,8 @@ void misa_destroy(misa_sim *s)
     cudaStreamSynchronize(s->st);
     if (s->gst) cudaStreamSynchronize(s->gst);
     if (s->graph) cudaGraphExecDestroy(s->graph);
+    for (unsigned long long t : {s->tex_f, s->tex_d0, s->tex_d1})
+        if (t) cudaDestroyTextureObject((cudaTextureObject_t)t);
     for (auto e : s->ev_pool) cudaEventDestroy(e);
     if (s->ev_in) cudaEventDestroy(s->ev_in);
     if (s->ev_out) cudaEventDestroy(s->ev_out);
@@ -1382,6 +1480,8 @@ int misa_tile_shape(int index, int *tx, int *ty, int *tz)
 
 int misa_tile_current(const misa_sim *s) { return s ? s->tile + 1 : 0; }
 
+int misa_tile_current_force(const misa_sim *s) { return s ? s->tile_f + 1 : 0; }
+
 int misa_selftest(long long n, long long *mismatches)
 {
     if (n <= 0 || !mismatches) return MISA_EINVAL;
@@ -1422,11 +1522,12 @@ namespace {
 
 constexpr size_t kStaticAlign = 256;
 // upper bound of the carve below for either precision: per site <= 160 B,
-// per run-away slot <= 512 B, per knot <= 160 B, one flag and one map entry
-// per cell, the replica table and scalars, and the alignment padding
+// per run-away slot <= 512 B, per knot <= 160 B, two flags and two map
+// entries per cell (density and force tile maps), two replica tables, the
+// scalars, and the alignment padding
 constexpr size_t kStaticNeed = 160ull * MISA_STATIC_MAX_ATOMS + 512ull * MISA_STATIC_RUNAWAY_CAP +
-                               160ull * MISA_STATIC_MAX_KNOTS + 8ull * (MISA_STATIC_MAX_ATOMS / 2) +
-                               sizeof(DevScalars) + sizeof(RepDesc) + 96 * kStaticAlign;
+                               160ull * MISA_STATIC_MAX_KNOTS + 16ull * (MISA_STATIC_MAX_ATOMS / 2) +
+                               sizeof(DevScalars) + 2 * sizeof(RepDesc) + 96 * kStaticAlign;
 static_assert(kStaticNeed <= MISA_STATIC_SCRATCH_BYTES, "static scratch too small");
 
 }  // namespace
@@ -1495,6 +1596,9 @@ size_t carve_static(misa_sim *s, unsigned char *base, int nk)
     s->aux_int = c.take<int>(ns);
     s->tile_flag = c.take<int>(ns / 2);
     s->tile_rep = c.take<int>(ns / 2);
+    s->reps_fd = c.take<RepDesc>(1);
+    s->tile_flag_f = c.take<int>(ns / 2);
+    s->tile_rep_f = c.take<int>(ns / 2);
     return c.off;
 }
 
@@ -1509,7 +1613,7 @@ int static_forces_impl(misa_sim *s, const double *knots, const double *x, double
                                                             (Vec4<T> *)s->tab_f, (Vec4<T> *)s->tab_phi,
                                                             (Vec4<T> *)s->tab_F, (Vec4<T> *)s->tab_d0,
                                                             (Vec2<T> *)s->tab_d1);
-    int rc = configure<T>(s, 0);
+    int rc = configure<T>(s, 0, 0);
     if (rc) return rc;
     // hash the positions into the lattice list (clears sites, claims, list)
     // and evaluate forces; then the energy pass for E_i

@@ -105,6 +105,12 @@ __global__ void k_spline_tables(const double *fk, const double *pk, const double
                                 Vec4<T> *tab_d0, Vec2<T> *tab_d1)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == n - 1) {
+        // one all-zero entry past the last segment: the FP32 gathers clamp
+        // every index at or beyond rc to it
+        tab_f[k] = tab_phi[k] = tab_F[k] = tab_d0[k] = Vec4<T>{0, 0, 0, 0};
+        tab_d1[k] = Vec2<T>{0, 0};
+    }
     if (k >= n - 1) return;
     double cf[4], cp[4], cF[4];
     const double *ys[3] = {fk, pk, Fk};
@@ -200,6 +206,7 @@ struct GatherArgs {
     // force pass evaluates only those.  mask_ok = 0: evaluate all of them.
     unsigned long long *bmask;
     int mask_ok;
+    unsigned long long tex_f, tex_d0, tex_d1;  // texture objects over tab_f, tab_d0, tab_d1
     // neighbour offset index for this tile shape: per parity, per lattice
     // vector: (shared-memory slot displacement as int bits, 2 n_x, 2 n_y, 2 n_z)
     float4 off[2][kNVec];

@@ -338,12 +338,22 @@ __device__ __forceinline__ float screen_thr(float nrm, float rc_lat, float ui_no
     return gap > 0.f ? gap * gap * 0.99999f : -1.f;
 }
 
+// Table reads of the two sites take two paths of the L1 unit that run side
+// by side: site a from shared memory, site b through the texture path (a
+// texture object over the global table; shared memory when there is none).
+__device__ __forceinline__ float4 tab_b(const float4 *__restrict__ tab, unsigned long long tex, int seg_lo, int i)
+{
+    if (tex) return tex1Dfetch<float4>((cudaTextureObject_t)tex, seg_lo + i);
+    return tab[i];
+}
+
 template <int SH>
 __device__ __forceinline__ void density_shells_p(const ShellInfo &shc, int seg_lo, const float4 *__restrict__ po,
                                                  const float4 *__restrict__ sA, const float4 *__restrict__ sB, int slot,
                                                  const PairSites &ui, float2 unorm, float rc_lat, float2 lim2, float2 S2,
-                                                 unsigned nwin, const float4 *__restrict__ tab, Acc<float> &ra,
-                                                 Acc<float> &rb, unsigned long long &ma, unsigned long long &mb)
+                                                 unsigned nwin, const float4 *__restrict__ tab, unsigned long long texf,
+                                                 Acc<float> &ra, Acc<float> &rb, unsigned long long &ma,
+                                                 unsigned long long &mb)
 {
     if constexpr (SH < kLVec.nshell) {
         constexpr int KB = kLVec.shell_begin[SH], KE = kLVec.shell_begin[SH + 1];
@@ -362,7 +372,7 @@ __device__ __forceinline__ void density_shells_p(const ShellInfo &shc, int seg_l
                 float2 t, rs;
                 int ia, ib;
                 arg_p(sh, g.q, S2, nwin, t, rs, ia, ib);
-                part = p_add(part, make_float2(cubic(tab[ia], t.x), cubic(tab[ib], t.y)));
+                part = p_add(part, make_float2(cubic(tab[ia], t.x), cubic(tab_b(tab, texf, seg_lo, ib), t.y)));
             }
         } else {
             const float ta = screen_thr(shc.nrm[SH], rc_lat, unorm.x, na);
@@ -376,7 +386,7 @@ __device__ __forceinline__ void density_shells_p(const ShellInfo &shc, int seg_l
                     float2 t, rs;
                     int ia, ib;
                     arg_p(sh, g.q, S2, nwin, t, rs, ia, ib);
-                    part = p_add(part, make_float2(cubic(tab[ia], t.x), cubic(tab[ib], t.y)));
+                    part = p_add(part, make_float2(cubic(tab[ia], t.x), cubic(tab_b(tab, texf, seg_lo, ib), t.y)));
                     const int bi = k - kSparseK0;
                     if (bi < 64) {  // configurations with more sparse candidates run unmasked
                         const unsigned long long bit = 1ull << bi;
@@ -388,22 +398,38 @@ __device__ __forceinline__ void density_shells_p(const ShellInfo &shc, int seg_l
         }
         kahan_nz(ra, part.x);
         kahan_nz(rb, part.y);
-        density_shells_p<SH + 1>(shc, seg_lo, po, sA, sB, slot, ui, unorm, rc_lat, lim2, S2, nwin, tab, ra, rb, ma, mb);
+        density_shells_p<SH + 1>(shc, seg_lo, po, sA, sB, slot, ui, unorm, rc_lat, lim2, S2, nwin, tab, texf, ra, rb, ma,
+                                 mb);
     }
 }
+
+struct ForceTex {
+    unsigned long long d0, d1;
+};
 
 // one candidate of the force pass for both sites, accumulated into p*
 template <bool ENERGY>
 __device__ __forceinline__ void force_pair_p(const PShell &sh, const PGeom &g, const float4 B, const PairSites &ui,
                                              float2 S2, unsigned nwin, int seg_lo, const float4 *__restrict__ tab0,
-                                             const float2 *__restrict__ tab1, const Vec4<float> *__restrict__ gphi,
-                                             float2 &px, float2 &py, float2 &pz, double &ea, double &eb)
+                                             const float2 *__restrict__ tab1, const ForceTex &tx,
+                                             const Vec4<float> *__restrict__ gphi, float2 &px, float2 &py, float2 &pz,
+                                             double &ea, double &eb)
 {
     float2 t, rs;
     int ia, ib;
     arg_p(sh, g.q, S2, nwin, t, rs, ia, ib);
+    // f' and the t^2 coefficient of phi' from shared memory, the rest of phi'
+    // through the texture path (the global table, whose last entry is the
+    // zero segment, without texture objects)
     const float4 ca = tab0[ia], cb = tab0[ib];
-    const float2 da = tab1[ia], db = tab1[ib];
+    float2 da, db;
+    if (tx.d1) {
+        da = tex1Dfetch<float2>((cudaTextureObject_t)tx.d1, seg_lo + ia);
+        db = tex1Dfetch<float2>((cudaTextureObject_t)tx.d1, seg_lo + ib);
+    } else {
+        da = tab1[seg_lo + ia];
+        db = tab1[seg_lo + ib];
+    }
     const float2 dfr = make_float2(fmaf(fmaf(ca.x, t.x, ca.y), t.x, ca.z), fmaf(fmaf(cb.x, t.y, cb.y), t.y, cb.z));
     const float2 dph = make_float2(fmaf(fmaf(ca.w, t.x, da.x), t.x, da.y), fmaf(fmaf(cb.w, t.y, db.x), t.y, db.y));
     const float2 sc = p_mul(p_fma(p_add(ui.fp, make_float2(B.z, B.w)), dfr, dph), rs);
@@ -434,7 +460,7 @@ __device__ __forceinline__ void force_shells_p(const ShellInfo &shc, int seg_lo,
                                                const float4 *__restrict__ sA, const float4 *__restrict__ sB, int slot,
                                                const PairSites &ui, float2 lim2, float2 S2, unsigned nwin,
                                                const float4 *__restrict__ tab0, const float2 *__restrict__ tab1,
-                                               const Vec4<float> *__restrict__ gphi, bool use_mask,
+                                               const ForceTex &tx, const Vec4<float> *__restrict__ gphi, bool use_mask,
                                                unsigned long long msk, Acc<float> (&fa)[3], Acc<float> (&fb)[3],
                                                double &ea, double &eb)
 {
@@ -454,7 +480,7 @@ __device__ __forceinline__ void force_shells_p(const ShellInfo &shc, int seg_lo,
                 const float4 B = sB[slot + D];
                 const PGeom g = pair_geom(o0, o1, sA[slot + D], B, ui);
                 if (dense || g.q.x < sh.thr || g.q.y < sh.thr)
-                    force_pair_p<ENERGY>(sh, g, B, ui, S2, nwin, seg_lo, tab0, tab1, gphi, px, py, pz, ea, eb);
+                    force_pair_p<ENERGY>(sh, g, B, ui, S2, nwin, seg_lo, tab0, tab1, tx, gphi, px, py, pz, ea, eb);
             }
         } else {
             unsigned long long sub = (msk >> (KB - kSparseK0)) & ((1ull << (KE - KB)) - 1ull);
@@ -465,12 +491,12 @@ __device__ __forceinline__ void force_shells_p(const ShellInfo &shc, int seg_lo,
                 const int D = __float_as_int(o1.z);
                 const float4 B = sB[slot + D];
                 const PGeom g = pair_geom(o0, o1, sA[slot + D], B, ui);
-                force_pair_p<ENERGY>(sh, g, B, ui, S2, nwin, seg_lo, tab0, tab1, gphi, px, py, pz, ea, eb);
+                force_pair_p<ENERGY>(sh, g, B, ui, S2, nwin, seg_lo, tab0, tab1, tx, gphi, px, py, pz, ea, eb);
             }
         }
         kahan3_nz(fa, px.x, py.x, pz.x);
         kahan3_nz(fb, px.y, py.y, pz.y);
-        force_shells_p<SH + 1, ENERGY>(shc, seg_lo, po, sA, sB, slot, ui, lim2, S2, nwin, tab0, tab1, gphi, use_mask,
+        force_shells_p<SH + 1, ENERGY>(shc, seg_lo, po, sA, sB, slot, ui, lim2, S2, nwin, tab0, tab1, tx, gphi, use_mask,
                                        msk, fa, fb, ea, eb);
     }
 }
@@ -610,8 +636,8 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_density_p(const __grid_consta
             const float2 un = make_float2(sqrtf(A.x * A.x + A.z * A.z + B.x * B.x), sqrtf(A.y * A.y + A.w * A.w + B.y * B.y));
             const float la = a.rc_lat + un.x + U, lb = a.rc_lat + un.y + U;
             const float2 lim2 = make_float2(live_a ? la * la : -1.f, live_b ? lb * lb : -1.f);
-            density_shells_p<0>(a.sh, a.seg_lo, po, cA, cB, th.slot, ui, un, a.rc_lat, lim2, S2, (unsigned)nwin, tab, ra,
-                                rb, ma, mb);
+            density_shells_p<0>(a.sh, a.seg_lo, po, cA, cB, th.slot, ui, un, a.rc_lat, lim2, S2, (unsigned)nwin, tab,
+                                a.tex_f, ra, rb, ma, mb);
         }
         if (has_ra) {
             int pos = 0;
@@ -669,15 +695,11 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_force_p(const __grid_constant
     extern __shared__ __align__(32) unsigned char smem[];
     const int nwin = a.nseg - a.seg_lo;
     float4 *tab0 = reinterpret_cast<float4 *>(smem);
-    float2 *tab1 = reinterpret_cast<float2 *>(smem + sizeof(float4) * (size_t)(nwin + 1));
     for (int k = threadIdx.x; k <= nwin; k += G::NT) {
         const Vec4<float> c0 = k < nwin ? a.tab_d0[a.seg_lo + k] : Vec4<float>{0.f, 0.f, 0.f, 0.f};
-        const Vec2<float> c1 = k < nwin ? a.tab_d1[a.seg_lo + k] : Vec2<float>{0.f, 0.f};
         tab0[k] = make_float4(c0.x, c0.y, c0.z, c0.w);
-        tab1[k] = make_float2(c1.x, c1.y);
     }
-    const PackedSmem sm =
-        carve_p<TX, TY, TZ>(smem, (sizeof(float4) + sizeof(float2)) * (size_t)(nwin + 1), 1);
+    const PackedSmem sm = carve_p<TX, TY, TZ>(smem, sizeof(float4) * (size_t)(nwin + 1), 1);
     fill_offsets_p(a, sm.off, G::NT);
     fill_rep_cache<float>(a, sm.rep);
     __syncthreads();
@@ -729,7 +751,9 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_force_p(const __grid_constant
                 if (live_a) msk |= a.bmask[site_of(L, th.lx, th.ly, th.lz, th.p)];
                 if (live_b) msk |= a.bmask[site_of(L, th.lx, th.ly, th.lz + G::HZ, th.p)];
             }
-            force_shells_p<0, ENERGY>(a.sh, a.seg_lo, po, cA, cB, th.slot, ui, lim2, S2, (unsigned)nwin, tab0, tab1,
+            const ForceTex tx{a.tex_d0, a.tex_d1};
+            const float2 *t1 = reinterpret_cast<const float2 *>(a.tab_d1);
+            force_shells_p<0, ENERGY>(a.sh, a.seg_lo, po, cA, cB, th.slot, ui, lim2, S2, (unsigned)nwin, tab0, t1, tx,
                                       a.tab_phi, a.mask_ok != 0, msk, fa, fb, ea, eb);
         }
         if (has_ra) {

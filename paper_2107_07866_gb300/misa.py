@@ -106,6 +106,7 @@ def lib():
         L.misa_replica_energies.argtypes = [C.c_void_p, _D, _D]
         L.misa_set_graphs.argtypes = [C.c_void_p, C.c_int]
         L.misa_tile_current.argtypes = [C.c_void_p]
+        L.misa_tile_current_force.argtypes = [C.c_void_p]
         L.misa_eam_forces_static.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
                                              C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
                                              C.c_void_p, C.c_void_p]
@@ -355,8 +356,12 @@ class Sim:
         self._check(lib().misa_set_graphs(self.h, 1 if enable else 0))
 
     def tile(self):
-        """Tile shape in use (cells)."""
+        """Tile shape of the density pass (cells)."""
         return tile_shapes()[lib().misa_tile_current(self.h) - 1]
+
+    def tile_force(self):
+        """Tile shape of the force pass (cells)."""
+        return tile_shapes()[lib().misa_tile_current_force(self.h) - 1]
 
     def clear_status(self):
         self._check(lib().misa_clear_status(self.h))

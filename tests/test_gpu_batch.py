@@ -79,7 +79,7 @@ def test_graph_replay_equals_direct_launches(misa, pot):
 
 def test_autotuner_picks_a_built_tile(misa, pot):
     with misa.Sim(pot, 12, precision="fp32", tile=0) as s:
-        assert s.tile() in misa.tile_shapes()
+        assert s.tile() in misa.tile_shapes() and s.tile_force() in misa.tile_shapes()
 
 
 def test_batch_pka_per_replica(misa, pot):
