@@ -464,12 +464,14 @@ def run_gpu(args):
             s = misa.Sim(pot, replicas=dims, precision=prec, dt_max=1.0, dx_max=w["dx_max"],
                          reassign_period=w["reassign"], tile=args.tile)
             s.set_state(x, v)
+            s.retune()
             for r, rep in enumerate(reps):
                 s.insert_pka_replica(r, rep.pka_energy, rep.pka_dir)
             return s
         s = misa.Sim(pot, n, precision=prec, dt_max=1.0, dx_max=w["dx_max"], reassign_period=w["reassign"],
                      tile=args.tile)
         s.set_state(x, v)
+        s.retune()  # tile shapes for the equilibrated crystal, not the perfect one
         s.insert_pka(-1, w["pka_eV"], d)
         return s
 

@@ -261,6 +261,15 @@ int misa_tile_valid(int precision, int index);
 int misa_tile_current(const misa_sim *s);
 int misa_tile_current_force(const misa_sim *s);
 
+/* Re-runs the tile autotuner on the current state (call it once after
+ * loading a representative configuration, e.g. an equilibrated crystal:
+ * the shapes that win on the perfect crystal of misa_create are not always
+ * the ones that win at temperature).  Results do not depend on the shapes;
+ * only speed does.  No-op when misa_params.tile fixed the shape.  Leaves
+ * the forces of the current positions in place; drops a captured step
+ * graph; synchronises. */
+int misa_retune(misa_sim *s);
+
 /* Allocation-free force evaluation (the paper has no counterpart; it exists
  * for callers that must not allocate device memory).
  *

@@ -73,7 +73,7 @@ constexpr double kRfloor = 1e-4;                      // A
 struct TileShape {
     int tx, ty, tz;
 };
-constexpr TileShape kTiles[] = {{8, 8, 8}, {8, 8, 4}, {8, 4, 4}, {16, 8, 4}, {8, 8, 16}};
+constexpr TileShape kTiles[] = {{8, 8, 8}, {8, 8, 4}, {8, 4, 4}, {16, 8, 4}, {8, 8, 16}, {8, 8, 12}, {16, 8, 8}};
 constexpr int kNTiles = sizeof(kTiles) / sizeof(kTiles[0]);
 
 // Shapes each precision's gathers are built for: FP64 runs one thread per
@@ -449,14 +449,16 @@ struct TileKernels {
     }
 };
 
-// kTiles order: {8,8,8}, {8,8,4}, {8,4,4}, {16,8,4}, {8,8,16}
+// kTiles order: {8,8,8}, {8,8,4}, {8,4,4}, {16,8,4}, {8,8,16}, {8,8,12}, {16,8,8}
 #define MISA_TILE_DISPATCH(T, idx, CALL)                      \
     switch (idx) {                                            \
     case 0: TileKernels<T, 8, 8, 8>::CALL; break;             \
     case 1: TileKernels<T, 8, 8, 4>::CALL; break;             \
     case 2: TileKernels<T, 8, 4, 4>::CALL; break;             \
     case 3: TileKernels<T, 16, 8, 4>::CALL; break;            \
-    default: TileKernels<T, 8, 8, 16>::CALL; break;           \
+    case 4: TileKernels<T, 8, 8, 16>::CALL; break;            \
+    case 5: TileKernels<T, 8, 8, 12>::CALL; break;            \
+    default: TileKernels<T, 16, 8, 8>::CALL; break;           \
     }
 
 // Tile counts of every replica for one tile shape and the global tile ->
@@ -1242,6 +1244,15 @@ int misa_step(misa_sim *s, int n)
         if (rc) return rc;
     }
     return MISA_OK;
+}
+
+int misa_retune(misa_sim *s)
+{
+    if (!s) return MISA_EINVAL;
+    if (s->p.tile != 0) return MISA_OK;
+    int rc = s->prec == MISA_FP64 ? autotune<double>(s) : autotune<float>(s);
+    if (rc) return rc;
+    return check_status(s);
 }
 
 int misa_set_graphs(misa_sim *s, int enable)

@@ -744,13 +744,15 @@ __device__ __forceinline__ RaPair<T> ra_pair(const GatherArgs<T> &a, const RepDe
 {
     RaPair<T> P;
     int nx_ = h.x - sx, ny_ = h.y - sy, nz_ = h.z - sz;
+    // minimum image; a tile may be wider than the box, so the two sides can
+    // be several box lengths apart
     const int Lx = 2 * rd.nx, Ly = 2 * rd.ny, Lz = 2 * rd.nz;
-    nx_ -= (nx_ > rd.nx) ? Lx : 0;
-    nx_ += (nx_ < -rd.nx) ? Lx : 0;
-    ny_ -= (ny_ > rd.ny) ? Ly : 0;
-    ny_ += (ny_ < -rd.ny) ? Ly : 0;
-    nz_ -= (nz_ > rd.nz) ? Lz : 0;
-    nz_ += (nz_ < -rd.nz) ? Lz : 0;
+    while (nx_ > rd.nx) nx_ -= Lx;
+    while (nx_ < -rd.nx) nx_ += Lx;
+    while (ny_ > rd.ny) ny_ -= Ly;
+    while (ny_ < -rd.ny) ny_ += Ly;
+    while (nz_ > rd.nz) nz_ -= Lz;
+    while (nz_ < -rd.nz) nz_ += Lz;
     const T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
     const T qq = (dx + (T)(2 * nx_)) * dx + (dy + (T)(2 * ny_)) * dy + (dz + (T)(2 * nz_)) * dz;
     const T r2 = (T)(nx_ * nx_ + ny_ * ny_ + nz_ * nz_) + qq;

@@ -107,6 +107,7 @@ def lib():
         L.misa_set_graphs.argtypes = [C.c_void_p, C.c_int]
         L.misa_tile_current.argtypes = [C.c_void_p]
         L.misa_tile_current_force.argtypes = [C.c_void_p]
+        L.misa_retune.argtypes = [C.c_void_p]
         L.misa_eam_forces_static.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
                                              C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
                                              C.c_void_p, C.c_void_p]
@@ -358,6 +359,10 @@ class Sim:
     def tile(self):
         """Tile shape of the density pass (cells)."""
         return tile_shapes()[lib().misa_tile_current(self.h) - 1]
+
+    def retune(self):
+        """Re-run the tile autotuner on the current state."""
+        self._check(lib().misa_retune(self.h))
 
     def tile_force(self):
         """Tile shape of the force pass (cells)."""

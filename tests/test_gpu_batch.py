@@ -95,3 +95,22 @@ def test_batch_pka_per_replica(misa, pot):
         b.step(4)
         t0, t1 = b.replica_stats(0)["time"], b.replica_stats(1)["time"]
         assert t0 == pytest.approx(4.0) and t1 < 0.5
+
+
+def test_retune_changes_speed_not_results(misa, pot):
+    # the autotuner re-run on a thermal state may pick other tile shapes for
+    # the two passes; per-site sums do not depend on the shapes
+    x = synth.thermal_snapshot(16, 12, 14, 0.12, 3)
+    v = synth.maxwell_velocities(len(x), 600.0, synth.MASS_FE, 4)
+    out = []
+    for tile in (0, 1):
+        with misa.Sim(pot, 16, 12, 14, precision="fp32", tile=tile) as s:
+            s.set_state(x, v)
+            f0 = s.forces()
+            s.retune()
+            assert s.tile() in misa.tile_shapes() and s.tile_force() in misa.tile_shapes()
+            np.testing.assert_array_equal(s.forces(), f0)
+            s.step(5)
+            out.append((s.positions(), s.forces()))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])

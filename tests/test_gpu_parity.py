@@ -93,13 +93,17 @@ def test_perfect_crystal_zero_force(misa, pot, oracle, opot, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_tile_shapes_bitwise_equal(misa, pot, prec):
-    x = synth.cascade_snapshot(12, 9, 10, 0.12, 24, 8, 2)
+@pytest.mark.parametrize("case", ["cascade_12x9x10", "cascade_6x6x6"])
+def test_tile_shapes_bitwise_equal(misa, pot, oracle_results, prec, case):
+    # every shape, including tiles more than twice as wide as the 6-cell box
+    # (run-away pairs then span several periodic images of the tile)
+    x, dims, _, _, f_o = oracle_results[case]
     ref = None
     for t in misa.tile_indices(prec):
-        with misa.Sim(pot, 12, 9, 10, precision=prec, tile=t) as s:
+        with misa.Sim(pot, *dims, precision=prec, tile=t) as s:
             s.set_state(x)
             f = s.forces()
+        assert nerr(f, f_o) < TOL[prec], (misa.tile_shapes()[t - 1], nerr(f, f_o))
         if ref is None:
             ref = f
         else:
