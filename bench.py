@@ -49,18 +49,27 @@ FLOPS_DENS_SITE = CAND * FLOP_CAND + PAIRS * FLOP_DENS_PAIR
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # Algorithmic HBM bytes per atom-step of the whole FP32-force step:
 #   kick/drift: read u64, v64, a32 (60), write u64, v64, u32 shadow (60)
-#   density:    read u32 (12), write F' (4)
-#   force:      read u32 (12), F' (4), v64 (24); write v64 (24), a32 (12)
-BYTES_STEP_FP32 = 120 + 16 + 76
-BYTES_FORCE_SITE = 76
-# DRAM traffic of k_force<float> per launch from one ncu capture, scaled to
-# the 54M-atom launch, keyed by the kernel source it was measured on.
-NCU_FORCE_TRAFFIC = {"source_sha": None, "bytes_per_launch": None}
+#   density:    read u32 (12), write F' (4) and the sparse-shell mask (8)
+#   force:      read u32 (12), F' (4), mask (8), v64 (24); write v64 (24), a32 (12)
+BYTES_STEP_FP32 = 120 + 24 + 84
+BYTES_FORCE_SITE = 84
+# DRAM traffic of the force pass (k_force_p) per launch at the 54M-atom
+# workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by the kernel sources it was measured on.
+NCU_FORCE_TRAFFIC = {"source_sha": "0fd16aec3b274482", "bytes_per_launch": 4.8948e9,
+                     "note": "k_force_p<8,8,12> at 300^3 cells: 3.000e9 B read + 1.895e9 B written per launch "
+                             "(mean of 3 launches), 90.6 B/site vs 84 algorithmic"}
+# Shared-memory (LSU) and texture wavefronts per site of the two gathers from
+# one ncu capture of the 2M-atom case (equilibrated crystal), same keying;
+# the L1 data pipe serves one wavefront per SM per clock.
+NCU_WAVEFRONTS = {"source_sha": "0fd16aec3b274482", "density": (32.3, 16.4), "force": (42.6, 23.6)}
 
 
 def kernel_source_sha():
-    p = os.path.join(ROOT, "paper_2107_07866_gb300", "csrc", "misa_kernels.cuh")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("misa_common.cuh", "misa_kernels.cuh", "misa_packed.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2107_07866_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():
@@ -516,7 +525,16 @@ def run_gpu(args):
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     step_s = el_ms / 1e3 / args.steps
-    roofline = {"bound": "alu", "kernel": "k_force<float>", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+    sha = kernel_source_sha()
+    l1 = None
+    if NCU_WAVEFRONTS["source_sha"] == sha:
+        # one L1 data-pipe wavefront per SM per clock at the sampled SM clock
+        clk_hz = (clocks.get("sm_mhz") or 2070.0) * 1e6
+        pipe = 152 * clk_hz
+        l1 = {k: {"lsu_wavefronts_per_site": NCU_WAVEFRONTS[k][0], "tex_wavefronts_per_site": NCU_WAVEFRONTS[k][1],
+                  "lsu_frac": NCU_WAVEFRONTS[k][0] * natoms / (t * pipe)}
+              for k, t in (("density", t_dens), ("force", t_force))}
+    roofline = {"bound": "alu", "kernel": "k_force_p (force pass)", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "peak_note": "FP32 FMA issue peak: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, not measured)",
                 "algorithmic_flops_per_site": FLOPS_FORCE_SITE,
@@ -526,7 +544,8 @@ def run_gpu(args):
                              "achieved_gbs": BYTES_STEP_FP32 * natoms / step_s / 1e9,
                              "peak_gbs": hbm_peak, "frac": BYTES_STEP_FP32 * natoms / step_s / 1e9 / hbm_peak,
                              "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json)"},
-                "phase_ms_per_step": {k: v_ / max(nsteps, 1) for k, v_ in phases.items()}}
+                "phase_ms_per_step": {k: v_ / max(nsteps, 1) for k, v_ in phases.items()},
+                "l1_data_pipe": l1, "kernel_source_sha": sha}
     stats_end = sim.stats()
     sim.close()
     del sim
