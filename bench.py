@@ -191,11 +191,13 @@ def init_dist():
 
 
 def barrier_max(ws, value):
+    """Max of a per-rank value over all ranks (NCCL on the GPUs, gloo on the host)."""
     if ws == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
