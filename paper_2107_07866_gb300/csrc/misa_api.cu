@@ -322,6 +322,8 @@ void fill_gather(misa_sim *s, GatherArgs<T> &g, bool force_pass = false)
             float fD;
             std::memcpy(&fD, &D, sizeof(int));
             g.off[par][k] = make_float4(fD, 2.0f * o.x, 2.0f * o.y, 2.0f * o.z);
+            g.offp[par][k][0] = make_float4(2.0f * o.x, 2.0f * o.x, 2.0f * o.y, 2.0f * o.y);
+            g.offp[par][k][1] = make_float4(2.0f * o.z, 2.0f * o.z, fD, 0.f);
         }
     const double roff = (s->p.rc + 2.0 * s->p.skin) / half;
     ShellInfo &sh = g.sh;

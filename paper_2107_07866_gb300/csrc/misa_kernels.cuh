@@ -210,6 +210,9 @@ struct GatherArgs {
     // neighbour offset index for this tile shape: per parity, per lattice
     // vector: (shared-memory slot displacement as int bits, 2 n_x, 2 n_y, 2 n_z)
     float4 off[2][kNVec];
+    // the same for the FP32 two-site gathers, components paired:
+    // (2nx, 2nx, 2ny, 2ny), (2nz, 2nz, slot displacement bits, 0)
+    float4 offp[2][kNVec][2];
     ShellInfo sh;
 };
 

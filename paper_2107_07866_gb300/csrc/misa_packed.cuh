@@ -80,7 +80,6 @@ __host__ __device__ inline size_t ptile_smem_bytes(int tx, int ty, int tz)
 
 struct PackedSmem {
     RepCache *rep;
-    float4 *off;  // per parity, per lattice vector: (2nx, 2nx, 2ny, 2ny), (2nz, 2nz, slot shift bits, 0)
     float4 *tA;   // nbuf staged tiles, plane A then plane B each
     int4 *rh;
     Vec4<float> *ru;
@@ -92,7 +91,6 @@ __host__ __device__ inline size_t packed_smem_bytes(size_t table_bytes, int tx, 
 {
     size_t off = (table_bytes + 255) & ~(size_t)255;
     off += sizeof(RepCache) * kRepSmem;
-    off += sizeof(float4) * 2 * 2 * kNVec;
     off += ptile_smem_bytes(tx, ty, tz) * nbuf;
     off += sizeof(int4) * kRaChunk + sizeof(Vec4<float>) * kRaChunk + sizeof(float) * kRedFloats + sizeof(RaStage);
     return off;
@@ -105,8 +103,6 @@ __device__ __forceinline__ PackedSmem carve_p(unsigned char *smem, size_t off, i
     off = (off + 255) & ~(size_t)255;
     g.rep = reinterpret_cast<RepCache *>(smem + off);
     off += sizeof(RepCache) * kRepSmem;
-    g.off = reinterpret_cast<float4 *>(smem + off);
-    off += sizeof(float4) * 2 * 2 * kNVec;
     g.tA = reinterpret_cast<float4 *>(smem + off);
     off += ptile_smem_bytes(TX, TY, TZ) * nbuf;
     g.rh = reinterpret_cast<int4 *>(smem + off);
@@ -117,17 +113,6 @@ __device__ __forceinline__ PackedSmem carve_p(unsigned char *smem, size_t off, i
     off += sizeof(float) * kRedFloats;
     g.st = reinterpret_cast<RaStage *>(smem + off);
     return g;
-}
-
-// the offset index in the packed layout: pairs of 2n components and the
-// slot shift (host-computed for the folded geometry)
-__device__ __forceinline__ void fill_offsets_p(const GatherArgs<float> &a, float4 *so, int nt)
-{
-    for (int k = threadIdx.x; k < 2 * kNVec; k += nt) {
-        const float4 o = (&a.off[0][0])[k];
-        so[2 * k] = make_float4(o.y, o.y, o.z, o.z);
-        so[2 * k + 1] = make_float4(o.w, o.w, o.x, 0.f);
-    }
 }
 
 // block-wide max of a per-thread value (floats >= 0), all threads get it
@@ -585,12 +570,13 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_density_p(const __grid_consta
         tab[k] = make_float4(c.x, c.y, c.z, c.w);
     }
     const PackedSmem sm = carve_p<TX, TY, TZ>(smem, sizeof(float4) * (size_t)(nwin + 1), DB ? 2 : 1);
-    fill_offsets_p(a, sm.off, G::NT);
     fill_rep_cache<float>(a, sm.rep);
     __syncthreads();
 
     const PThread<TX, TY, TZ> th;
-    const float4 *po = sm.off + 2 * kNVec * th.p;
+    // offset records read from the kernel parameters (constant bank): warp-
+    // uniform, so they stay off the shared-memory pipe
+    const float4 *po = &a.offp[th.p][0][0];
     const float2 S2 = p_dup(a.S);
     unsigned st = 0;
     int buf = 0;
@@ -700,12 +686,13 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_force_p(const __grid_constant
         tab0[k] = make_float4(c0.x, c0.y, c0.z, c0.w);
     }
     const PackedSmem sm = carve_p<TX, TY, TZ>(smem, sizeof(float4) * (size_t)(nwin + 1), 1);
-    fill_offsets_p(a, sm.off, G::NT);
     fill_rep_cache<float>(a, sm.rep);
     __syncthreads();
 
     const PThread<TX, TY, TZ> th;
-    const float4 *po = sm.off + 2 * kNVec * th.p;
+    // offset records read from the kernel parameters (constant bank): warp-
+    // uniform, so they stay off the shared-memory pipe
+    const float4 *po = &a.offp[th.p][0][0];
     const float2 S2 = p_dup(a.S);
     const float conv = (float)a.acc_conv;
     unsigned st = 0;
