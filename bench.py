@@ -522,8 +522,8 @@ def run_gpu(args):
     t_dens = phases["density"] / max(nsteps, 1) / 1e3
     ach = FLOPS_FORCE_SITE * natoms / t_force / 1e12
     traffic = None
-    if NCU_FORCE_TRAFFIC["source_sha"] == kernel_source_sha():
-        traffic = NCU_FORCE_TRAFFIC["bytes_per_launch"]
+    if NCU_FORCE_TRAFFIC["source_sha"] == kernel_source_sha() and args.workload == "c3":
+        traffic = NCU_FORCE_TRAFFIC["bytes_per_launch"]  # captured on this workload only
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     step_s = el_ms / 1e3 / args.steps
