@@ -315,6 +315,25 @@ int64_t or_nearest_site(int bx, int by, int bz, double a0, const double p[3])
     return idc < ide ? idc : ide;
 }
 
+/* Wigner-Seitz defect count of a configuration (the vacancy / interstitial
+ * counts behind the Frenkel-pair curves of Sec. 5.1): every atom belongs to
+ * the cell of its nearest lattice site; a site whose cell holds no atom is a
+ * vacancy, every atom beyond the first in a cell an interstitial. */
+void or_ws_defects(int bx, int by, int bz, double a0, int64_t N, const double *x, int64_t *n_vac, int64_t *n_int)
+{
+    int64_t ns = 2 * (int64_t)bx * by * bz;
+    int64_t *occ = (int64_t *)calloc((size_t)(ns > 0 ? ns : 1), sizeof(int64_t));
+    for (int64_t i = 0; i < N; ++i) occ[or_nearest_site(bx, by, bz, a0, x + 3 * i)]++;
+    int64_t v = 0, e = 0;
+    for (int64_t s = 0; s < ns; ++s) {
+        if (occ[s] == 0) ++v;
+        if (occ[s] > 1) e += occ[s] - 1;
+    }
+    free(occ);
+    *n_vac = v;
+    *n_int = e;
+}
+
 /* PKA site of Sec. 5.1: the atom at the box centre, i.e. the cube corner of
  * cell (bx/2, by/2, bz/2). */
 int64_t or_pka_site(int bx, int by, int bz)

@@ -56,6 +56,8 @@ def lib():
         L.or_nearest_site.restype = C.c_int64
         L.or_pka_site.argtypes = [C.c_int, C.c_int, C.c_int]
         L.or_pka_site.restype = C.c_int64
+        L.or_ws_defects.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int64, _D,
+                                    C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.or_eam.argtypes = [C.c_void_p, C.c_int64, _D, _D, C.c_int, C.c_int, _D, _D, _D, _D]
         L.or_eam_sample.argtypes = [C.c_void_p, C.c_int64, _D, _D, C.c_int, C.c_int64, _I64, _D, _D, _D]
         L.or_pair_list.argtypes = [C.c_int64, _D, _D, C.c_double, C.c_int, C.c_int64, _I64, _I64, _D]
@@ -180,6 +182,14 @@ def site_position(bx, by, a0, sid) -> np.ndarray:
 def nearest_site(bx, by, bz, a0, p) -> int:
     p = _c64(p)
     return int(lib().or_nearest_site(bx, by, bz, a0, _d(p)))
+
+
+def ws_defects(bx, by, bz, a0, x):
+    """(vacancies, interstitials) of the Wigner-Seitz analysis of positions x."""
+    x = _c64(x).reshape(-1, 3)
+    v, i = C.c_int64(), C.c_int64()
+    lib().or_ws_defects(bx, by, bz, a0, x.shape[0], _d(x), C.byref(v), C.byref(i))
+    return int(v.value), int(i.value)
 
 
 def pka_site(bx, by, bz) -> int:

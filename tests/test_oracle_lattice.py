@@ -147,3 +147,45 @@ def test_offset_memory_independent_of_system_size(oracle):
     # O(M) offsets vs O(MN) neighbour lists (Sec. 3): the offset index depends
     # on a0 and the radius only
     assert len(oracle.offsets(A0, 6.8, 0)) == len(oracle.offsets(A0, 6.8, 1)) == 112
+
+
+# --- Wigner-Seitz defect count (Frenkel pairs, Sec. 5.1) --------------------
+
+def _ws_brute(nx, ny, nz, a0, x):
+    """Occupancy by brute force: each atom to the closest site over all sites
+    and periodic images (ties to the lower site index)."""
+    sites = synth.bcc_positions(nx, ny, nz, a0)
+    L = synth.box(nx, ny, nz, a0)
+    occ = np.zeros(len(sites), int)
+    for p in x:
+        d = sites - p
+        d -= L * np.round(d / L)
+        r2 = np.einsum("ij,ij->i", d, d)
+        occ[int(np.flatnonzero(r2 <= r2.min() + 1e-12)[0])] += 1
+    return int((occ == 0).sum()), int(np.maximum(occ - 1, 0).sum())
+
+
+def test_ws_defects_perfect_crystal(oracle):
+    x = synth.bcc_positions(6, 5, 7)
+    assert oracle.ws_defects(6, 5, 7, synth.A0_FE, x) == (0, 0)
+
+
+def test_ws_defects_single_frenkel_pair(oracle):
+    a0 = synth.A0_FE
+    x = synth.bcc_positions(6, 6, 6, a0)
+    # an octahedral interstitial position (face centre of a cube): nearest
+    # sites are occupied corners, so one vacancy and one interstitial
+    x[17] = np.array([2.5, 2.5, 2.0]) * a0 + 0.01
+    assert oracle.ws_defects(6, 6, 6, a0, x) == (1, 1)
+    # a second atom into the first one's empty cell: still one pair
+    x[40] = synth.bcc_positions(6, 6, 6, a0)[17] + 0.3
+    assert oracle.ws_defects(6, 6, 6, a0, x) == (1, 1)
+
+
+def test_ws_defects_match_brute_force(oracle):
+    a0 = synth.A0_FE
+    for seed in range(3):
+        x = synth.cascade_snapshot(5, 5, 5, 0.25, 6, 2, seed)
+        got = oracle.ws_defects(5, 5, 5, a0, x)
+        assert got == _ws_brute(5, 5, 5, a0, x)
+        assert got[0] == got[1] > 0  # atoms = sites: vacancies = interstitials
