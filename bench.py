@@ -549,6 +549,7 @@ def run_gpu(args):
                 "phase_ms_per_step": {k: v_ / max(nsteps, 1) for k, v_ in phases.items()},
                 "l1_data_pipe": l1, "kernel_source_sha": sha}
     stats_end = sim.stats()
+    frenkel = [int(c) for c in sim.defects()]
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -617,7 +618,8 @@ def run_gpu(args):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "clocks": clocks, "fp64_path": fp64,
                 "end_state": {"step": stats_end["step"], "time_fs": stats_end["time"],
-                              "n_runaway": stats_end["n_runaway"], "status": stats_end["status"]}}
+                              "n_runaway": stats_end["n_runaway"], "status": stats_end["status"],
+                              "frenkel_pairs": sum(frenkel)}}
         print(json.dumps(line))
     return 0
 

@@ -261,6 +261,14 @@ int misa_tile_valid(int precision, int index);
 int misa_tile_current(const misa_sim *s);
 int misa_tile_current_force(const misa_sim *s);
 
+/* Wigner-Seitz defect count of every replica (Sec. 5.1, the vacancy and
+ * interstitial counts behind the Frenkel-pair curves): each atom belongs to
+ * the cell of its nearest site -- an array atom to its own site, a run-away
+ * to its home -- and since atoms = sites, vacancies = interstitials =
+ * Frenkel pairs.  n_frenkel receives nrep counts (host memory).  Uses the
+ * library's scratch; synchronises. */
+int misa_defects(misa_sim *s, int64_t *n_frenkel);
+
 /* Re-runs the tile autotuner on the current state (call it once after
  * loading a representative configuration, e.g. an equilibrated crystal:
  * the shapes that win on the perfect crystal of misa_create are not always

@@ -1248,6 +1248,29 @@ int misa_step(misa_sim *s, int n)
     return MISA_OK;
 }
 
+int misa_defects(misa_sim *s, int64_t *n_frenkel)
+{
+    if (!s || !n_frenkel) return MISA_EINVAL;
+    unsigned long long *filled = reinterpret_cast<unsigned long long *>(s->partial);
+    CK(cudaMemsetAsync(filled, 0, sizeof(unsigned long long) * s->nrep, s->st));
+    if (s->prec == MISA_FP64) {
+        k_defects_reset<double><<<list_grid(s), 256, 0, s->st>>>(md_args<double>(s), s->aux_int);
+        k_defects_count<double><<<list_grid(s), 256, 0, s->st>>>(md_args<double>(s), s->aux_int, filled);
+    } else {
+        k_defects_reset<float><<<list_grid(s), 256, 0, s->st>>>(md_args<float>(s), s->aux_int);
+        k_defects_count<float><<<list_grid(s), 256, 0, s->st>>>(md_args<float>(s), s->aux_int, filled);
+    }
+    CK(cudaGetLastError());
+    std::vector<unsigned long long> f(s->nrep);
+    std::vector<DevScalars> h(s->nrep);
+    CK(cudaMemcpyAsync(f.data(), filled, sizeof(unsigned long long) * s->nrep, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(h.data(), s->sc, sizeof(DevScalars) * s->nrep, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    for (int r = 0; r < s->nrep; ++r) n_frenkel[r] = (int64_t)h[r].n_ra - (int64_t)f[r];
+    s->launches += 2;
+    return check_status(s);
+}
+
 int misa_retune(misa_sim *s)
 {
     if (!s) return MISA_EINVAL;

@@ -831,6 +831,35 @@ __global__ void k_sum_stage2(const double *partial, int n, double *out)
 
 // Site map read-out (storage check): atom per site; run-away ids at their
 // pooled slots.
+// Wigner-Seitz defect count (the vacancies and interstitials behind the
+// Frenkel-pair curves of Sec. 5.1).  An array atom lies within the skin of
+// its own site, so it belongs to that site's cell; a run-away belongs to its
+// home, its nearest site.  Atoms = sites, so vacancies = interstitials =
+// run-aways - (distinct empty sites that are the home of a run-away).
+// k_defects_reset marks every run-away home; k_defects_count claims each
+// empty home once.  grid.y = replica.
+template <typename T>
+__global__ void k_defects_reset(MdArgs<T> m, int *mark)
+{
+    const int r = blockIdx.y;
+    const RepDesc rd = m.reps[r];
+    const int n = m.sc[r].n_ra;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        mark[rd.site_base + m.ra_home[rd.ra_base + j]] = -1;
+}
+
+template <typename T>
+__global__ void k_defects_count(MdArgs<T> m, int *mark, unsigned long long *filled)
+{
+    const int r = blockIdx.y;
+    const RepDesc rd = m.reps[r];
+    const int n = m.sc[r].n_ra;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const long long h = rd.site_base + m.ra_home[rd.ra_base + j];
+        if (m.sid[h] < 0 && atomicCAS(&mark[h], -1, j) == -1) atomicAdd(&filled[r], 1ull);
+    }
+}
+
 template <typename T>
 __global__ void k_site_map(MdArgs<T> m, long long *site_atom, long long *ra_ids)
 {

@@ -108,6 +108,7 @@ def lib():
         L.misa_tile_current.argtypes = [C.c_void_p]
         L.misa_tile_current_force.argtypes = [C.c_void_p]
         L.misa_retune.argtypes = [C.c_void_p]
+        L.misa_defects.argtypes = [C.c_void_p, C.c_void_p]
         L.misa_eam_forces_static.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
                                              C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
                                              C.c_void_p, C.c_void_p]
@@ -359,6 +360,12 @@ class Sim:
     def tile(self):
         """Tile shape of the density pass (cells)."""
         return tile_shapes()[lib().misa_tile_current(self.h) - 1]
+
+    def defects(self):
+        """Frenkel pairs (vacancies = interstitials) of every replica."""
+        out = np.empty(lib().misa_replica_count(self.h), np.int64)
+        self._check(lib().misa_defects(self.h, _ptr(out)))
+        return out
 
     def retune(self):
         """Re-run the tile autotuner on the current state."""

@@ -262,3 +262,29 @@ def test_integer_pipe_conversions_match_hardware(misa):
     # the FP64 integration kernels convert float <-> double with integer
     # operations; they must agree bit for bit with the GPU's conversions
     assert misa.selftest(1 << 22) == (0, 0)
+
+
+def test_frenkel_pairs_match_oracle(misa, pot, oracle):
+    # Wigner-Seitz count on the device (site array + run-away homes) against
+    # the oracle's nearest-site occupancy of the same positions: after
+    # set_state on cascade snapshots, and after a knock-on cascade has run
+    a0 = synth.A0_FE
+    for dims, x in (((12, 9, 10), synth.cascade_snapshot(12, 9, 10, 0.12, 24, 8, 2)),
+                    ((6, 6, 6), synth.cascade_snapshot(6, 6, 6, 0.1, 5, 3, 3))):
+        with misa.Sim(pot, *dims, precision="fp32") as s:
+            s.set_state(x)
+            nf = s.defects()
+            nv, ni = oracle.ws_defects(*dims, a0, s.positions())
+            assert nv == ni == int(nf[0]) > 0
+    n = 10
+    with misa.Sim(pot, n, precision="fp32", dx_max=0.02, reassign_period=5) as s:
+        s.set_state(synth.thermal_snapshot(n, n, n, 0.08, 5),
+                    synth.maxwell_velocities(2 * n ** 3, 300.0, synth.MASS_FE, 6))
+        s.insert_pka(-1, 2000.0, synth.random_direction(7))
+        counts = []
+        for _ in range(6):
+            s.step(100)
+            nv, ni = oracle.ws_defects(n, n, n, a0, s.positions())
+            counts.append(int(s.defects()[0]))
+            assert nv == ni == counts[-1]
+        assert max(counts) > 0
