@@ -537,6 +537,129 @@ int or_eam(const or_pot *p, int64_t N, const double *x, const double L[3], int m
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Alloys (Sec. 2.2, Eq. eam_base and eam_force_ij with atom types)          */
+/* ------------------------------------------------------------------------ */
+/* Species a has a density function rho_a(r) and an embedding function
+ * F_a(rho); each unordered pair (a, b) a pair function phi_ab(r).  Each is
+ * held in an or_pot on the same grids: spec[a] keeps rho_a in f and F_a in F,
+ * pair[ab] keeps phi_ab in phi, ab = a n - a (a - 1)/2 + (b - a) for a <= b. */
+typedef struct or_alloy {
+    int nsp;
+    or_pot **spec, **pair;
+} or_alloy;
+
+static int pair_slot(int a, int b, int nsp)
+{
+    if (a > b) {
+        int t = a;
+        a = b;
+        b = t;
+    }
+    return a * nsp - a * (a - 1) / 2 + (b - a);
+}
+
+or_alloy *or_alloy_new(int n, int nsp, double rc, double rho_max, const double *f, const double *F,
+                       const double *phi)
+{
+    if (nsp < 1 || nsp > 8) return NULL;
+    int npair = nsp * (nsp + 1) / 2;
+    or_alloy *a = (or_alloy *)calloc(1, sizeof(or_alloy));
+    a->nsp = nsp;
+    a->spec = (or_pot **)calloc((size_t)nsp, sizeof(or_pot *));
+    a->pair = (or_pot **)calloc((size_t)npair, sizeof(or_pot *));
+    double *zero = (double *)calloc((size_t)n, sizeof(double));
+    for (int s = 0; s < nsp; ++s) a->spec[s] = or_pot_new(n, rc, rho_max, f + (size_t)s * n, zero, F + (size_t)s * n);
+    for (int q = 0; q < npair; ++q) a->pair[q] = or_pot_new(n, rc, rho_max, zero, phi + (size_t)q * n, zero);
+    free(zero);
+    return a;
+}
+
+void or_alloy_free(or_alloy *a)
+{
+    if (!a) return;
+    for (int s = 0; s < a->nsp; ++s) or_pot_free(a->spec[s]);
+    for (int q = 0; q < a->nsp * (a->nsp + 1) / 2; ++q) or_pot_free(a->pair[q]);
+    free(a->spec);
+    free(a->pair);
+    free(a);
+}
+
+typedef struct {
+    const or_alloy *al;
+    const int8_t *type;
+    const double *Fp;
+    int ti;
+    double Fpi;
+    double rho, ephi, F[3];
+} alloy_ctx;
+
+static void visit_rho_alloy(void *c, int64_t j, const double dv[3], double r)
+{
+    (void)dv;
+    alloy_ctx *e = (alloy_ctx *)c;
+    double d;
+    e->rho += pair_fn(e->al->spec[e->type[j]], 0, r, &d); /* step 1: rho_i = sum_j rho_{t_j}(r_ij) */
+}
+
+static void visit_force_alloy(void *c, int64_t j, const double dv[3], double r)
+{
+    alloy_ctx *e = (alloy_ctx *)c;
+    const int tj = e->type[j];
+    double dfj, dfi, dphi;
+    pair_fn(e->al->spec[tj], 0, r, &dfj);   /* rho_{t_j}'(r) */
+    pair_fn(e->al->spec[e->ti], 0, r, &dfi); /* rho_{t_i}'(r) */
+    e->ephi += 0.5 * pair_fn(e->al->pair[pair_slot(e->ti, tj, e->al->nsp)], 1, r, &dphi);
+    if (r < e->al->spec[0]->r_floor) return;
+    /* Eq. eam_force_ij: -[F'_i rho_j'(r) + F'_j rho_i'(r) + phi_ij'(r)] (x_i - x_j)/r */
+    double s = -(e->Fpi * dfj + e->Fp[j] * dfi + dphi) / r;
+    for (int d = 0; d < 3; ++d) e->F[d] += s * dv[d];
+}
+
+/* or_eam for an alloy: type[i] in [0, nsp) is the species of atom i. */
+int or_eam_alloy(const or_alloy *al, int64_t N, const double *x, const int8_t *type, const double L[3], int mode,
+                 int nthreads, double *rho, double *Fp, double *E, double *F)
+{
+    if (!al || N < 0) return -1;
+    for (int64_t i = 0; i < N; ++i)
+        if (type[i] < 0 || type[i] >= al->nsp) return -2;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    const size_t n1 = (size_t)(N > 0 ? N : 1);
+    double *xw = (double *)malloc(sizeof(double) * 3 * n1);
+    double *rh = (double *)malloc(sizeof(double) * n1);
+    double *fp = (double *)malloc(sizeof(double) * n1);
+    double *fe = (double *)malloc(sizeof(double) * n1);
+    wrap_positions(N, x, L, xw);
+    or_nbr nb;
+    nbr_init(&nb, N, xw, L, al->spec[0]->rc, mode);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < N; ++i) {
+        alloy_ctx e = {al, type, NULL, type[i], 0.0, 0.0, 0.0, {0, 0, 0}};
+        nbr_visit(&nb, i, visit_rho_alloy, &e);
+        double d;
+        rh[i] = e.rho;
+        fe[i] = embed_fn(al->spec[type[i]], e.rho, &d); /* F_{t_i}(rho_i) */
+        fp[i] = d;                                       /* step 2 */
+    }
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < N; ++i) {
+        alloy_ctx e = {al, type, fp, type[i], fp[i], 0.0, 0.0, {0, 0, 0}};
+        nbr_visit(&nb, i, visit_force_alloy, &e);
+        if (E) E[i] = fe[i] + e.ephi;
+        if (F)
+            for (int d = 0; d < 3; ++d) F[3 * i + d] = e.F[d];
+    }
+    if (rho) memcpy(rho, rh, sizeof(double) * (size_t)N);
+    if (Fp) memcpy(Fp, fp, sizeof(double) * (size_t)N);
+    nbr_free(&nb);
+    free(xw); free(rh); free(fp); free(fe);
+    return 0;
+}
+
 /* Same quantities for a sample of atoms only (for systems too large for a
  * full oracle pass): each target's density, energy and force, with the
  * embedding derivatives of its neighbours computed on demand.  Cell list. */

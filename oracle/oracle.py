@@ -56,6 +56,10 @@ def lib():
         L.or_nearest_site.restype = C.c_int64
         L.or_pka_site.argtypes = [C.c_int, C.c_int, C.c_int]
         L.or_pka_site.restype = C.c_int64
+        L.or_alloy_new.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _D, _D, _D]
+        L.or_alloy_new.restype = C.c_void_p
+        L.or_alloy_free.argtypes = [C.c_void_p]
+        L.or_eam_alloy.argtypes = [C.c_void_p, C.c_int64, _D, C.c_void_p, _D, C.c_int, C.c_int, _D, _D, _D, _D]
         L.or_ws_defects.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int64, _D,
                                     C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.or_eam.argtypes = [C.c_void_p, C.c_int64, _D, _D, C.c_int, C.c_int, _D, _D, _D, _D]
@@ -182,6 +186,41 @@ def site_position(bx, by, a0, sid) -> np.ndarray:
 def nearest_site(bx, by, bz, a0, p) -> int:
     p = _c64(p)
     return int(lib().or_nearest_site(bx, by, bz, a0, _d(p)))
+
+
+class Alloy:
+    """Oracle alloy potential: per-species density and embedding tables,
+    pair tables for a <= b in row-major upper-triangle order."""
+
+    def __init__(self, al):
+        nsp = al.nsp
+        f = _c64(al.f).reshape(nsp, al.n)
+        F = _c64(al.F).reshape(nsp, al.n)
+        phi = _c64(al.phi).reshape(nsp * (nsp + 1) // 2, al.n)
+        self.h = lib().or_alloy_new(al.n, nsp, al.rc, al.rho_max, _d(f), _d(F), _d(phi))
+        if not self.h:
+            raise ValueError("bad alloy tables")
+        self.nsp = nsp
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().or_alloy_free(self.h)
+            self.h = None
+
+
+def eam_alloy(al: Alloy, x, types, L, mode: int = 0, nthreads: int = 0):
+    """rho, F'(rho), per-atom energy, forces of an alloy configuration."""
+    x = _c64(x).reshape(-1, 3)
+    L = _c64(L)
+    t = np.ascontiguousarray(types, dtype=np.int8)
+    n = x.shape[0]
+    rho, fp, e = np.empty(n), np.empty(n), np.empty(n)
+    f = np.empty((n, 3))
+    rc = lib().or_eam_alloy(al.h, n, _d(x), t.ctypes.data_as(C.c_void_p), _d(L), mode, nthreads, _d(rho), _d(fp),
+                            _d(e), _d(f))
+    if rc != 0:
+        raise ValueError(f"or_eam_alloy failed ({rc})")
+    return rho, fp, e, f
 
 
 def ws_defects(bx, by, bz, a0, x):

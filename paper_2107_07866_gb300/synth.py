@@ -126,6 +126,94 @@ def potential(n: int = N_KNOTS, rc: float = RC, a0: float = A0_FE) -> Potential:
     return Potential(n, rc, rho_max, fs(r), ps(r), embed_analytic(rho))
 
 
+# ---------------------------------------------------------------------------
+# alloys: per-species density and embedding functions, pair functions per
+# unordered species pair (the paper's Fe-Cu-Ni tables are not available;
+# these analytic forms stand in for them)
+# ---------------------------------------------------------------------------
+
+# species: density prefactor A and decay b of A exp(-b (r/2.47 - 1)), embedding
+# strength c of -c sqrt(rho), Morse depth D and minimum r0 of the pair term;
+# species 0 is the single-species potential above
+SPECIES = (
+    dict(A=1.0, b=3.0, c=1.8, D=0.40, r0=2.60),
+    dict(A=0.8, b=3.4, c=1.5, D=0.35, r0=2.65),
+    dict(A=1.1, b=3.2, c=1.6, D=0.45, r0=2.55),
+    dict(A=0.9, b=2.8, c=1.7, D=0.38, r0=2.62),
+)
+
+
+def pair_index(a: int, b: int, nsp: int) -> int:
+    """Row of pair (a, b) in the upper-triangle pair table (a <= b)."""
+    a, b = min(a, b), max(a, b)
+    return a * nsp - a * (a - 1) // 2 + (b - a)
+
+
+def alloy_functions(nsp: int):
+    """Analytic (untruncated) rho_a, rho_a', F_a, F_a', phi_ab, phi_ab' as callables."""
+    sp = SPECIES[:nsp]
+
+    def dens(a):
+        A, b = sp[a]["A"], sp[a]["b"]
+        g = lambda r: A * np.exp(-b * (np.asarray(r, dtype=np.float64) / 2.47 - 1.0))
+        dg = lambda r: -b / 2.47 * g(r)
+        return g, dg
+
+    def emb(a):
+        c = sp[a]["c"]
+        return (lambda rho: -c * np.sqrt(np.asarray(rho, dtype=np.float64)),
+                lambda rho: -0.5 * c / np.sqrt(np.asarray(rho, dtype=np.float64)))
+
+    def pair(a, b):
+        D = math.sqrt(sp[a]["D"] * sp[b]["D"])
+        r0 = 0.5 * (sp[a]["r0"] + sp[b]["r0"])
+        g = lambda r: D * (np.exp(-3.2 * (np.asarray(r, dtype=np.float64) - r0))
+                           - 2.0 * np.exp(-1.6 * (np.asarray(r, dtype=np.float64) - r0)))
+        dg = lambda r: D * (-3.2 * np.exp(-3.2 * (np.asarray(r, dtype=np.float64) - r0))
+                            + 3.2 * np.exp(-1.6 * (np.asarray(r, dtype=np.float64) - r0)))
+        return g, dg
+
+    return dens, emb, pair
+
+
+@dataclass
+class AlloyPotential:
+    nsp: int
+    n: int
+    rc: float
+    rho_max: float
+    f: np.ndarray    # (nsp, n): density function of each species on r_k
+    F: np.ndarray    # (nsp, n): embedding function of each species on rho_k
+    phi: np.ndarray  # (nsp (nsp + 1) / 2, n): pair functions, rows by pair_index
+
+    def species(self, a: int) -> Potential:
+        """The single-species potential of species a."""
+        return Potential(self.n, self.rc, self.rho_max, self.f[a], self.phi[pair_index(a, a, self.nsp)], self.F[a])
+
+
+def alloy_potential(nsp: int = 2, n: int = N_KNOTS, rc: float = RC, a0: float = A0_FE) -> AlloyPotential:
+    """Knot tables of an nsp-species alloy (shifted-force truncated density
+    and pair functions); the embedding tables span [0, 4 max_a rho_eq,a]."""
+    if not 1 <= nsp <= len(SPECIES):
+        raise ValueError("1 to 4 species")
+    dens, emb, pair = alloy_functions(nsp)
+    r = np.arange(n, dtype=np.float64) * (rc / (n - 1))
+    rho_max = 4.0 * equilibrium_density(a0, rc) * max(s["A"] for s in SPECIES[:nsp]) * math.exp(
+        max(s["b"] for s in SPECIES[:nsp]) - 3.0)
+    rho = np.arange(n, dtype=np.float64) * (rho_max / (n - 1))
+    f = np.stack([truncated(*dens(a), rc)[0](r) for a in range(nsp)])
+    F = np.stack([emb(a)[0](rho) for a in range(nsp)])
+    phi = np.stack([truncated(*pair(a, b), rc)[0](r) for a in range(nsp) for b in range(a, nsp)])
+    return AlloyPotential(nsp, n, rc, rho_max, f, F, phi)
+
+
+def random_types(n_atoms: int, fractions, seed: int) -> np.ndarray:
+    """Species of each atom: i.i.d. draws with the given fractions (int8)."""
+    g = _rng(seed)
+    p = np.asarray(fractions, dtype=np.float64)
+    return g.choice(len(p), size=n_atoms, p=p / p.sum()).astype(np.int8)
+
+
 def knot_perturbation(n: int, sigma: float, seed: int):
     """Three arrays eps ~ N(0, sigma^2), one per table."""
     g = _rng(seed)
