@@ -50,8 +50,11 @@ def test_dimer_closed_form(oracle, alloy3, a, b):
         assert e[0] == pytest.approx(Fa + 0.5 * p, rel=1e-6)
         assert e[1] == pytest.approx(Fb + 0.5 * p, rel=1e-6)
         dE = dFa * drb + dFb * dra + dp  # d(E_0 + E_1)/dr
-        assert f[0, 0] == pytest.approx(dE, rel=1e-6)   # atom 0 is pulled along +x when dE/dr > 0
-        assert f[1, 0] == pytest.approx(-dE, rel=1e-6)
+        # a dimer's densities are ~1, where -c sqrt(rho) bends sharply: the
+        # derivative of the cubic Hermite interpolant is accurate to
+        # O(h_rho^3 d4F/drho4) ~ 1e-5 there (h_rho = rho_max / 4999)
+        assert f[0, 0] == pytest.approx(dE, rel=5e-5)   # atom 0 is pulled along +x when dE/dr > 0
+        assert f[1, 0] == pytest.approx(-dE, rel=5e-5)
         assert np.abs(f[:, 1:]).max() < 1e-12
 
 
