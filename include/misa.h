@@ -223,6 +223,23 @@ int misa_load(misa_sim *s, const char *path);
  * device (Sec. 4.1) and re-evaluates the forces of the current positions. */
 int misa_set_tables(misa_sim *s, const double *f_knots, const double *phi_knots, const double *F_knots);
 
+/* Alloys (Sec. 2.2: Eq. eam_base and Eq. eam_force_ij with atom types; the
+ * n(n+1)/2 + 3n functions of an n-type system).  Replaces the potential by
+ * n_species (1..4) types on the grids given at create:
+ *   f_knots    n_species x n_knots  density function rho_a(r) of each type
+ *   F_knots    n_species x n_knots  embedding function F_a(rho) of each type
+ *   phi_knots  n_species (n_species + 1)/2 x n_knots  pair functions phi_ab(r),
+ *              rows (a, b), a <= b, in the order (0,0), (0,1), .., (0,n-1), (1,1), ..
+ *   types      natoms bytes: type of each atom id (ignored for one species)
+ * Host or device pointers.  Types stay with the atoms; with one species the
+ * single-type tables and gathers are used.  Recomputes the forces of the
+ * current positions and drops a captured step graph; synchronises;
+ * MISA_EINVAL for a type outside [0, n_species).  Alloy passes run one
+ * thread per site with tables in global memory; misa_loss_grad and
+ * misa_save keep to one type.  misa_set_tables returns to one type. */
+int misa_set_species(misa_sim *s, int n_species, const double *f_knots, const double *F_knots,
+                     const double *phi_knots, const int8_t *types);
+
 /* Potential fitting (no counterpart in the paper): loss and its gradient
  * with respect to the 3 n_knots knot values, for the current positions of
  * every replica against target forces Fref (3 natoms doubles, eV/A, by atom

@@ -50,6 +50,8 @@ struct AdjArgs {
     T *ra_lx, *ra_ly, *ra_lz;        // per run-away slot
     T *dl, *ra_dl;                   // D_lambda rho per site / run-away slot
     int nvec;                        // offsets within rc + 2 skin (prefix of kLVec)
+    const int *tile_flag;            // null: every site scans the run-away list
+    int tx, ty, tz;
 };
 
 // one pair seen from atom i: |r| in lattice units, unit vector i -> j, the
@@ -70,9 +72,9 @@ struct AdjPair {
 // split into integer and fraction) plus (r - |n|) S with
 // r - |n| = q / (r + |n|), q = (2n + d).d: full precision in t also in FP32
 // (x is near 2000, where a plain FP32 r S keeps only ~1e-4 of t).
-template <typename T>
-__device__ __forceinline__ bool adj_pair(const AdjArgs<T> &a, int nx, int ny, int nz, T dx, T dy, T dz, bool ra,
-                                         long long j, AdjPair<T> &P)
+template <typename T, typename A>
+__device__ __forceinline__ bool adj_pair(const A &a, int nx, int ny, int nz, T dx, T dy, T dz, bool ra, long long j,
+                                         AdjPair<T> &P)
 {
     const T q = ((T)(2 * nx) + dx) * dx + ((T)(2 * ny) + dy) * dy + ((T)(2 * nz) + dz) * dz;
     const int n2 = nx * nx + ny * ny + nz * nz;
@@ -116,9 +118,10 @@ __device__ __forceinline__ bool adj_pair(const AdjArgs<T> &a, int nx, int ny, in
 
 // Visits every neighbour j of array atom i (pooled site s, replica-local
 // site ls) inside rc: array atoms through the offset vectors, then the
-// replica's run-away list.
-template <typename T, typename Fn>
-__device__ __forceinline__ void visit_site(const AdjArgs<T> &a, const RepDesc &rd, int nra, long long ls, Fn &fn)
+// replica's run-away list (only from tiles flagged as within reach of a
+// run-away when a.tile_flag is set; rd's tile counts are those tiles').
+template <typename T, typename A, typename Fn>
+__device__ __forceinline__ void visit_site(const A &a, const RepDesc &rd, int nra, long long ls, Fn &fn)
 {
     const long long s = rd.site_base + ls;
     const T uix = a.ux[s], uiy = a.uy[s], uiz = a.uz[s];
@@ -135,6 +138,11 @@ __device__ __forceinline__ void visit_site(const AdjArgs<T> &a, const RepDesc &r
         if (a.sid[t] < 0) continue;
         AdjPair<T> P;
         if (adj_pair<T>(a, o.x, o.y, o.z, a.ux[t] - uix, a.uy[t] - uiy, a.uz[t] - uiz, false, t, P)) fn(P);
+    }
+    if (nra == 0) return;
+    if (a.tile_flag) {
+        const int tl = rd.tile_base + ((cz / a.tz) * rd.nty + cy / a.ty) * rd.ntx + (x2 >> 1) / a.tx;
+        if (!a.tile_flag[tl]) return;
     }
     int X, Y, Z;
     site_lat(ls, rd.nx, rd.ny, X, Y, Z);
@@ -157,8 +165,8 @@ __device__ __forceinline__ void visit_site(const AdjArgs<T> &a, const RepDesc &r
 
 // Visits every neighbour of run-away j (pooled slot g): array sites in a
 // 7-cell window around its home site, then the other run-aways.
-template <typename T, typename Fn>
-__device__ __forceinline__ void visit_ra(const AdjArgs<T> &a, const RepDesc &rd, int nra, int jl, Fn &fn)
+template <typename T, typename A, typename Fn>
+__device__ __forceinline__ void visit_ra(const A &a, const RepDesc &rd, int nra, int jl, Fn &fn)
 {
     const int g = rd.ra_base + jl;
     int X, Y, Z;

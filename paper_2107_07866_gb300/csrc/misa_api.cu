@@ -14,6 +14,7 @@
 #include "misa.h"
 #include "misa_adjoint.cuh"
 #include "misa_packed.cuh"
+#include "misa_alloy.cuh"
 
 using namespace misa;
 
@@ -150,6 +151,12 @@ struct misa_sim {
     void *dl = nullptr, *ra_dl = nullptr;
     double *adj_partial = nullptr, *adj_grad = nullptr, *adj_eref = nullptr, *adj_fref = nullptr;
     int adj_cta = 0;
+    // alloys (misa_set_species): species per atom id, coefficient tables
+    int nsp = 1;
+    int8_t *atype = nullptr;
+    double *al_knots = nullptr;
+    void *al_fv = nullptr, *al_fd = nullptr, *al_Fv = nullptr, *al_pv = nullptr, *al_pd = nullptr;
+    int al_cap = 0;  // species the alloy arrays were allocated for
     // captured step graph
     bool use_graph = true;
     cudaGraphExec_t graph = nullptr;
@@ -554,8 +561,74 @@ void launch_force(misa_sim *s, const GatherArgs<T> &g, bool energy)
 }
 
 template <typename T>
+AlloyArgs<T> alloy_args(misa_sim *s, int kick, bool energy)
+{
+    AlloyArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.reps = s->reps_d;
+    a.nrep = s->nrep;
+    a.sid = s->sid;
+    a.ux = (const T *)s->s[0]; a.uy = (const T *)s->s[1]; a.uz = (const T *)s->s[2];
+    a.fp = (T *)s->fp; a.rho_out = (T *)s->rho; a.e_out = s->esite;
+    a.ax = (T *)s->a[0]; a.ay = (T *)s->a[1]; a.az = (T *)s->a[2];
+    a.vx = s->v[0]; a.vy = s->v[1]; a.vz = s->v[2];
+    a.ra_home = s->ra_home; a.ra_id = s->ra_id;
+    a.ra_ux = (const T *)s->ra_s[0]; a.ra_uy = (const T *)s->ra_s[1]; a.ra_uz = (const T *)s->ra_s[2];
+    a.ra_fp = (T *)s->ra_fp; a.ra_rho = (T *)s->ra_rho; a.ra_e = s->ra_e;
+    a.ra_ax = (T *)s->ra_a[0]; a.ra_ay = (T *)s->ra_a[1]; a.ra_az = (T *)s->ra_a[2];
+    a.ra_vx = s->ra_v[0]; a.ra_vy = s->ra_v[1]; a.ra_vz = s->ra_v[2];
+    a.sc = s->sc;
+    a.atype = s->atype;
+    a.nsp = s->nsp;
+    const int n = s->p.n_knots;
+    a.n = n;
+    a.tfv = (const Vec4<T> *)s->al_fv; a.tfd = (const Vec4<T> *)s->al_fd; a.tFv = (const Vec4<T> *)s->al_Fv;
+    a.tpv = (const Vec4<T> *)s->al_pv; a.tpd = (const Vec4<T> *)s->al_pd;
+    const double half = 0.5 * s->p.a0, hr = s->p.rc / (n - 1), hrho = s->p.rho_max / (n - 1);
+    a.S = (T)(half / hr);
+    const double rcl = s->p.rc / half;
+    a.rc2 = (T)(rcl * rcl);
+    a.rfloor2 = (T)((kRfloor / half) * (kRfloor / half));
+    a.Srho = (T)(1.0 / hrho);
+    a.rho_max = (T)s->p.rho_max;
+    a.acc_conv = kAccUnit / s->p.mass;
+    a.kick = kick;
+    a.energy = energy ? 1 : 0;
+    const double roff = (s->p.rc + 2.0 * s->p.skin) / half;
+    int nsh = 0;
+    while (nsh < kLVec.nshell && kLVec.shell_n2[nsh] <= roff * roff) ++nsh;
+    a.nvec = kLVec.shell_begin[nsh];
+    a.tile_flag = s->tile_flag;
+    const TileShape &ts = kTiles[s->tile];
+    a.tx = ts.tx; a.ty = ts.ty; a.tz = ts.tz;
+    return a;
+}
+
+// the four alloy passes (density, run-away density, force + kick, run-away force + kick)
+template <typename T>
+int launch_alloy(misa_sim *s, int kick, bool energy, bool step_marks)
+{
+    int rc = mark_tiles<T>(s);
+    if (rc) return rc;
+    const AlloyArgs<T> a = alloy_args<T>(s, kick, energy);
+    if (step_marks) mark(s);
+    k_alloy_density<T><<<site_grid(s), 256, 0, s->st>>>(a);
+    if (step_marks) mark(s);
+    k_alloy_ra_density<T><<<dim3(16, s->nrep), 256, 0, s->st>>>(a);
+    if (step_marks) mark(s);
+    k_alloy_force<T><<<site_grid(s), 256, 0, s->st>>>(a);
+    if (step_marks) mark(s);
+    k_alloy_ra_force<T><<<dim3(16, s->nrep), 256, 0, s->st>>>(a);
+    if (step_marks) mark(s);
+    s->launches += 6;
+    CK(cudaGetLastError());
+    return MISA_OK;
+}
+
+template <typename T>
 int launch_forces(misa_sim *s, int kick, bool energy, bool step_marks = false)
 {
+    if (s->nsp > 1) return launch_alloy<T>(s, kick, energy, step_marks);
     GatherArgs<T> gd, gf;
     fill_gather<T>(s, gd, false);
     fill_gather<T>(s, gf, true);
@@ -982,7 +1055,69 @@ int set_tables_impl(misa_sim *s, const double *f, const double *phi, const doubl
                                                             (Vec4<T> *)s->tab_F, (Vec4<T> *)s->tab_d0,
                                                             (Vec2<T> *)s->tab_d1);
     CK(cudaGetLastError());
+    if (s->nsp != 1 && s->graph) {  // back to the single-type passes
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+    }
+    s->nsp = 1;
     return refresh<T>(s, true);
+}
+
+// Alloy tables and per-atom species (Eq. eam_base with atom types).  One
+// species falls back to the single-type tables and gathers.
+template <typename T>
+int set_species_impl(misa_sim *s, int nsp, const double *f, const double *F, const double *phi, const int8_t *types)
+{
+    const int n = s->p.n_knots;
+    if (nsp == 1) {
+        std::vector<double> pf(n), pF(n), pp(n);
+        CK(cudaMemcpy(pf.data(), f, sizeof(double) * n, cudaMemcpyDefault));
+        CK(cudaMemcpy(pF.data(), F, sizeof(double) * n, cudaMemcpyDefault));
+        CK(cudaMemcpy(pp.data(), phi, sizeof(double) * n, cudaMemcpyDefault));
+        s->nsp = 1;
+        if (s->graph) {
+            cudaGraphExecDestroy(s->graph);
+            s->graph = nullptr;
+        }
+        return set_tables_impl<T>(s, pf.data(), pp.data(), pF.data());
+    }
+    std::vector<int8_t> ht((size_t)s->ns);
+    CK(cudaMemcpy(ht.data(), types, (size_t)s->ns, cudaMemcpyDefault));
+    for (int8_t t : ht)
+        if (t < 0 || t >= nsp) return fail(s, MISA_EINVAL, "atom type outside [0, n_species)");
+    const int npair = nsp * (nsp + 1) / 2;
+    if (nsp > s->al_cap) {
+        const int cp = kMaxSpecies, pp = kMaxSpecies * (kMaxSpecies + 1) / 2;
+        if (!s->atype) s->atype = (int8_t *)dalloc(s, (size_t)s->ns);
+        s->al_knots = (double *)dalloc(s, sizeof(double) * (size_t)n * (2 * cp + pp));
+        s->al_fv = dalloc(s, sizeof(Vec4<T>) * (size_t)n * cp);
+        s->al_fd = dalloc(s, sizeof(Vec4<T>) * (size_t)n * cp);
+        s->al_Fv = dalloc(s, sizeof(Vec4<T>) * (size_t)n * cp);
+        s->al_pv = dalloc(s, sizeof(Vec4<T>) * (size_t)n * pp);
+        s->al_pd = dalloc(s, sizeof(Vec4<T>) * (size_t)n * pp);
+        if (!s->atype || !s->al_knots || !s->al_fv || !s->al_fd || !s->al_Fv || !s->al_pv || !s->al_pd)
+            return fail(s, MISA_EOOM, "alloy tables");
+        s->al_cap = cp;
+    }
+    CK(cudaMemcpyAsync(s->atype, ht.data(), (size_t)s->ns, cudaMemcpyHostToDevice, s->st));
+    double *kf = s->al_knots, *kF = kf + (size_t)nsp * n, *kp = kF + (size_t)nsp * n;
+    CK(cudaMemcpyAsync(kf, f, sizeof(double) * (size_t)nsp * n, cudaMemcpyDefault, s->st));
+    CK(cudaMemcpyAsync(kF, F, sizeof(double) * (size_t)nsp * n, cudaMemcpyDefault, s->st));
+    CK(cudaMemcpyAsync(kp, phi, sizeof(double) * (size_t)npair * n, cudaMemcpyDefault, s->st));
+    const double hr = s->p.rc / (n - 1), hrho = s->p.rho_max / (n - 1);
+    k_alloy_tables<T><<<256, 256, 0, s->st>>>(kf, kF, kp, nsp, npair, n, hr, hrho, (Vec4<T> *)s->al_fv,
+                                              (Vec4<T> *)s->al_fd, (Vec4<T> *)s->al_Fv, (Vec4<T> *)s->al_pv,
+                                              (Vec4<T> *)s->al_pd);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->st));  // ht is a host temporary
+    s->nsp = nsp;
+    if (s->graph) {
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+    }
+    int rc = refresh<T>(s, true);
+    if (rc) return rc;
+    return check_status(s);
 }
 
 // Loss and knot gradient of the current state against target forces and
@@ -990,6 +1125,7 @@ int set_tables_impl(misa_sim *s, const double *f, const double *phi, const doubl
 template <typename T>
 int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *loss, double *grad)
 {
+    if (s->nsp > 1) return fail(s, MISA_EINVAL, "the knot gradient is built for one atom type");
     const int n = s->p.n_knots;
     const size_t capt = (size_t)s->cap * s->nrep;
     if (!s->dl) {
@@ -1248,6 +1384,17 @@ int misa_step(misa_sim *s, int n)
     return MISA_OK;
 }
 
+int misa_set_species(misa_sim *s, int n_species, const double *f_knots, const double *F_knots,
+                     const double *phi_knots, const int8_t *types)
+{
+    if (!s || n_species < 1 || n_species > kMaxSpecies || !f_knots || !F_knots || !phi_knots ||
+        (n_species > 1 && !types))
+        return s ? fail(s, MISA_EINVAL, "misa_set_species arguments") : MISA_EINVAL;
+    int rc = s->prec == MISA_FP64 ? set_species_impl<double>(s, n_species, f_knots, F_knots, phi_knots, types)
+                                  : set_species_impl<float>(s, n_species, f_knots, F_knots, phi_knots, types);
+    return rc;
+}
+
 int misa_defects(misa_sim *s, int64_t *n_frenkel)
 {
     if (!s || !n_frenkel) return MISA_EINVAL;
@@ -1481,7 +1628,11 @@ static int ckpt_io(misa_sim *s, const char *path, bool save)
     return MISA_OK;
 }
 
-int misa_save(misa_sim *s, const char *path) { return ckpt_io(s, path, true); }
+int misa_save(misa_sim *s, const char *path)
+{
+    if (s && s->nsp > 1) return fail(s, MISA_EINVAL, "checkpoints hold one atom type");
+    return ckpt_io(s, path, true);
+}
 int misa_load(misa_sim *s, const char *path) { return ckpt_io(s, path, false); }
 
 int misa_set_tables(misa_sim *s, const double *f_knots, const double *phi_knots, const double *F_knots)

@@ -109,6 +109,7 @@ def lib():
         L.misa_tile_current_force.argtypes = [C.c_void_p]
         L.misa_retune.argtypes = [C.c_void_p]
         L.misa_defects.argtypes = [C.c_void_p, C.c_void_p]
+        L.misa_set_species.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.misa_eam_forces_static.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
                                              C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
                                              C.c_void_p, C.c_void_p]
@@ -360,6 +361,18 @@ class Sim:
     def tile(self):
         """Tile shape of the density pass (cells)."""
         return tile_shapes()[lib().misa_tile_current(self.h) - 1]
+
+    def set_species(self, alloy, types):
+        """Alloy potential (synth.AlloyPotential-like: nsp, f, F, phi knot
+        arrays) and the type of every atom id."""
+        nsp = int(alloy.nsp)
+        f = np.ascontiguousarray(alloy.f, dtype=np.float64).reshape(nsp, -1)
+        F = np.ascontiguousarray(alloy.F, dtype=np.float64).reshape(nsp, -1)
+        phi = np.ascontiguousarray(alloy.phi, dtype=np.float64).reshape(nsp * (nsp + 1) // 2, -1)
+        t = np.ascontiguousarray(types, dtype=np.int8)
+        if t.shape != (self.natoms,):
+            raise ValueError("one type per atom")
+        self._check(lib().misa_set_species(self.h, nsp, _ptr(f), _ptr(F), _ptr(phi), C.c_void_p(t.ctypes.data)))
 
     def defects(self):
         """Frenkel pairs (vacancies = interstitials) of every replica."""
