@@ -151,6 +151,10 @@ WORKLOADS = {
     "c4": dict(n=None, nrep=64, seed=4, dx_max=0.02, reassign=10,
                desc="64 batched replicas, dims ~ U{20..60}^3 cells (seeded), equilibrated at 300-900 K, 1-5 keV PKA each, "
                     "FP32 forces, adaptive dt per replica, steps captured in a CUDA graph, autotuned tile"),
+    # alloy: three atom types (Eq. eam_base and eam_force_ij with types)
+    "alloy": dict(n=100, T=600.0, seed=3, pka_eV=5000.0, dx_max=0.02, reassign=10, nsp=3, fractions=(0.7, 0.2, 0.1),
+                  desc="100x100x100 cells (2,000,000 atoms), three atom types (70/20/10 %), equilibrated at 600 K "
+                       "(seed 3), 5 keV PKA, FP32 forces, adaptive dt, hash update every 10 steps"),
     # potential fitting: knot gradient of the force-matching + energy loss
     "c5": dict(n=16, nrep=16, seed=5, sigma=0.02, adjoint=True,
                desc="16 thermal snapshots of 16x16x16 cells (8,192 atoms each, 300-1500 K), targets from knots "
@@ -298,6 +302,38 @@ def run_reference_adjoint(args, ws):
     return 0
 
 
+def run_reference_alloy(args, ws):
+    """The oracle's alloy evaluation (densities, energies, forces) on a
+    bounded sample of the alloy workload; it has no alloy MD loop, so one
+    step is one force evaluation of the sample."""
+    w = WORKLOADS[args.workload]
+    from oracle import oracle as O
+    O.build()
+    al = synth.alloy_potential(w["nsp"])
+    oal = O.Alloy(al)
+    n = args.ref_cells
+    x, _ = equilibrated(n, n, n, w["T"], w["seed"])
+    t = synth.random_types(len(x), w["fractions"], w["seed"] + 77)
+    L = synth.box(n, n, n)
+    for _ in range(max(1, args.warmup // 3)):
+        O.eam_alloy(oal, x, t, L, mode=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.eam_alloy(oal, x, t, L, mode=1)
+    el = time.perf_counter() - t0
+    val = len(x) * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"oracle sample: {n}x{n}x{n} cells ({len(x)} atoms) of the {args.workload} "
+                                   f"workload ({w['desc']}); one step = one alloy force evaluation", "cache": "cpu"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} alloy force evaluations of a {n}^3-cell box"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = init_dist()
     if rank != 0:
@@ -305,6 +341,8 @@ def run_reference(args):
     w = WORKLOADS[args.workload]
     if w.get("adjoint"):
         return run_reference_adjoint(args, ws)
+    if w.get("nsp"):
+        return run_reference_alloy(args, ws)
     from oracle import oracle as O
     O.build()
     pot = synth.potential()
@@ -459,6 +497,11 @@ def run_gpu(args):
 
     w = WORKLOADS[args.workload]
     pot = synth.potential()
+    alloy = types = None
+    if w.get("nsp"):
+        alloy = synth.alloy_potential(w["nsp"])
+        pot = alloy.species(0)  # grids of the alloy tables
+        args.no_cpu = True      # the oracle's MD loop is single-type
     batched = w.get("nrep") is not None
     if batched:
         reps, dims, x, v = batch_inputs(w)
@@ -469,6 +512,8 @@ def run_gpu(args):
         n = w["n"]
         natoms = 2 * n ** 3
         x, v, d = make_inputs(w, rank)
+        if alloy is not None:
+            types = synth.random_types(natoms, w["fractions"], w["seed"] + 77 + 1000 * rank)
 
     def fresh(prec):
         if batched:
@@ -481,6 +526,8 @@ def run_gpu(args):
             return s
         s = misa.Sim(pot, n, precision=prec, dt_max=1.0, dx_max=w["dx_max"], reassign_period=w["reassign"],
                      tile=args.tile)
+        if alloy is not None:
+            s.set_species(alloy, types)
         s.set_state(x, v)
         s.retune()  # tile shapes for the equilibrated crystal, not the perfect one
         s.insert_pka(-1, w["pka_eV"], d)
@@ -529,14 +576,15 @@ def run_gpu(args):
     step_s = el_ms / 1e3 / args.steps
     sha = kernel_source_sha()
     l1 = None
-    if NCU_WAVEFRONTS["source_sha"] == sha:
+    if NCU_WAVEFRONTS["source_sha"] == sha and alloy is None:
         # one L1 data-pipe wavefront per SM per clock at the sampled SM clock
         clk_hz = (clocks.get("sm_mhz") or 2070.0) * 1e6
         pipe = 152 * clk_hz
         l1 = {k: {"lsu_wavefronts_per_site": NCU_WAVEFRONTS[k][0], "tex_wavefronts_per_site": NCU_WAVEFRONTS[k][1],
                   "lsu_frac": NCU_WAVEFRONTS[k][0] * natoms / (t * pipe)}
               for k, t in (("density", t_dens), ("force", t_force))}
-    roofline = {"bound": "alu", "kernel": "k_force_p (force pass)", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+    kname = "k_force_p (force pass)" if alloy is None else "k_alloy_force (alloy force pass; flops counted as for one type)"
+    roofline = {"bound": "alu", "kernel": kname, "achieved": ach, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "peak_note": "FP32 FMA issue peak: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, not measured)",
                 "algorithmic_flops_per_site": FLOPS_FORCE_SITE,
@@ -559,6 +607,8 @@ def run_gpu(args):
     if not args.no_e2e:
         s = misa.Sim(pot, n, precision="fp32", dt_max=1.0, dx_max=w["dx_max"], reassign_period=w["reassign"],
                      tile=args.tile)
+        if alloy is not None:
+            s.set_species(alloy, types)
         x_host = torch.from_numpy(x).pin_memory()
         v0 = v.copy()
         pka = synth.pka_atom(n, n, n)
