@@ -159,7 +159,7 @@ WORKLOADS = {
     "c5": dict(n=16, nrep=16, seed=5, sigma=0.02, adjoint=True,
                desc="16 thermal snapshots of 16x16x16 cells (8,192 atoms each, 300-1500 K), targets from knots "
                     "scaled by 1 + N(0, 0.02^2); one step = loss + gradient w.r.t. 3 x 5000 knots, FP32 pair "
-                    "arithmetic, FP64 bins"),
+                    "arithmetic and bins, FP64 reduction"),
 }
 
 

@@ -247,8 +247,8 @@ int misa_set_species(misa_sim *s, int n_species, const double *f_knots, const do
  *   loss = sum_r [ (1/(3 N_r)) sum_i |F_i - Fref_i|^2 + ((E_r - Eref_r)/N_r)^2 ]
  * (Eq. eam_base for E, Eq. eam_force_ij for F).  grad (3 n_knots doubles,
  * host or device; may be NULL) receives d loss / d knot in the order f knots,
- * phi knots, F knots.  Pair arithmetic in the handle's precision,
- * accumulation in FP64 (per-CTA shared-memory bins, one ordered reduction).
+ * phi knots, F knots.  Pair arithmetic and the per-CTA shared-memory bins
+ * in the handle's precision, one ordered FP64 reduction over CTAs.
  * Synchronises. */
 int misa_loss_grad(misa_sim *s, const double *Fref, const double *Eref, double *loss, double *grad);
 

@@ -14,8 +14,10 @@
 //   F knots:   sum over atoms of          c_e w_k(rho_i) - dw_k(rho_i) Dl_i
 // where D = d r_ij / d eps along lambda and Dl_i = sum_j f'(r_ij) D.
 // Kernels: lambda (+ force-loss sums), Dl gather, gradient scatter into
-// per-CTA FP64 bins in shared memory, one ordered reduction over CTAs.
-// Pair arithmetic in the precision T of the handle, accumulation in FP64.
+// per-CTA bins in shared memory (in the handle's precision: FP32 bins take
+// native shared-memory atomics and half the space; their rounding, ~1e-6 of
+// a bin, is far below the FP32 gradient's own error), one ordered FP64
+// reduction over CTAs.  Pair arithmetic in the precision T of the handle.
 #pragma once
 
 #include "misa_md.cuh"
@@ -360,7 +362,7 @@ __global__ void k_adj_dl(AdjArgs<T> a)
 template <typename T>
 struct GradFn {
     const AdjArgs<T> &a;
-    double *bins;
+    T *bins;
     T lix, liy, liz;
     T ce, Fpi, Fppi, dli;
     __device__ __forceinline__ void operator()(const AdjPair<T> &P)
@@ -377,8 +379,8 @@ struct GradFn {
             if (k < 0 || k >= a.n) continue;
             const T gphi = (T)0.5 * ce * w[q] - (T)0.5 * dw[q] * D;
             const T gf = ce * Fpi * w[q] - (Fppi * dli * w[q] + Fpi * dw[q] * D);
-            if (gf != (T)0) atomicAdd(&bins[k], (double)gf);
-            if (gphi != (T)0) atomicAdd(&bins[a.n + k], (double)gphi);
+            if (gf != (T)0) atomicAdd(&bins[k], gf);
+            if (gphi != (T)0) atomicAdd(&bins[a.n + k], gphi);
         }
     }
 };
@@ -396,7 +398,7 @@ __device__ __forceinline__ T embed_dd(const AdjArgs<T> &a, T rho)
 }
 
 template <typename T>
-__device__ __forceinline__ void embed_bins(const AdjArgs<T> &a, double *bins, T rho, T ce, T dli)
+__device__ __forceinline__ void embed_bins(const AdjArgs<T> &a, T *bins, T rho, T ce, T dli)
 {
     T w[6], dw[6];
     int sg;
@@ -414,22 +416,23 @@ __device__ __forceinline__ void embed_bins(const AdjArgs<T> &a, double *bins, T 
         const int k = sg - 2 + q;
         if (k < 0 || k >= a.n) continue;
         const T g = ce * (w[q] + dw[q] * ex) - dw[q] * dli;
-        if (g != (T)0) atomicAdd(&bins[2 * a.n + k], (double)g);
+        if (g != (T)0) atomicAdd(&bins[2 * a.n + k], g);
     }
 }
 
-// gradient scatter: grid (blocks, replica); each CTA zeroes its 3n FP64 bins
-// in shared memory, scatters its atoms' pair terms with shared-memory
-// atomics, then writes the bins to partial[cta][3n]
+// gradient scatter: grid (blocks, replica); each CTA zeroes its 3n bins in
+// shared memory, scatters its atoms' pair terms with shared-memory atomics,
+// then writes the bins to partial[cta][3n] (FP64)
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_grad(AdjArgs<T> a, double *partial)
 {
-    extern __shared__ double bins[];
+    extern __shared__ __align__(16) unsigned char bin_smem[];
+    T *bins = reinterpret_cast<T *>(bin_smem);
     const int r = blockIdx.y;
     const RepDesc rd = a.reps[r];
     const int nra = a.sc[r].n_ra;
     const int nb = 3 * a.n;
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) bins[k] = 0.0;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) bins[k] = (T)0;
     __syncthreads();
     const double Nr = (double)rd.ns;
     const T ce = (T)(2.0 * (a.Etot[r] - a.Eref[r]) / (Nr * Nr));
@@ -450,7 +453,7 @@ __global__ void __launch_bounds__(256) k_adj_grad(AdjArgs<T> a, double *partial)
     }
     __syncthreads();
     double *out = partial + ((size_t)r * gridDim.x + blockIdx.x) * nb;
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) out[k] = bins[k];
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) out[k] = (double)bins[k];
 }
 
 // grad[k] = sum over CTAs of partial[cta][k], in CTA order

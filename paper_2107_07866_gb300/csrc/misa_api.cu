@@ -1144,9 +1144,9 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
         s->adj_fref = (double *)dalloc(s, sizeof(double) * 3 * s->ns);
         if (!s->dl || !s->ra_dl || !s->adj_partial || !s->adj_grad || !s->adj_eref || !s->adj_fref)
             return fail(s, MISA_EOOM, "adjoint work arrays");
-        CK(cudaFuncSetAttribute(k_adj_grad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * 3 * n)));
+        CK(cudaFuncSetAttribute(k_adj_grad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(T) * 3 * n)));
     }
-    if ((size_t)3 * n * sizeof(double) > 227u * 1024u) return fail(s, MISA_EINVAL, "too many knots for the gradient bins");
+    if ((size_t)3 * n * sizeof(T) > 227u * 1024u) return fail(s, MISA_EINVAL, "too many knots for the gradient bins");
     // forward: rho, F', E_i, forces of the current positions
     int rc = launch_forces<T>(s, 0, true);
     if (rc) return rc;
@@ -1195,7 +1195,7 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
     k_adj_lambda<T><<<dim3(nb, s->nrep), 256, 0, s->st>>>(a, s->partial);
     k_sum_stage2<<<s->nrep, 1024, 0, s->st>>>(s->partial, nb, s->red_out + s->nrep);  // sum |F - Fref|^2
     k_adj_dl<T><<<site_grid(s), 256, 0, s->st>>>(a);
-    k_adj_grad<T><<<dim3(s->adj_cta, s->nrep), 256, sizeof(double) * 3 * n, s->st>>>(a, s->adj_partial);
+    k_adj_grad<T><<<dim3(s->adj_cta, s->nrep), 256, sizeof(T) * 3 * n, s->st>>>(a, s->adj_partial);
     k_adj_reduce<<<(3 * n + 255) / 256, 256, 0, s->st>>>(s->adj_partial, s->adj_cta * s->nrep, 3 * n, s->adj_grad);
     s->launches += 8;
     CK(cudaGetLastError());
