@@ -27,6 +27,14 @@ namespace misa {
 // the bcc lattice vectors for runtime-indexed device loops
 static __constant__ LVecTable c_lvec = kLVec;
 
+// |n| S = xint + xfrac for every |n|^2 <= kMaxN2 (S: knot index per lattice
+// unit), split on the host in FP64 so that the FP32 pair geometry needs no
+// FP64 arithmetic
+struct SplitN2 {
+    float nrm, xfrac;
+    int xint, pad;
+};
+
 template <typename T>
 struct AdjArgs {
     const RepDesc *reps;
@@ -54,6 +62,7 @@ struct AdjArgs {
     int nvec;                        // offsets within rc + 2 skin (prefix of kLVec)
     const int *tile_flag;            // null: every site scans the run-away list
     int tx, ty, tz;
+    SplitN2 split[kMaxN2 + 1];
 };
 
 // one pair seen from atom i: |r| in lattice units, unit vector i -> j, the
@@ -97,6 +106,13 @@ __device__ __forceinline__ bool adj_pair(const A &a, int nx, int ny, int nz, T d
         const double fl = floor(x);
         P.seg = (int)fl;
         P.t = (T)(x - fl);
+    } else if constexpr (sizeof(T) == 4) {
+        const SplitN2 sp = a.split[n2];
+        const T dr = q / (r + (T)sp.nrm);
+        const T x = (T)sp.xfrac + dr * a.S;
+        const T fl = floor(x);
+        P.seg = sp.xint + (int)fl;
+        P.t = x - fl;
     } else {
         const double nn = sqrt((double)n2);
         const double x0 = nn * (double)a.S;

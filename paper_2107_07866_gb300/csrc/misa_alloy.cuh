@@ -48,6 +48,7 @@ struct AlloyArgs {
     int kick, energy, nvec;
     const int *tile_flag;
     int tx, ty, tz;
+    SplitN2 split[kMaxN2 + 1];
 };
 
 __device__ __forceinline__ int alloy_pair(int a, int b, int nsp)

@@ -20,6 +20,15 @@ using namespace misa;
 
 namespace {
 
+// |n| S split into integer and fraction for every |n|^2 (see SplitN2)
+void fill_split(SplitN2 *sp, double S)
+{
+    for (int n2 = 0; n2 <= kMaxN2; ++n2) {
+        const double x0 = std::sqrt((double)n2) * S, xi = std::floor(x0);
+        sp[n2] = SplitN2{(float)std::sqrt((double)n2), (float)(x0 - xi), (int)xi, 0};
+    }
+}
+
 // Self-test of the integer-pipe conversions against the hardware ones on
 // generated bit patterns: [0] double -> float, [1] float -> double.  A
 // subnormal hardware result is matched by a zero of the same sign.
@@ -601,6 +610,7 @@ AlloyArgs<T> alloy_args(misa_sim *s, int kick, bool energy)
     a.tile_flag = s->tile_flag;
     const TileShape &ts = kTiles[s->tile];
     a.tx = ts.tx; a.ty = ts.ty; a.tz = ts.tz;
+    fill_split(a.split, half / hr);
     return a;
 }
 
@@ -1177,6 +1187,7 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
     a.hr = (T)(s->p.rc / (n - 1));
     a.hrho = (T)(s->p.rho_max / (n - 1));
     a.S = (T)(half / (s->p.rc / (n - 1)));
+    fill_split(a.split, half / (s->p.rc / (n - 1)));
     a.rho_max = (T)s->p.rho_max;
     const double rcl = s->p.rc / half;
     a.rc2 = (T)(rcl * rcl);
