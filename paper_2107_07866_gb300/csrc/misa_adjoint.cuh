@@ -181,11 +181,19 @@ __device__ __forceinline__ void visit_site(const A &a, const RepDesc &rd, int nr
     }
 }
 
-// Visits every neighbour of run-away j (pooled slot g): array sites in a
-// 7-cell window around its home site, then the other run-aways.
+// One warp per run-away: j runs over the warps of the grid (warp-uniform).
+#define MISA_RA_WARP_LOOP(nra, j)                                                                       \
+    for (int j = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); j < (nra);                        \
+         j += (int)((gridDim.x * blockDim.x) >> 5))
+
+// Visits the neighbours of run-away j (pooled slot g): array sites in a
+// 7-cell window around its home site, then the other run-aways.  The
+// candidates are dealt out over the 32 lanes of a warp (lane takes every
+// 32nd); the caller sums the lanes' partial results with warp_sum (FP64).
 template <typename T, typename A, typename Fn>
 __device__ __forceinline__ void visit_ra(const A &a, const RepDesc &rd, int nra, int jl, Fn &fn)
 {
+    const int lane = threadIdx.x & 31;
     const int g = rd.ra_base + jl;
     int X, Y, Z;
     site_lat(a.ra_home[g], rd.nx, rd.ny, X, Y, Z);
@@ -193,7 +201,7 @@ __device__ __forceinline__ void visit_ra(const A &a, const RepDesc &rd, int nra,
     const int hcx = X >> 1, hcy = (Y - hp) >> 1, hcz = (Z - hp) >> 1;
     const T ujx = a.ra_ux[g], ujy = a.ra_uy[g], ujz = a.ra_uz[g];
     const int wx = rd.nx < 7 ? rd.nx : 7, wy = rd.ny < 7 ? rd.ny : 7, wz = rd.nz < 7 ? rd.nz : 7;
-    for (int c = 0; c < wx * wy * wz * 2; ++c) {
+    for (int c = lane; c < wx * wy * wz * 2; c += 32) {
         const int qq = c & 1, rr = c >> 1;
         const int ox = rr % wx, oy = (rr / wx) % wy, oz = rr / (wx * wy);
         const int cx = hcx - 3 + ox, cy = hcy - 3 + oy, cz = hcz - 3 + oz;
@@ -205,7 +213,7 @@ __device__ __forceinline__ void visit_ra(const A &a, const RepDesc &rd, int nra,
             fn(P);
     }
     const int Lx = 2 * rd.nx, Ly = 2 * rd.ny, Lz = 2 * rd.nz;
-    for (int k = 0; k < nra; ++k) {
+    for (int k = lane; k < nra; k += 32) {
         if (k == jl) continue;
         const int gk = rd.ra_base + k;
         int Xk, Yk, Zk;
@@ -338,7 +346,7 @@ template <typename T>
 struct DlFn {
     const AdjArgs<T> &a;
     T lix, liy, liz;
-    double acc;
+    Acc<T> acc;
     __device__ __forceinline__ void operator()(const AdjPair<T> &P)
     {
         if (P.floor_hit) return;  // direction undefined: no derivative
@@ -348,7 +356,7 @@ struct DlFn {
         const Vec4<T> c = a.tab_d0[P.seg];
         const T dfr = (c.x * t + c.y) * t + c.z;
         const T D = P.ex * (ljx - lix) + P.ey * (ljy - liy) + P.ez * (ljz - liz);
-        acc += (double)(dfr * D);
+        acc.add(dfr * D);
     }
 };
 
@@ -361,15 +369,16 @@ __global__ void k_adj_dl(AdjArgs<T> a)
     MISA_SITE_LOOP(rd, ls) {
         const long long s = rd.site_base + ls;
         if (a.sid[s] < 0) continue;
-        DlFn<T> fn{a, a.lam_x[s], a.lam_y[s], a.lam_z[s], 0.0};
+        DlFn<T> fn{a, a.lam_x[s], a.lam_y[s], a.lam_z[s], Acc<T>()};
         visit_site<T>(a, rd, nra, ls, fn);
-        a.dl[s] = (T)fn.acc;
+        a.dl[s] = fn.acc.value();
     }
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nra; j += gridDim.x * blockDim.x) {
+    MISA_RA_WARP_LOOP(nra, j) {
         const int g = rd.ra_base + j;
-        DlFn<T> fn{a, a.ra_lx[g], a.ra_ly[g], a.ra_lz[g], 0.0};
+        DlFn<T> fn{a, a.ra_lx[g], a.ra_ly[g], a.ra_lz[g], Acc<T>()};
         visit_ra<T>(a, rd, nra, j, fn);
-        a.ra_dl[g] = (T)fn.acc;
+        const double dl = warp_sum((double)fn.acc.value());
+        if ((threadIdx.x & 31) == 0) a.ra_dl[g] = (T)dl;
     }
 }
 
@@ -460,12 +469,12 @@ __global__ void __launch_bounds__(256) k_adj_grad(AdjArgs<T> a, double *partial)
         visit_site<T>(a, rd, nra, ls, fn);
         embed_bins<T>(a, bins, rho, ce, a.dl[s]);
     }
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nra; j += gridDim.x * blockDim.x) {
+    MISA_RA_WARP_LOOP(nra, j) {
         const int g = rd.ra_base + j;
         const T rho = a.ra_rho[g];
         GradFn<T> fn{a, bins, a.ra_lx[g], a.ra_ly[g], a.ra_lz[g], ce, a.ra_fp[g], embed_dd<T>(a, rho), a.ra_dl[g]};
         visit_ra<T>(a, rd, nra, j, fn);
-        embed_bins<T>(a, bins, rho, ce, a.ra_dl[g]);
+        if ((threadIdx.x & 31) == 0) embed_bins<T>(a, bins, rho, ce, a.ra_dl[g]);
     }
     __syncthreads();
     double *out = partial + ((size_t)r * gridDim.x + blockIdx.x) * nb;

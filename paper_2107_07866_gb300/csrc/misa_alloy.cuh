@@ -9,8 +9,8 @@
 //
 // One thread per site (and one per run-away), neighbours through the offset
 // index and the run-away list (run-aways only from tiles flagged as within
-// reach of one), spline tables read from global memory through L1, sums in
-// FP64.  These passes serve correctness for any number of types; the
+// reach of one), spline tables read from global memory through L1, sums
+// compensated in FP32 (plain in FP64) as in the single-type passes.  These passes serve correctness for any number of types; the
 // single-type path keeps the packed FP32 gathers.
 #pragma once
 
@@ -79,10 +79,10 @@ __device__ __forceinline__ T quad_at(const Vec4<T> &c, T t)
 template <typename T>
 struct AlloyRhoFn {
     const AlloyArgs<T> &a;
-    double rho;
+    Acc<T> rho;
     __device__ __forceinline__ void operator()(const AdjPair<T> &P)
     {
-        rho += (double)cubic_at<T>(a.tfv[(size_t)type_of(a, P) * a.n + P.seg], P.t);
+        rho.add(cubic_at<T>(a.tfv[(size_t)type_of(a, P) * a.n + P.seg], P.t));
     }
 };
 
@@ -92,7 +92,8 @@ struct AlloyForceFn {
     const AlloyArgs<T> &a;
     int ti;
     T Fpi;
-    double fx, fy, fz, ephi;
+    Acc<T> fx, fy, fz;
+    double ephi;
     __device__ __forceinline__ void operator()(const AdjPair<T> &P)
     {
         const int tj = type_of(a, P);
@@ -103,10 +104,10 @@ struct AlloyForceFn {
         const T dfi = quad_at<T>(a.tfd[(size_t)ti * a.n + sg], P.t);
         const T dph = quad_at<T>(a.tpd[(size_t)pr * a.n + sg], P.t);
         // Eq. eam_force_ij; the unit vector is zero below r_floor
-        const double s = (double)(Fpi * dfj + Fpj * dfi + dph);
-        fx += s * (double)P.ex;
-        fy += s * (double)P.ey;
-        fz += s * (double)P.ez;
+        const T s = Fpi * dfj + Fpj * dfi + dph;
+        fx.add(s * P.ex);
+        fy.add(s * P.ey);
+        fz.add(s * P.ez);
         if (a.energy) ephi += 0.5 * (double)cubic_at<T>(a.tpv[(size_t)pr * a.n + sg], P.t);
     }
 };
@@ -132,9 +133,9 @@ __global__ void k_alloy_density(AlloyArgs<T> a)
             a.fp[s] = 0;
             continue;
         }
-        AlloyRhoFn<T> fn{a, 0.0};
+        AlloyRhoFn<T> fn{a, Acc<T>()};
         visit_site<T>(a, rd, nra, ls, fn);
-        const T rho = (T)fn.rho;
+        const T rho = fn.rho.value();
         T dF;
         const T Fv = alloy_embed<T>(a, a.atype[id], rho, dF, st);
         a.fp[s] = dF;
@@ -154,16 +155,18 @@ __global__ void k_alloy_ra_density(AlloyArgs<T> a)
     const RepDesc rd = a.reps[r];
     const int nra = a.sc[r].n_ra;
     unsigned st = 0;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nra; j += gridDim.x * blockDim.x) {
+    MISA_RA_WARP_LOOP(nra, j) {
         const int g = rd.ra_base + j;
-        AlloyRhoFn<T> fn{a, 0.0};
+        AlloyRhoFn<T> fn{a, Acc<T>()};
         visit_ra<T>(a, rd, nra, j, fn);
-        const T rho = (T)fn.rho;
-        T dF;
-        const T Fv = alloy_embed<T>(a, a.atype[a.ra_id[g]], rho, dF, st);
-        a.ra_fp[g] = dF;
-        a.ra_rho[g] = rho;
-        if (a.energy) a.ra_e[g] = (double)Fv;
+        const T rho = (T)warp_sum((double)fn.rho.value());
+        if ((threadIdx.x & 31) == 0) {
+            T dF;
+            const T Fv = alloy_embed<T>(a, a.atype[a.ra_id[g]], rho, dF, st);
+            a.ra_fp[g] = dF;
+            a.ra_rho[g] = rho;
+            if (a.energy) a.ra_e[g] = (double)Fv;
+        }
     }
     if (st) atomicOr(&a.sc[0].status, st);
 }
@@ -174,7 +177,8 @@ __device__ __forceinline__ void alloy_finish(const AlloyArgs<T> &a, double hdt, 
                                              T *az, double *vx, double *vy, double *vz, long long i,
                                              unsigned long long &vmax2, unsigned &st)
 {
-    const T gx = (T)(fn.fx * a.acc_conv), gy = (T)(fn.fy * a.acc_conv), gz = (T)(fn.fz * a.acc_conv);
+    const T gx = (T)((double)fn.fx.value() * a.acc_conv), gy = (T)((double)fn.fy.value() * a.acc_conv),
+            gz = (T)((double)fn.fz.value() * a.acc_conv);
     ax[i] = gx;
     ay[i] = gy;
     az[i] = gz;
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(256) k_alloy_force(AlloyArgs<T> a)
         const long long s = rd.site_base + ls;
         const int id = a.sid[s];
         if (id < 0) continue;
-        AlloyForceFn<T> fn{a, a.atype[id], a.fp[s], 0.0, 0.0, 0.0, 0.0};
+        AlloyForceFn<T> fn{a, a.atype[id], a.fp[s], Acc<T>(), Acc<T>(), Acc<T>(), 0.0};
         visit_site<T>(a, rd, nra, ls, fn);
         alloy_finish<T>(a, hdt, fn, a.ax, a.ay, a.az, a.vx, a.vy, a.vz, s, vmax2, st);
         if (a.energy) a.e_out[s] += fn.ephi;
@@ -224,12 +228,18 @@ __global__ void __launch_bounds__(256) k_alloy_ra_force(AlloyArgs<T> a)
     const double hdt = 0.5 * a.sc[r].dt;
     unsigned st = 0;
     unsigned long long vmax2 = 0;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nra; j += gridDim.x * blockDim.x) {
+    MISA_RA_WARP_LOOP(nra, j) {
         const int g = rd.ra_base + j;
-        AlloyForceFn<T> fn{a, a.atype[a.ra_id[g]], a.ra_fp[g], 0.0, 0.0, 0.0, 0.0};
+        AlloyForceFn<T> fn{a, a.atype[a.ra_id[g]], a.ra_fp[g], Acc<T>(), Acc<T>(), Acc<T>(), 0.0};
         visit_ra<T>(a, rd, nra, j, fn);
-        alloy_finish<T>(a, hdt, fn, a.ra_ax, a.ra_ay, a.ra_az, a.ra_vx, a.ra_vy, a.ra_vz, g, vmax2, st);
-        if (a.energy) a.ra_e[g] += fn.ephi;
+        fn.fx = Acc<T>{(T)warp_sum((double)fn.fx.value()), (T)0};
+        fn.fy = Acc<T>{(T)warp_sum((double)fn.fy.value()), (T)0};
+        fn.fz = Acc<T>{(T)warp_sum((double)fn.fz.value()), (T)0};
+        fn.ephi = warp_sum(fn.ephi);
+        if ((threadIdx.x & 31) == 0) {
+            alloy_finish<T>(a, hdt, fn, a.ra_ax, a.ra_ay, a.ra_az, a.ra_vx, a.ra_vy, a.ra_vz, g, vmax2, st);
+            if (a.energy) a.ra_e[g] += fn.ephi;
+        }
     }
     if (a.kick) flush_vmax<256>(__longlong_as_double((long long)vmax2), red, a.sc + r);
     if (st) atomicOr(&a.sc[0].status, st);
