@@ -152,6 +152,29 @@ const char *misa_last_error(const misa_sim *s);
  * the run-away list.  Then the forces of the new positions are evaluated. */
 int misa_set_state(misa_sim *s, const double *x, const double *v, int64_t n);
 
+/* Starts copying positions x and, if v is not NULL, velocities v (3 natoms
+ * each, host or device memory, layout as in misa_set_state) into staging
+ * buffers of the handle (48 B per atom of device memory, allocated on first
+ * use) on a copy stream of its own, and returns at once: the copy runs
+ * beside the steps already launched, so the next state streams in while
+ * the current one is simulated.  The new copy waits on the device for the
+ * previous staged state to have been read, and the call waits on the host
+ * for the previous staged copy to be complete.  x and v must stay valid and
+ * unchanged until this copy is complete: once the next misa_stage_state has
+ * returned, the handle's stream has passed misa_set_state_staged, or
+ * misa_destroy has returned (from pageable host memory the copy completes
+ * before the call returns).  A second call before misa_set_state_staged
+ * replaces the staged state.  MISA_EOOM if the staging buffers cannot be
+ * allocated. */
+int misa_stage_state(misa_sim *s, const double *x, const double *v, int64_t n);
+
+/* misa_set_state from the state staged by misa_stage_state: the handle's
+ * stream waits for the staged copy, then the atoms are hashed to their sites
+ * and the forces of the new positions are evaluated, exactly as in
+ * misa_set_state.  Velocities are set to zero if none were staged.
+ * MISA_EINVAL if nothing is staged. */
+int misa_set_state_staged(misa_sim *s);
+
 /* Replaces the velocities (3 natoms, A/fs). */
 int misa_set_velocities(misa_sim *s, const double *v, int64_t n);
 
@@ -256,13 +279,18 @@ int misa_loss_grad(misa_sim *s, const double *Fref, const double *Eref, double *
 int misa_tile_count(void);
 int misa_tile_shape(int index, int *tx, int *ty, int *tz);
 
-/* Self-test of the library's float <-> double conversions done with integer
- * operations (used by the FP64 integration kernels; no counterpart in the
- * paper) against the GPU's own conversions on n generated bit patterns.
- * mismatches[0] counts double -> float, mismatches[1] float -> double
- * disagreements (a subnormal result flushed to a signed zero is not one).
- * Runs on the current device, synchronises; MISA_EINVAL for n <= 0 or a
- * null pointer, MISA_ECUDA on a CUDA error. */
+/* Self-test of two shortcuts of the library that have no counterpart in the
+ * paper.  (1) The float <-> double conversions done with integer operations
+ * (used by the FP64 integration kernels), against the GPU's own conversions
+ * on n generated bit patterns: mismatches[0] counts double -> float,
+ * mismatches[1] float -> double disagreements (a subnormal result flushed to
+ * a signed zero is not one).  (2) The hash of Sec. 3 with the site decided
+ * in FP32 under a certifying margin (used when a state is set), against the
+ * all-FP64 hash on n generated positions (thermal, near floor and distance
+ * ties, exact ties, uniform): mismatches[2] counts positions whose site or
+ * displacement differs in any bit.  mismatches holds 3 values.  Runs on the
+ * current device, synchronises; MISA_EINVAL for n <= 0 or a null pointer,
+ * MISA_ECUDA on a CUDA error. */
 int misa_selftest(long long n, long long *mismatches);
 
 /* 1 if shape `index` (1-based) is built for `precision`, else 0.  The FP64

@@ -77,6 +77,52 @@ __global__ void k_selftest_conv(unsigned long long n, unsigned long long *bad)
     if (b1) atomicAdd(bad + 1, b1);
 }
 
+// nearest_site_fast against nearest_site (site and displacement bits) on
+// positions in half-lattice units: thermal, near floor and decision ties,
+// exact ties, uniform, and far outside the box.
+__global__ void k_selftest_site(unsigned long long n, unsigned long long *bad)
+{
+    unsigned long long b = 0;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long h = mix64(i), g = mix64(i ^ 0x9e3779b97f4a7c15ull);
+        const int nb = 2 + (int)(h % 600ull);
+        const double L = 2.0 * nb;
+        double P[3];
+        for (int d = 0; d < 3; ++d) {
+            const unsigned long long q = mix64(h + 31ull * d + 7ull);
+            const double k = (double)(q % (unsigned long long)(2 * nb));
+            const double v = (double)(q >> 11) * 0x1p-53;  // [0, 1)
+            switch ((i + (unsigned long long)d * (g & 1ull)) % 6ull) {
+            case 0:  // thermal
+                P[d] = k + (v - 0.5) * 0.4;
+                break;
+            case 1:  // a few ulps around an integer (floor ties)
+                P[d] = k + (double)((long long)(q >> 60) - 8) * 0x1p-52 * (k + 1.0);
+                break;
+            case 2:  // around a half-integer (distance ties between the sublattices)
+                P[d] = k + 0.5 + (double)((long long)(q >> 60) - 8) * 0x1p-40;
+                break;
+            case 3:  // exact half-integer
+                P[d] = k + 0.5;
+                break;
+            case 4:  // uniform in the box
+                P[d] = v * L;
+                break;
+            default:  // FP32-scale offsets from an integer
+                P[d] = k + (double)((long long)(q >> 58) - 32) * 0x1p-24 * (k + 2.0) * 0.05;
+            }
+        }
+        double ax, ay, az, bx, by, bz;
+        const long long sa = nearest_site(P[0], P[1], P[2], nb, nb, nb, ax, ay, az);
+        const long long sb = nearest_site_fast(P[0], P[1], P[2], nb, nb, nb, bx, by, bz);
+        if (sa != sb || __double_as_longlong(ax) != __double_as_longlong(bx) ||
+            __double_as_longlong(ay) != __double_as_longlong(by) || __double_as_longlong(az) != __double_as_longlong(bz))
+            ++b;
+    }
+    if (b) atomicAdd(bad, b);
+}
+
 constexpr double kAccUnit = 9.6485332123310018e-3;  // 1 eV/(A amu) in A/fs^2 (CODATA 2018)
 constexpr double kRfloor = 1e-4;                      // A
 
@@ -146,6 +192,13 @@ struct misa_sim {
     double *out_buf = nullptr;  // 3 natoms scratch for read-out / set_state
     int *aux_int = nullptr;     // natoms scratch
     double *aux_dbl = nullptr;  // 3 natoms scratch
+    // staged state (misa_stage_state): x, v copied on the handle's copy
+    // stream into buffers of their own, consumed by misa_set_state_staged
+    cudaStream_t cst = nullptr;
+    cudaEvent_t ev_stg = nullptr;       // the staged copies are complete
+    cudaEvent_t ev_stg_free = nullptr;  // the last staged state has been read
+    double *stg_x = nullptr, *stg_v = nullptr;
+    bool stg_pending = false, stg_has_v = false;
     long long ntile_cap = 0;    // tile_flag / tile_rep capacity (smallest tile shape)
     int ntiles = 0;
     size_t smem_density = 0, smem_force = 0;
@@ -885,30 +938,41 @@ int create_impl(misa_sim *s)
     return refresh<T>(s, true);
 }
 
+// Sets the state from device arrays xd (3 natoms) and vd (3 natoms or
+// null); xd may be out_buf (each atom's displacement from its nearest site
+// then overwrites its position in place).  done, if given, is recorded once
+// xd and vd have been read.
+template <typename T>
+int set_state_dev(misa_sim *s, const double *xd, const double *vd, cudaEvent_t done)
+{
+    const long long N = s->ns;
+    MdArgs<T> m = md_args<T>(s);
+    k_reset_list<T><<<rep_blocks(s), 128, 0, s->st>>>(m);
+    k_clear_sites<T><<<site_grid(s), 256, 0, s->st>>>(m);
+    k_state_claim<T><<<site_grid(s), 256, 0, s->st>>>(m, xd, s->aux_int, s->out_buf);
+    if (!vd) {
+        CK(cudaMemsetAsync(s->v[0], 0, sizeof(double) * N, s->st));
+        CK(cudaMemsetAsync(s->v[1], 0, sizeof(double) * N, s->st));
+        CK(cudaMemsetAsync(s->v[2], 0, sizeof(double) * N, s->st));
+    }
+    k_state_place<T><<<site_grid(s), 256, 0, s->st>>>(m, vd, s->aux_int, s->out_buf);
+    if (done) CK(cudaEventRecord(done, s->st));
+    k_ra_sort<T><<<s->nrep, 1024, sizeof(unsigned long long) * kSortMax, s->st>>>(m);
+    CK(cudaGetLastError());
+    return refresh<T>(s, true);
+}
+
 template <typename T>
 int set_state_impl(misa_sim *s, const double *x, const double *v)
 {
     const long long N = s->ns;
-    MdArgs<T> m = md_args<T>(s);
     CK(cudaMemcpyAsync(s->out_buf, x, sizeof(double) * 3 * N, cudaMemcpyDefault, s->st));
     const double *vd = nullptr;
     if (v) {
         CK(cudaMemcpyAsync(s->aux_dbl, v, sizeof(double) * 3 * N, cudaMemcpyDefault, s->st));
         vd = s->aux_dbl;
     }
-    k_reset_list<T><<<rep_blocks(s), 128, 0, s->st>>>(m);
-    k_clear_sites<T><<<site_grid(s), 256, 0, s->st>>>(m);
-    // each atom's displacement from its nearest site overwrites its position in place
-    k_state_claim<T><<<site_grid(s), 256, 0, s->st>>>(m, s->out_buf, s->aux_int, s->out_buf);
-    if (!v) {
-        CK(cudaMemsetAsync(s->v[0], 0, sizeof(double) * N, s->st));
-        CK(cudaMemsetAsync(s->v[1], 0, sizeof(double) * N, s->st));
-        CK(cudaMemsetAsync(s->v[2], 0, sizeof(double) * N, s->st));
-    }
-    k_state_place<T><<<site_grid(s), 256, 0, s->st>>>(m, vd, s->aux_int, s->out_buf);
-    k_ra_sort<T><<<s->nrep, 1024, sizeof(unsigned long long) * kSortMax, s->st>>>(m);
-    CK(cudaGetLastError());
-    return refresh<T>(s, true);
+    return set_state_dev<T>(s, s->out_buf, vd, nullptr);
 }
 
 // per-replica potential and kinetic energy (eV) into pe[r], ke[r]
@@ -1300,6 +1364,7 @@ void misa_destroy(misa_sim *s)
     if (!s) return;
     cudaStreamSynchronize(s->st);
     if (s->gst) cudaStreamSynchronize(s->gst);
+    if (s->cst) cudaStreamSynchronize(s->cst);
     if (s->graph) cudaGraphExecDestroy(s->graph);
     for (unsigned long long t : {s->tex_f, s->tex_d0, s->tex_d1})
         if (t) cudaDestroyTextureObject((cudaTextureObject_t)t);
@@ -1307,6 +1372,9 @@ void misa_destroy(misa_sim *s)
     if (s->ev_in) cudaEventDestroy(s->ev_in);
     if (s->ev_out) cudaEventDestroy(s->ev_out);
     if (s->gst) cudaStreamDestroy(s->gst);
+    if (s->ev_stg) cudaEventDestroy(s->ev_stg);
+    if (s->ev_stg_free) cudaEventDestroy(s->ev_stg_free);
+    if (s->cst) cudaStreamDestroy(s->cst);
     for (auto &a : s->allocs) {
         if (s->p.free) s->p.free(a.first, a.second, s->p.alloc_ctx);
         else cudaFree(a.first);
@@ -1336,6 +1404,47 @@ int misa_set_state(misa_sim *s, const double *x, const double *v, int64_t n)
     if (!s) return MISA_EINVAL;
     if (!x || n != s->ns) return fail(s, MISA_EINVAL, "set_state: x required, n must equal natoms");
     return s->prec == MISA_FP64 ? set_state_impl<double>(s, x, v) : set_state_impl<float>(s, x, v);
+}
+
+int misa_stage_state(misa_sim *s, const double *x, const double *v, int64_t n)
+{
+    if (!s) return MISA_EINVAL;
+    if (!x || n != s->ns) return fail(s, MISA_EINVAL, "stage_state: x required, n must equal natoms");
+    if (!s->cst) {
+        CK(cudaStreamCreateWithFlags(&s->cst, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&s->ev_stg, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&s->ev_stg_free, cudaEventDisableTiming));
+    }
+    if (!s->stg_x) {
+        s->stg_x = (double *)dalloc(s, sizeof(double) * 3 * s->ns);
+        if (!s->stg_x) return fail(s, MISA_EOOM, "stage_state: staging buffer");
+    }
+    if (v && !s->stg_v) {
+        s->stg_v = (double *)dalloc(s, sizeof(double) * 3 * s->ns);
+        if (!s->stg_v) return fail(s, MISA_EOOM, "stage_state: staging buffer");
+    }
+    // the previous staged copy is complete before this call returns (its
+    // host arrays may then be released); the new copies wait on the device
+    // until the previous staged state has been read
+    CK(cudaEventSynchronize(s->ev_stg));
+    CK(cudaStreamWaitEvent(s->cst, s->ev_stg_free, 0));
+    CK(cudaMemcpyAsync(s->stg_x, x, sizeof(double) * 3 * s->ns, cudaMemcpyDefault, s->cst));
+    if (v) CK(cudaMemcpyAsync(s->stg_v, v, sizeof(double) * 3 * s->ns, cudaMemcpyDefault, s->cst));
+    CK(cudaEventRecord(s->ev_stg, s->cst));
+    s->stg_pending = true;
+    s->stg_has_v = v != nullptr;
+    return MISA_OK;
+}
+
+int misa_set_state_staged(misa_sim *s)
+{
+    if (!s) return MISA_EINVAL;
+    if (!s->stg_pending) return fail(s, MISA_EINVAL, "set_state_staged: no state staged");
+    CK(cudaStreamWaitEvent(s->st, s->ev_stg, 0));
+    s->stg_pending = false;
+    const double *vd = s->stg_has_v ? s->stg_v : nullptr;
+    return s->prec == MISA_FP64 ? set_state_dev<double>(s, s->stg_x, vd, s->ev_stg_free)
+                                : set_state_dev<float>(s, s->stg_x, vd, s->ev_stg_free);
 }
 
 int misa_set_velocities(misa_sim *s, const double *v, int64_t n)
@@ -1684,11 +1793,12 @@ int misa_selftest(long long n, long long *mismatches)
 {
     if (n <= 0 || !mismatches) return MISA_EINVAL;
     unsigned long long *d = nullptr;
-    if (cudaMalloc(&d, 2 * sizeof(unsigned long long)) != cudaSuccess) return MISA_ECUDA;
-    unsigned long long h[2] = {0, 0};
+    unsigned long long h[3] = {0, 0, 0};
+    if (cudaMalloc(&d, sizeof(h)) != cudaSuccess) return MISA_ECUDA;
     cudaError_t e = cudaMemset(d, 0, sizeof(h));
     if (e == cudaSuccess) {
         k_selftest_conv<<<1024, 256>>>((unsigned long long)n, d);
+        k_selftest_site<<<1024, 256>>>((unsigned long long)n, d + 2);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
@@ -1696,6 +1806,7 @@ int misa_selftest(long long n, long long *mismatches)
     if (e != cudaSuccess) return MISA_ECUDA;
     mismatches[0] = (long long)h[0];
     mismatches[1] = (long long)h[1];
+    mismatches[2] = (long long)h[2];
     return MISA_OK;
 }
 

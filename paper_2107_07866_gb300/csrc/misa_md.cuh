@@ -99,6 +99,54 @@ __device__ __forceinline__ long long nearest_site(double Px, double Py, double P
     return ide;
 }
 
+// nearest_site with the site decided in FP32 wherever a margin certifies
+// that the FP64 arithmetic decides the same way, FP64 otherwise: the same
+// site and displacement, bit for bit, at a few FP64 operations per atom (FP64
+// runs at a small fraction of the FP32 rate on GB300).  Certified when (i)
+// the winning candidate's three floors are unambiguous (floor arguments
+// farther from an integer than the FP32 error of P/2, so both precisions
+// take the same integers) and (ii) the squared distances differ by more than
+// their FP32 error plus what an ambiguous floor of the losing candidate can
+// change (a coordinate of the loser then sits at distance 1 -+ 2 amb either
+// way).  Bounds in units of u = 2^-24 (max |P| + 2): |fP - P| <= u per
+// coordinate and |a - (P/2 + 1/2)| <= u, so a floor argument farther than
+// amb = 16 u from an integer floors alike in both precisions; a squared
+// distance carries <= 3 (8 u + 6 u) of FP32 rounding, and an ambiguous
+// losing coordinate (P within 34 u of the tie) changes it by <= 136 u, three
+// coordinates 408 u; the margin is 1024 u.
+__device__ __forceinline__ long long nearest_site_fast(double Px, double Py, double Pz, int nx, int ny, int nz,
+                                                       double &ux, double &uy, double &uz)
+{
+    const float f[3] = {d2f_bits(Px), d2f_bits(Py), d2f_bits(Pz)};
+    const float pm = fmaxf(fabsf(f[0]), fmaxf(fabsf(f[1]), fabsf(f[2]))) + 2.f;
+    const float amb = pm * 0x1p-20f;
+    float c[3], e[3], dc = 0.f, de = 0.f;
+    bool cok = true, eok = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float h = 0.5f * f[d];
+        const float a = h + 0.5f;
+        const float fa = floorf(a), fb = floorf(h);
+        cok = cok && (a - fa >= amb) && (fa + 1.f - a >= amb);
+        eok = eok && (h - fb >= amb) && (fb + 1.f - h >= amb);
+        c[d] = 2.f * fa;
+        e[d] = fmaf(2.f, fb, 1.f);
+        const float dcd = f[d] - c[d], ded = f[d] - e[d];
+        dc = fmaf(dcd, dcd, dc);
+        de = fmaf(ded, ded, de);
+    }
+    const bool corner = dc < de;
+    if (fabsf(dc - de) > pm * 0x1p-14f && (corner ? cok : eok)) {
+        const int X = (int)(corner ? c[0] : e[0]), Y = (int)(corner ? c[1] : e[1]), Z = (int)(corner ? c[2] : e[2]);
+        ux = Px - (double)X;
+        uy = Py - (double)Y;
+        uz = Pz - (double)Z;
+        const int cx = wrapi(X >> 1, nx), cy = wrapi(Y >> 1, ny), cz = wrapi(Z >> 1, nz);
+        return (((long long)cz * ny + cy) * nx + cx) * 2 + (X & 1);
+    }
+    return nearest_site(Px, Py, Pz, nx, ny, nz, ux, uy, uz);
+}
+
 // grid-stride loop over the replica-local sites of replica rd
 #define MISA_SITE_LOOP(rd, s)                                                                     \
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < (rd).ns;            \
@@ -616,14 +664,22 @@ __global__ void k_state_claim(MdArgs<T> m, const double *x, int *home, double *r
 {
     const RepDesc rd = m.reps[blockIdx.y];
     const double L[3] = {rd.nx * 2.0 * m.half, rd.ny * 2.0 * m.half, rd.nz * 2.0 * m.half};
+    // p - L floor(p / L) leaves p in [0, L (1 - 2^-50)) unchanged (the
+    // quotient stays below 1): only other coordinates take the division.
+    // Non-negative doubles order as their bit patterns (integer compares).
+    long long Lw[3];
+    for (int d = 0; d < 3; ++d) Lw[d] = __double_as_longlong(L[d] * (1.0 - 0x1p-50));
     MISA_SITE_LOOP(rd, li) {
         const long long i = rd.site_base + li;
-        double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
-        px -= L[0] * floor(px / L[0]);
-        py -= L[1] * floor(py / L[1]);
-        pz -= L[2] * floor(pz / L[2]);
+        double p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const long long b = __double_as_longlong(p[d]);
+            if (b < 0 || b >= Lw[d]) p[d] -= L[d] * floor(p[d] / L[d]);
+        }
         double rx, ry, rz;
-        long long h = nearest_site(px * m.inv_half, py * m.inv_half, pz * m.inv_half, rd.nx, rd.ny, rd.nz, rx, ry, rz);
+        long long h = nearest_site_fast(p[0] * m.inv_half, p[1] * m.inv_half, p[2] * m.inv_half, rd.nx, rd.ny, rd.nz,
+                                        rx, ry, rz);
         home[i] = (int)h;
         rel[3 * i] = rx; rel[3 * i + 1] = ry; rel[3 * i + 2] = rz;
         if (rx * rx + ry * ry + rz * rz <= m.skin2) atomicMin(&m.claim[rd.site_base + h], (int)i);

@@ -85,6 +85,8 @@ def lib():
         L.misa_last_error.restype = C.c_char_p
         L.misa_set_state.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
         L.misa_set_velocities.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+        L.misa_stage_state.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
+        L.misa_set_state_staged.argtypes = [C.c_void_p]
         L.misa_insert_pka.argtypes = [C.c_void_p, C.c_int64, C.c_double, _D]
         L.misa_step.argtypes = [C.c_void_p, C.c_int]
         L.misa_get_energies.argtypes = [C.c_void_p, _D, _D, C.c_void_p]
@@ -254,6 +256,19 @@ class Sim:
         v = _f64(v)
         self._check(lib().misa_set_state(self.h, _ptr(x), _ptr(v), self.natoms))
 
+    def stage_state(self, x, v=None):
+        """Starts copying x (and v) into the handle's staging buffers on its
+        copy stream; set_state_staged() applies them.  The arrays stay
+        referenced here until the next stage_state call, which waits for
+        this copy to be complete (they must not change meanwhile)."""
+        x = _f64(x)
+        v = _f64(v)
+        self._check(lib().misa_stage_state(self.h, _ptr(x), _ptr(v), self.natoms))
+        self._staged = (x, v)
+
+    def set_state_staged(self):
+        self._check(lib().misa_set_state_staged(self.h))
+
     def set_velocities(self, v):
         v = _f64(v)
         self._check(lib().misa_set_velocities(self.h, _ptr(v), self.natoms))
@@ -410,13 +425,15 @@ def tile_shapes():
 
 
 def selftest(n=1 << 22):
-    """Mismatch counts (double -> float, float -> double) of the library's
-    integer-pipe conversions against the GPU's own on n bit patterns."""
-    out = (C.c_longlong * 2)()
+    """Mismatch counts of the library's shortcuts against their exact
+    counterparts: (double -> float, float -> double) integer-pipe conversions
+    against the GPU's own on n bit patterns, and the FP32-decided site hash
+    against the FP64 one on n positions."""
+    out = (C.c_longlong * 3)()
     code = lib().misa_selftest(n, out)
     if code != MISA_OK:
         raise MisaError(code, "misa_selftest failed")
-    return int(out[0]), int(out[1])
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def tile_indices(precision):
