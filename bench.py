@@ -583,7 +583,7 @@ def run_gpu(args):
         l1 = {k: {"lsu_wavefronts_per_site": NCU_WAVEFRONTS[k][0], "tex_wavefronts_per_site": NCU_WAVEFRONTS[k][1],
                   "lsu_frac": NCU_WAVEFRONTS[k][0] * natoms / (t * pipe)}
               for k, t in (("density", t_dens), ("force", t_force))}
-    kname = "k_force_p (force pass)" if alloy is None else "k_alloy_force (alloy force pass; flops counted as for one type)"
+    kname = "k_force_p (force pass)" if alloy is None else "k_force_pa (alloy force pass; flops counted as for one type)"
     roofline = {"bound": "alu", "kernel": kname, "achieved": ach, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "peak_note": "FP32 FMA issue peak: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, not measured)",

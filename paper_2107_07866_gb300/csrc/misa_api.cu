@@ -15,6 +15,7 @@
 #include "misa_adjoint.cuh"
 #include "misa_packed.cuh"
 #include "misa_alloy.cuh"
+#include "misa_alloy_packed.cuh"
 
 using namespace misa;
 
@@ -202,6 +203,7 @@ struct misa_sim {
     long long ntile_cap = 0;    // tile_flag / tile_rep capacity (smallest tile shape)
     int ntiles = 0;
     size_t smem_density = 0, smem_force = 0;
+    size_t smem_alloy_d = 0, smem_alloy_f = 0;  // FP32 alloy passes (density, force tile shape)
     bool dens_db = false;  // FP32 density pass double-buffers its tiles
     long long launches = 0;
     // phase timing
@@ -219,6 +221,7 @@ struct misa_sim {
     double *al_knots = nullptr;
     void *al_fv = nullptr, *al_fd = nullptr, *al_Fv = nullptr, *al_pv = nullptr, *al_pd = nullptr;
     int al_cap = 0;  // species the alloy arrays were allocated for
+    unsigned long long tex_afv = 0, tex_afd = 0, tex_apd = 0;  // FP32: texture objects over the alloy tables
     // captured step graph
     bool use_graph = true;
     cudaGraphExec_t graph = nullptr;
@@ -415,6 +418,18 @@ void fill_gather(misa_sim *s, GatherArgs<T> &g, bool force_pass = false)
     g.tex_d0 = s->tex_d0;
     g.tex_d1 = s->tex_d1;
     g.mask_ok = s->bmask && kLVec.shell_begin[sh.nshell] - kSparseK0 <= 64 ? 1 : 0;
+    g.sid = s->sid;
+    if (s->nsp > 1) {
+        g.atype = s->atype;
+        g.ra_id = s->ra_id;
+        g.nsp = s->nsp;
+        g.nknot = n;
+        g.tex_afv = s->tex_afv;
+        g.tex_afd = s->tex_afd;
+        g.tex_apd = s->tex_apd;
+        g.al_tFv = (const Vec4<T> *)s->al_Fv;
+        g.al_tpv = (const Vec4<T> *)s->al_pv;
+    }
 }
 
 // FP32: the table window plus one zero segment, the folded tile (two
@@ -462,6 +477,9 @@ struct TileKernels {
             CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
             CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
             CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
+            const int ad = (int)s->smem_alloy_d;
+            CK(cudaFuncSetAttribute(k_density_pa<TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ad));
+            CK(cudaFuncSetAttribute(k_density_pa<TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ad));
             return MISA_OK;
         } else {
             CK(cudaFuncSetAttribute(k_density<T, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_density));
@@ -477,6 +495,9 @@ struct TileKernels {
             const int f = (int)s->smem_force;
             CK(cudaFuncSetAttribute(k_force_p<TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, f));
             CK(cudaFuncSetAttribute(k_force_p<TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, f));
+            const int af = (int)s->smem_alloy_f;
+            CK(cudaFuncSetAttribute(k_force_pa<TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, af));
+            CK(cudaFuncSetAttribute(k_force_pa<TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, af));
             return MISA_OK;
         } else {
             CK(cudaFuncSetAttribute(k_force<T, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_force));
@@ -490,6 +511,11 @@ struct TileKernels {
             return;
         } else if constexpr (kF32) {
             constexpr int nt = TX * TY * TZ;
+            if (s->nsp > 1) {  // alloys
+                if (energy) k_density_pa<TX, TY, TZ, true><<<grid, nt, s->smem_alloy_d, s->st>>>(g);
+                else k_density_pa<TX, TY, TZ, false><<<grid, nt, s->smem_alloy_d, s->st>>>(g);
+                return;
+            }
             const size_t b = s->smem_density;
             if (s->dens_db) {
                 if (energy) k_density_p<TX, TY, TZ, true, true><<<grid, nt, b, s->st>>>(g);
@@ -510,6 +536,11 @@ struct TileKernels {
             return;
         } else if constexpr (kF32) {
             constexpr int nt = TX * TY * TZ;
+            if (s->nsp > 1) {  // alloys
+                if (energy) k_force_pa<TX, TY, TZ, true><<<grid, nt, s->smem_alloy_f, s->st>>>(g);
+                else k_force_pa<TX, TY, TZ, false><<<grid, nt, s->smem_alloy_f, s->st>>>(g);
+                return;
+            }
             if (energy) k_force_p<TX, TY, TZ, true><<<grid, nt, s->smem_force, s->st>>>(g);
             else k_force_p<TX, TY, TZ, false><<<grid, nt, s->smem_force, s->st>>>(g);
         } else {
@@ -577,6 +608,13 @@ int configure(misa_sim *s, int td, int tf)
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     s->smem_density = smem_density_bytes<T>(s, (size_t)optin);
     s->smem_force = smem_force_bytes<T>(s);
+    if (sizeof(T) == 4) {
+        const TileShape &a = kTiles[td], &b = kTiles[tf];
+        s->smem_alloy_d = alloy_smem_bytes(a.tx, a.ty, a.tz);
+        s->smem_alloy_f = alloy_smem_bytes(b.tx, b.ty, b.tz);
+        if (s->smem_alloy_d > (size_t)optin || s->smem_alloy_f > (size_t)optin)
+            return fail(s, MISA_EINVAL, "tile shape exceeds the shared memory of a block (alloy passes)");
+    }
     if (s->smem_density > (size_t)optin || s->smem_force > (size_t)optin)
         return fail(s, MISA_EINVAL, "tile shape and table window exceed the shared memory of a block");
     int arc = MISA_OK;
@@ -667,19 +705,29 @@ AlloyArgs<T> alloy_args(misa_sim *s, int kick, bool energy)
     return a;
 }
 
-// the four alloy passes (density, run-away density, force + kick, run-away force + kick)
+// the four alloy passes (density, run-away density, force + kick, run-away
+// force + kick): FP32 the packed tile gathers with species (array atoms),
+// FP64 one thread per site
 template <typename T>
 int launch_alloy(misa_sim *s, int kick, bool energy, bool step_marks)
 {
     int rc = mark_tiles<T>(s);
     if (rc) return rc;
     const AlloyArgs<T> a = alloy_args<T>(s, kick, energy);
+    GatherArgs<T> gd, gf;
+    if constexpr (sizeof(T) == 4) {
+        fill_gather<T>(s, gd, false);
+        fill_gather<T>(s, gf, true);
+        gd.kick = gf.kick = kick;
+    }
     if (step_marks) mark(s);
-    k_alloy_density<T><<<site_grid(s), 256, 0, s->st>>>(a);
+    if constexpr (sizeof(T) == 4) launch_density<T>(s, gd, energy);
+    else k_alloy_density<T><<<site_grid(s), 256, 0, s->st>>>(a);
     if (step_marks) mark(s);
     k_alloy_ra_density<T><<<dim3(16, s->nrep), 256, 0, s->st>>>(a);
     if (step_marks) mark(s);
-    k_alloy_force<T><<<site_grid(s), 256, 0, s->st>>>(a);
+    if constexpr (sizeof(T) == 4) launch_force<T>(s, gf, energy);
+    else k_alloy_force<T><<<site_grid(s), 256, 0, s->st>>>(a);
     if (step_marks) mark(s);
     k_alloy_ra_force<T><<<dim3(16, s->nrep), 256, 0, s->st>>>(a);
     if (step_marks) mark(s);
@@ -1183,6 +1231,27 @@ int set_species_impl(misa_sim *s, int nsp, const double *f, const double *F, con
                                               (Vec4<T> *)s->al_fd, (Vec4<T> *)s->al_Fv, (Vec4<T> *)s->al_pv,
                                               (Vec4<T> *)s->al_pd);
     CK(cudaGetLastError());
+    if (sizeof(T) == 4) {  // texture objects over the tables of the FP32 alloy gathers
+        for (unsigned long long *t : {&s->tex_afv, &s->tex_afd, &s->tex_apd}) {
+            if (*t) cudaDestroyTextureObject((cudaTextureObject_t)*t);
+            *t = 0;
+        }
+        void *ptrs[3] = {s->al_fv, s->al_fd, s->al_pd};
+        const size_t cnt[3] = {(size_t)nsp * n, (size_t)nsp * n, (size_t)npair * n};
+        unsigned long long *out[3] = {&s->tex_afv, &s->tex_afd, &s->tex_apd};
+        for (int q = 0; q < 3; ++q) {
+            cudaResourceDesc rd{};
+            rd.resType = cudaResourceTypeLinear;
+            rd.res.linear.devPtr = ptrs[q];
+            rd.res.linear.desc = cudaCreateChannelDesc<float4>();
+            rd.res.linear.sizeInBytes = sizeof(float4) * cnt[q];
+            cudaTextureDesc td{};
+            td.readMode = cudaReadModeElementType;
+            cudaTextureObject_t to = 0;
+            CK(cudaCreateTextureObject(&to, &rd, &td, nullptr));
+            *out[q] = to;
+        }
+    }
     CK(cudaStreamSynchronize(s->st));  // ht is a host temporary
     s->nsp = nsp;
     if (s->graph) {
@@ -1366,7 +1435,7 @@ void misa_destroy(misa_sim *s)
     if (s->gst) cudaStreamSynchronize(s->gst);
     if (s->cst) cudaStreamSynchronize(s->cst);
     if (s->graph) cudaGraphExecDestroy(s->graph);
-    for (unsigned long long t : {s->tex_f, s->tex_d0, s->tex_d1})
+    for (unsigned long long t : {s->tex_f, s->tex_d0, s->tex_d1, s->tex_afv, s->tex_afd, s->tex_apd})
         if (t) cudaDestroyTextureObject((cudaTextureObject_t)t);
     for (auto e : s->ev_pool) cudaEventDestroy(e);
     if (s->ev_in) cudaEventDestroy(s->ev_in);

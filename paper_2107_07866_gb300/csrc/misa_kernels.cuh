@@ -207,6 +207,16 @@ struct GatherArgs {
     unsigned long long *bmask;
     int mask_ok;
     unsigned long long tex_f, tex_d0, tex_d1;  // texture objects over tab_f, tab_d0, tab_d1
+    // alloys (several species; null / zero for one): species per atom id,
+    // run-away atom ids, and the per-species tables (nknot entries each, the
+    // last all zero) through texture objects: density value and derivative
+    // per species, pair derivative per unordered species pair; embedding and
+    // pair values (energy evaluations) from global memory
+    const int8_t *atype;
+    const int *sid, *ra_id;  // atom id per site (-1: vacant), per run-away
+    int nsp, nknot;
+    unsigned long long tex_afv, tex_afd, tex_apd;
+    const Vec4<T> *al_tFv, *al_tpv;
     // neighbour offset index for this tile shape: per parity, per lattice
     // vector: (shared-memory slot displacement as int bits, 2 n_x, 2 n_y, 2 n_z)
     float4 off[2][kNVec];
@@ -351,7 +361,8 @@ __device__ __forceinline__ int stage_runaways(const GatherArgs<T> &a, const Tile
             const int room = kRaChunk - cnt;
             const int rank = __popc(bal & ((1u << lane) - 1u));
             if (take && rank < room) {
-                sRh[cnt + rank] = make_int4(hx, hy, hz, 0);
+                // w: the run-away's species (alloys)
+                sRh[cnt + rank] = make_int4(hx, hy, hz, a.atype ? (int)a.atype[a.ra_id[rd.ra_base + j]] : 0);
                 Vec4<T> u;
                 u.x = a.ra_ux[rd.ra_base + j];
                 u.y = a.ra_uy[rd.ra_base + j];

@@ -58,6 +58,31 @@ def test_alloy_parity(misa, oracle, prec, case):
         assert st["n_runaway"] > 0
 
 
+@pytest.mark.parametrize("case", ["cascade_3sp_10x9x12", "cascade_2sp_6x6x6"])
+def test_alloy_tile_shapes_bitwise_equal(misa, oracle, case):
+    # FP32 alloy gathers: per-site sums do not depend on the tile shape (tiles
+    # wider than the box included), and every shape meets the oracle bound
+    nsp, dims, mk, frac = CASES[case]
+    al = synth.alloy_potential(nsp)
+    x = mk()
+    t = synth.random_types(len(x), frac, 32)
+    rho_o, _, e_o, f_o = oracle.eam_alloy(oracle.Alloy(al), x, t, synth.box(*dims), mode=1)
+    ref = None
+    for k in misa.tile_indices("fp32"):
+        with misa.Sim(al.species(0), *dims, precision="fp32", tile=k) as s:
+            s.set_species(al, t)
+            s.set_state(x)
+            got = (s.forces(), s.density(), s.energies(per_atom=True)[2])
+        assert nerr(got[0], f_o) < TOL["fp32"], (k, nerr(got[0], f_o))
+        assert nerr(got[1], rho_o) < TOL["fp32"], (k, nerr(got[1], rho_o))
+        assert nerr(got[2], e_o) < TOL["fp32"], (k, nerr(got[2], e_o))
+        if ref is None:
+            ref = got
+        else:
+            for a_, b_ in zip(ref, got):
+                np.testing.assert_array_equal(a_, b_)
+
+
 def test_identical_species_match_single_type(misa):
     pot = synth.potential()
     nsp = 3
