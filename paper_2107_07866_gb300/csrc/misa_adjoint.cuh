@@ -52,6 +52,7 @@ struct AdjArgs {
     int n;                          // knots per table
     T S;                            // knot index per lattice unit of r
     T hr, hrho, rho_max, rc2, rfloor2, half;
+    T inv_hr, inv_hrho;  // 1/hr, 1/hrho
     double acc_conv;
     const double *Fref;   // 3 per atom id
     const double *Eref;   // per replica
@@ -234,11 +235,30 @@ __device__ __forceinline__ void visit_ra(const A &a, const RepDesc &rd, int nra,
 // local Hermite spline (slopes: 4th-order central differences inside,
 // 2nd order at the two outer knots of each end).
 template <typename T>
-__device__ __forceinline__ void basis6(int s, T t, int n, T h, T w[6], T dw[6])
+__device__ __forceinline__ void basis6(int s, T t, int n, T inv_h, T w[6], T dw[6])
 {
     const T t2 = t * t, t3 = t2 * t;
     const T c0 = 2 * t3 - 3 * t2 + 1, c1 = t3 - 2 * t2 + t, c2 = -2 * t3 + 3 * t2, c3 = t3 - t2;
-    const T d0 = (6 * t2 - 6 * t) / h, d1 = (3 * t2 - 4 * t + 1) / h, d2 = (-6 * t2 + 6 * t) / h, d3 = (3 * t2 - 2 * t) / h;
+    const T d0 = (6 * t2 - 6 * t) * inv_h, d1 = (3 * t2 - 4 * t + 1) * inv_h, d2 = (-6 * t2 + 6 * t) * inv_h,
+            d3 = (3 * t2 - 2 * t) * inv_h;
+    if (s >= 2 && s <= n - 4) {
+        // both knot slopes from the 4th-order stencil (y_{k-2} - 8 y_{k-1} +
+        // 8 y_{k+1} - y_{k+2}) / 12: the weights of knots s-2 .. s+3 in closed form
+        const T a = (T)(1.0 / 12.0), b = (T)(8.0 / 12.0);
+        w[0] = c1 * a;
+        w[1] = c3 * a - c1 * b;
+        w[2] = c0 - c3 * b;
+        w[3] = c2 + c1 * b;
+        w[4] = c3 * b - c1 * a;
+        w[5] = -(c3 * a);
+        dw[0] = d1 * a;
+        dw[1] = d3 * a - d1 * b;
+        dw[2] = d0 - d3 * b;
+        dw[3] = d2 + d1 * b;
+        dw[4] = d3 * b - d1 * a;
+        dw[5] = -(d3 * a);
+        return;
+    }
     for (int q = 0; q < 6; ++q) {
         w[q] = 0;
         dw[q] = 0;
@@ -389,23 +409,24 @@ struct GradFn {
     const AdjArgs<T> &a;
     T *bins;
     T lix, liy, liz;
-    T ce, Fpi, Fppi, dli;
+    T cw;   // ce F'_i - F''_i D_lrho_i: weight of the knot values in the f scatter
+    T Fpi;  // F'_i: weight of the knot-derivative term
+    T hce;  // ce / 2
     __device__ __forceinline__ void operator()(const AdjPair<T> &P)
     {
         T ljx, ljy, ljz;
         LamOf<T>{a}.get(P, ljx, ljy, ljz);
         // unit vector is zero below r_floor: no derivative term there
         const T D = P.ex * (ljx - lix) + P.ey * (ljy - liy) + P.ez * (ljz - liz);
+        const T fD = Fpi * D, hD = (T)0.5 * D;
         const int sg = P.seg;
         T w[6], dw[6];
-        basis6<T>(sg, P.t, a.n, a.hr, w, dw);
+        basis6<T>(sg, P.t, a.n, a.inv_hr, w, dw);
         for (int q = 0; q < 6; ++q) {
             const int k = sg - 2 + q;
             if (k < 0 || k >= a.n) continue;
-            const T gphi = (T)0.5 * ce * w[q] - (T)0.5 * dw[q] * D;
-            const T gf = ce * Fpi * w[q] - (Fppi * dli * w[q] + Fpi * dw[q] * D);
-            if (gf != (T)0) atomicAdd(&bins[k], gf);
-            if (gphi != (T)0) atomicAdd(&bins[a.n + k], gphi);
+            atomicAdd(&bins[k], cw * w[q] - fD * dw[q]);          // f knots
+            atomicAdd(&bins[a.n + k], hce * w[q] - hD * dw[q]);  // phi knots
         }
     }
 };
@@ -417,9 +438,9 @@ __device__ __forceinline__ T embed_dd(const AdjArgs<T> &a, T rho)
     if (rho > a.rho_max) return 0;
     if (rho < 0) rho = 0;
     T t;
-    const int sg = seg_t<T>(rho, (T)1 / a.hrho, a.n, t);
+    const int sg = seg_t<T>(rho, a.inv_hrho, a.n, t);
     const Vec4<T> c = a.tab_F[sg];
-    return (6 * c.x * t + 2 * c.y) / (a.hrho * a.hrho);
+    return (6 * c.x * t + 2 * c.y) * (a.inv_hrho * a.inv_hrho);
 }
 
 template <typename T>
@@ -430,12 +451,12 @@ __device__ __forceinline__ void embed_bins(const AdjArgs<T> &a, T *bins, T rho, 
     T ex = 0;
     if (rho > a.rho_max) {
         sg = a.n - 2;
-        basis6<T>(sg, (T)1, a.n, a.hrho, w, dw);
+        basis6<T>(sg, (T)1, a.n, a.inv_hrho, w, dw);
         ex = rho - a.rho_max;
     } else {
         T t;
-        sg = seg_t<T>(rho < 0 ? (T)0 : rho, (T)1 / a.hrho, a.n, t);
-        basis6<T>(sg, t, a.n, a.hrho, w, dw);
+        sg = seg_t<T>(rho < 0 ? (T)0 : rho, a.inv_hrho, a.n, t);
+        basis6<T>(sg, t, a.n, a.inv_hrho, w, dw);
     }
     for (int q = 0; q < 6; ++q) {
         const int k = sg - 2 + q;
@@ -465,14 +486,18 @@ __global__ void __launch_bounds__(256) k_adj_grad(AdjArgs<T> a, double *partial)
         const long long s = rd.site_base + ls;
         if (a.sid[s] < 0) continue;
         const T rho = a.rho[s];
-        GradFn<T> fn{a, bins, a.lam_x[s], a.lam_y[s], a.lam_z[s], ce, a.fp[s], embed_dd<T>(a, rho), a.dl[s]};
+        const T Fpi = a.fp[s];
+        GradFn<T> fn{a, bins, a.lam_x[s], a.lam_y[s], a.lam_z[s], ce * Fpi - embed_dd<T>(a, rho) * a.dl[s], Fpi,
+                     (T)0.5 * ce};
         visit_site<T>(a, rd, nra, ls, fn);
         embed_bins<T>(a, bins, rho, ce, a.dl[s]);
     }
     MISA_RA_WARP_LOOP(nra, j) {
         const int g = rd.ra_base + j;
         const T rho = a.ra_rho[g];
-        GradFn<T> fn{a, bins, a.ra_lx[g], a.ra_ly[g], a.ra_lz[g], ce, a.ra_fp[g], embed_dd<T>(a, rho), a.ra_dl[g]};
+        const T Fpi = a.ra_fp[g];
+        GradFn<T> fn{a, bins, a.ra_lx[g], a.ra_ly[g], a.ra_lz[g], ce * Fpi - embed_dd<T>(a, rho) * a.ra_dl[g], Fpi,
+                     (T)0.5 * ce};
         visit_ra<T>(a, rd, nra, j, fn);
         if ((threadIdx.x & 31) == 0) embed_bins<T>(a, bins, rho, ce, a.ra_dl[g]);
     }

@@ -1319,6 +1319,8 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
     a.half = (T)half;
     a.hr = (T)(s->p.rc / (n - 1));
     a.hrho = (T)(s->p.rho_max / (n - 1));
+    a.inv_hr = (T)((n - 1) / s->p.rc);
+    a.inv_hrho = (T)((n - 1) / s->p.rho_max);
     a.S = (T)(half / (s->p.rc / (n - 1)));
     fill_split(a.split, half / (s->p.rc / (n - 1)));
     a.rho_max = (T)s->p.rho_max;

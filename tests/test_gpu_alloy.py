@@ -153,3 +153,28 @@ def test_alloy_replicas_equal_single_boxes(misa, prec):
         s.step(20)
         fb = s.forces()
     np.testing.assert_array_equal(fb, np.concatenate(single))
+
+
+def test_alloy_parity_at_benchmark_size(misa, oracle):
+    # the alloy benchmark's box (100^3 cells, three species 70/20/10 %) in the
+    # launch configuration it times: tiles retuned on the state, steps replayed
+    # from a captured graph, adaptive dt, knock-on atom, hash update every 10
+    # steps; then every atom against the oracle on the GPU's own positions
+    n, nsp = 100, 3
+    natoms = 2 * n ** 3
+    al = synth.alloy_potential(nsp)
+    t = synth.random_types(natoms, (0.7, 0.2, 0.1), 80)
+    with misa.Sim(al.species(0), n, precision="fp32", dt_max=1.0, dx_max=0.02, reassign_period=10) as s:
+        s.set_species(al, t)
+        s.set_velocities(synth.maxwell_velocities(natoms, 600.0, synth.MASS_FE, 3))
+        s.retune()
+        s.insert_pka(-1, 5000.0, synth.random_direction(20))
+        s.step(30)
+        st = s.stats()
+        assert st["status"] == 0 and st["step"] == 30
+        x, f, rho = s.positions(), s.forces(), s.density()
+        _, _, e = s.energies(per_atom=True)
+    rho_o, _, e_o, f_o = oracle.eam_alloy(oracle.Alloy(al), x, t, synth.box(n, n, n), mode=1)
+    assert nerr(f, f_o) < TOL["fp32"], nerr(f, f_o)
+    assert nerr(rho, rho_o) < TOL["fp32"], nerr(rho, rho_o)
+    assert nerr(e, e_o) < TOL["fp32"], nerr(e, e_o)
