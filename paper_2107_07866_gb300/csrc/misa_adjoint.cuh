@@ -53,7 +53,7 @@ struct AdjArgs {
     T S;                            // knot index per lattice unit of r
     T hr, hrho, rho_max, rc2, rfloor2, half;
     T inv_hr, inv_hrho;  // 1/hr, 1/hrho
-    double acc_conv;
+    double acc_conv, inv_acc_conv;
     const double *Fref;   // 3 per atom id
     const double *Eref;   // per replica
     const double *Etot;   // per replica
@@ -316,9 +316,9 @@ __global__ void k_adj_lambda(AdjArgs<T> a, double *partial)
         const long long s = rd.site_base + ls;
         const int id = a.sid[s];
         if (id < 0) continue;
-        const double fx = (double)a.ax[s] / a.acc_conv - a.Fref[3LL * id];
-        const double fy = (double)a.ay[s] / a.acc_conv - a.Fref[3LL * id + 1];
-        const double fz = (double)a.az[s] / a.acc_conv - a.Fref[3LL * id + 2];
+        const double fx = (double)a.ax[s] * a.inv_acc_conv - a.Fref[3LL * id];
+        const double fy = (double)a.ay[s] * a.inv_acc_conv - a.Fref[3LL * id + 1];
+        const double fz = (double)a.az[s] * a.inv_acc_conv - a.Fref[3LL * id + 2];
         acc += fx * fx + fy * fy + fz * fz;
         a.lam_x[s] = (T)(c * fx);
         a.lam_y[s] = (T)(c * fy);
@@ -328,9 +328,9 @@ __global__ void k_adj_lambda(AdjArgs<T> a, double *partial)
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nra; j += gridDim.x * blockDim.x) {
         const int g = rd.ra_base + j;
         const int id = a.ra_id[g];
-        const double fx = (double)a.ra_ax[g] / a.acc_conv - a.Fref[3LL * id];
-        const double fy = (double)a.ra_ay[g] / a.acc_conv - a.Fref[3LL * id + 1];
-        const double fz = (double)a.ra_az[g] / a.acc_conv - a.Fref[3LL * id + 2];
+        const double fx = (double)a.ra_ax[g] * a.inv_acc_conv - a.Fref[3LL * id];
+        const double fy = (double)a.ra_ay[g] * a.inv_acc_conv - a.Fref[3LL * id + 1];
+        const double fz = (double)a.ra_az[g] * a.inv_acc_conv - a.Fref[3LL * id + 2];
         acc += fx * fx + fy * fy + fz * fz;
         a.ra_lx[g] = (T)(c * fx);
         a.ra_ly[g] = (T)(c * fy);

@@ -279,6 +279,15 @@ dim3 site_grid(const misa_sim *s)
     return dim3(gx < 4 ? 4 : gx, s->nrep);
 }
 dim3 list_grid(const misa_sim *s) { return dim3(8, s->nrep); }
+// blocks per replica of the two-stage sums (k_sum_stage1, k_adj_lambda): one
+// 256-thread block per 256 sites of the largest replica, at most 512
+int red_blocks(const misa_sim *s)
+{
+    long long mx = 1;
+    for (const RepDesc &rd : s->reps) mx = rd.ns > mx ? rd.ns : mx;
+    const long long b = (mx + 255) / 256;
+    return (int)(b > 512 ? 512 : b);
+}
 int rep_blocks(const misa_sim *s) { return (s->nrep + 127) / 128; }
 
 template <typename T>
@@ -1030,7 +1039,7 @@ int reduce_energy(misa_sim *s, double *pe, double *ke, double *per_atom)
     int rc = launch_forces<T>(s, 0, true);
     if (rc) return rc;
     MdArgs<T> m = md_args<T>(s);
-    const int nb = 512;
+    const int nb = red_blocks(s);
     k_sum_stage1<T><<<dim3(nb, s->nrep), 256, 0, s->st>>>(m, 0, s->partial);
     k_sum_stage2<<<s->nrep, 1024, 0, s->st>>>(s->partial, nb, s->red_out);
     k_sum_stage1<T><<<dim3(nb, s->nrep), 256, 0, s->st>>>(m, 1, s->partial);
@@ -1294,7 +1303,7 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
     int rc = launch_forces<T>(s, 0, true);
     if (rc) return rc;
     MdArgs<T> m = md_args<T>(s);
-    const int nb = 512;
+    const int nb = red_blocks(s);
     k_sum_stage1<T><<<dim3(nb, s->nrep), 256, 0, s->st>>>(m, 0, s->partial);
     k_sum_stage2<<<s->nrep, 1024, 0, s->st>>>(s->partial, nb, s->red_out);  // E_r
     CK(cudaMemcpyAsync(s->adj_fref, Fref, sizeof(double) * 3 * s->ns, cudaMemcpyDefault, s->st));
@@ -1328,6 +1337,7 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
     a.rc2 = (T)(rcl * rcl);
     a.rfloor2 = (T)((kRfloor / half) * (kRfloor / half));
     a.acc_conv = kAccUnit / s->p.mass;
+    a.inv_acc_conv = s->p.mass / kAccUnit;
     a.Fref = s->adj_fref;
     a.Eref = s->adj_eref;
     a.Etot = s->red_out;
