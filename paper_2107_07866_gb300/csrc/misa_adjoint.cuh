@@ -21,6 +21,7 @@
 #pragma once
 
 #include "misa_md.cuh"
+#include "misa_packed.cuh"
 
 namespace misa {
 
@@ -96,9 +97,17 @@ __device__ __forceinline__ bool adj_pair(const A &a, int nx, int ny, int nz, T d
     P.ra = ra;
     P.j = j;
     P.floor_hit = r2 < a.rfloor2;
-    const T r = sqrt(P.floor_hit ? a.rfloor2 : r2);
+    T r, inv;
+    if constexpr (sizeof(T) == 4) {  // approximate reciprocal square root, as in the tile gathers
+        const T rr2 = P.floor_hit ? a.rfloor2 : r2;
+        const T rs = rsqrt_approx(rr2);
+        r = rr2 * rs;
+        inv = P.floor_hit ? (T)0 : rs;
+    } else {
+        r = sqrt(P.floor_hit ? a.rfloor2 : r2);
+        inv = P.floor_hit ? (T)0 : (T)1 / r;
+    }
     P.r = r;
-    const T inv = P.floor_hit ? (T)0 : (T)1 / r;
     P.ex = rx * inv;
     P.ey = ry * inv;
     P.ez = rz * inv;
@@ -109,7 +118,7 @@ __device__ __forceinline__ bool adj_pair(const A &a, int nx, int ny, int nz, T d
         P.t = (T)(x - fl);
     } else if constexpr (sizeof(T) == 4) {
         const SplitN2 sp = a.split[n2];
-        const T dr = q / (r + (T)sp.nrm);
+        const T dr = q * rcp_approx(r + (T)sp.nrm);
         const T x = (T)sp.xfrac + dr * a.S;
         const T fl = floor(x);
         P.seg = sp.xint + (int)fl;
@@ -506,13 +515,23 @@ __global__ void __launch_bounds__(256) k_adj_grad(AdjArgs<T> a, double *partial)
     for (int k = threadIdx.x; k < nb; k += blockDim.x) out[k] = (double)bins[k];
 }
 
-// grad[k] = sum over CTAs of partial[cta][k], in CTA order
-__global__ void k_adj_reduce(const double *partial, int ncta, int nb, double *grad)
+// grad[k] = sum over CTAs of partial[cta][k] in a fixed order: a block of
+// 32 x 8 threads takes 32 knots; thread row y sums CTAs y, y + 8, ... in
+// order, then the 8 row sums are added in row order.  Launch with blockDim
+// (32, 8) and ceil(nb / 32) blocks.
+__global__ void __launch_bounds__(256) k_adj_reduce(const double *partial, int ncta, int nb, double *grad)
 {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int c = 0; c < ncta; ++c) s += partial[(size_t)c * nb + k];
-        grad[k] = s;
+    __shared__ double rows[8][33];
+    const int k = blockIdx.x * 32 + threadIdx.x;
+    double s = 0.0;
+    if (k < nb)
+        for (int c = threadIdx.y; c < ncta; c += 8) s += partial[(size_t)c * nb + k];
+    rows[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && k < nb) {
+        double t = rows[0][threadIdx.x];
+        for (int y = 1; y < 8; ++y) t += rows[y][threadIdx.x];
+        grad[k] = t;
     }
 }
 

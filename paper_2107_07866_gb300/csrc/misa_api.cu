@@ -1352,7 +1352,7 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
     k_sum_stage2<<<s->nrep, 1024, 0, s->st>>>(s->partial, nb, s->red_out + s->nrep);  // sum |F - Fref|^2
     k_adj_dl<T><<<site_grid(s), 256, 0, s->st>>>(a);
     k_adj_grad<T><<<dim3(s->adj_cta, s->nrep), 256, sizeof(T) * 3 * n, s->st>>>(a, s->adj_partial);
-    k_adj_reduce<<<(3 * n + 255) / 256, 256, 0, s->st>>>(s->adj_partial, s->adj_cta * s->nrep, 3 * n, s->adj_grad);
+    k_adj_reduce<<<(3 * n + 31) / 32, dim3(32, 8), 0, s->st>>>(s->adj_partial, s->adj_cta * s->nrep, 3 * n, s->adj_grad);
     s->launches += 8;
     CK(cudaGetLastError());
     if (grad) CK(cudaMemcpyAsync(grad, s->adj_grad, sizeof(double) * 3 * n, cudaMemcpyDefault, s->st));
