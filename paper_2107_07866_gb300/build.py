@@ -14,8 +14,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libmisa.so")
 SOURCES = [os.path.join(PKG, "csrc", "misa_api.cu")]
-DEPS = SOURCES + [os.path.join(PKG, "csrc", f) for f in ("misa_common.cuh", "misa_kernels.cuh", "misa_md.cuh", "misa_adjoint.cuh", "misa_packed.cuh", "misa_alloy.cuh")] + [
-    os.path.join(ROOT, "include", "misa.h")]
+DEPS = SOURCES + sorted(os.path.join(PKG, "csrc", f) for f in os.listdir(os.path.join(PKG, "csrc"))
+                        if f.endswith(".cuh")) + [os.path.join(ROOT, "include", "misa.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
