@@ -520,7 +520,8 @@ def run_gpu(args):
             s = misa.Sim(pot, replicas=dims, precision=prec, dt_max=1.0, dx_max=w["dx_max"],
                          reassign_period=w["reassign"], tile=args.tile)
             s.set_state(x, v)
-            s.retune()
+            if not args.tile:
+                s.retune()
             for r, rep in enumerate(reps):
                 s.insert_pka_replica(r, rep.pka_energy, rep.pka_dir)
             return s
@@ -529,7 +530,8 @@ def run_gpu(args):
         if alloy is not None:
             s.set_species(alloy, types)
         s.set_state(x, v)
-        s.retune()  # tile shapes for the equilibrated crystal, not the perfect one
+        if not args.tile:
+            s.retune()  # tile shapes for the equilibrated crystal, not the perfect one
         s.insert_pka(-1, w["pka_eV"], d)
         return s
 
@@ -686,7 +688,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="misa", choices=["misa", "reference"])
     ap.add_argument("--workload", default="c3", choices=list(WORKLOADS))
-    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=0,
+                    help="pin both gathers to tile shape K (1-based, see misa.tile_shapes()); 0: autotune")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-iters", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
