@@ -7,10 +7,16 @@
 // both sites of every folded slot (species a | species b << 8; a vacant site
 // reads species 0 and adds zero through its displacement sentinel).  The
 // tables of an alloy (a density and an embedding function per species, a
-// pair function per unordered species pair) do not fit beside the staged
-// tile in shared memory, so every spline read goes through the texture path,
-// indexed by species and segment over the whole table; the last segment of
-// every table is all zero and indices at or beyond rc clamp to it.
+// pair function per unordered species pair) do not all fit beside the
+// staged tile in shared memory.  The density pass keeps the window
+// (segments an array-array pair can reach) of the dominant species m's
+// density function there, as the single-type pass does, and reads the other
+// species' through the texture path; the force pass reads every table
+// through the texture path (its texture latency is not hidden better by a
+// window: a warp whose lanes mix species waits for the fetch either way).
+// Texture reads are indexed by species and segment over the whole table;
+// the last segment of every table is all zero and indices at or beyond rc
+// clamp to it (the window's zero entry is the same segment).
 //
 // Density: rho_i = sum_j rho_{t_j}(r_ij), F'_i from the embedding function
 // of t_i.  Force: [F'_i rho'_{t_j}(r) + F'_j rho'_{t_i}(r) + phi'_{t_i t_j}(r)]
@@ -29,11 +35,19 @@ __host__ __device__ inline size_t ptype_smem_bytes(int tx, int ty, int tz)
     return (sizeof(unsigned short) * 2 * plane + 255) & ~(size_t)255;
 }
 
-// shared memory of the alloy passes: no table window; the staged tile, the
-// run-away chunk, the replica cache, then the species plane
-__host__ __device__ inline size_t alloy_smem_bytes(int tx, int ty, int tz)
+// shared-memory bytes of the dominant species' density window (nwin
+// segments plus the zero one); the force pass holds no window
+__host__ __device__ inline size_t alloy_window_bytes(bool force, int nwin)
 {
-    return ((packed_smem_bytes(0, tx, ty, tz, 1) + 255) & ~(size_t)255) + ptype_smem_bytes(tx, ty, tz);
+    return force ? 0 : sizeof(float4) * (size_t)(nwin + 1);
+}
+
+// shared memory of the alloy passes: the window, the replica cache, the
+// staged tile, the run-away chunk, then the species plane
+__host__ __device__ inline size_t alloy_smem_bytes(bool force, int nwin, int tx, int ty, int tz)
+{
+    return ((packed_smem_bytes(alloy_window_bytes(force, nwin), tx, ty, tz, 1) + 255) & ~(size_t)255) +
+           ptype_smem_bytes(tx, ty, tz);
 }
 
 __device__ __forceinline__ unsigned short site_species(const GatherArgs<float> &a, long long s)
@@ -76,13 +90,25 @@ __device__ __forceinline__ float4 tex4(unsigned long long tex, int i)
 
 __device__ __forceinline__ float quad(const float4 c, float t) { return fmaf(fmaf(c.x, t, c.y), t, c.z); }
 
+// density spline coefficients of neighbour species j at window segment i:
+// the shared-memory window for the dominant species, the texture path else
+__device__ __forceinline__ float4 dens_coef(const float4 *__restrict__ tab, int m, unsigned long long texv, int n,
+                                            int seg_lo, int j, int i)
+{
+    float4 c;
+    if (j == m) c = tab[i];
+    else c = tex4(texv, j * n + seg_lo + i);
+    return c;
+}
+
 template <int SH>
-__device__ __forceinline__ void density_shells_pa(const ShellInfo &shc, const float4 *__restrict__ po,
+__device__ __forceinline__ void density_shells_pa(const ShellInfo &shc, int seg_lo, const float4 *__restrict__ po,
                                                   const float4 *__restrict__ sA, const float4 *__restrict__ sB,
                                                   const unsigned short *__restrict__ sT, int slot, const PairSites &ui,
                                                   float2 unorm, float rc_lat, float2 lim2, float2 S2, unsigned nwin,
-                                                  unsigned long long texv, int n, Acc<float> &ra, Acc<float> &rb,
-                                                  unsigned long long &ma, unsigned long long &mb)
+                                                  const float4 *__restrict__ tab, int m, unsigned long long texv, int n,
+                                                  Acc<float> &ra, Acc<float> &rb, unsigned long long &ma,
+                                                  unsigned long long &mb)
 {
     if constexpr (SH < kLVec.nshell) {
         constexpr int KB = kLVec.shell_begin[SH], KE = kLVec.shell_begin[SH + 1];
@@ -90,7 +116,7 @@ __device__ __forceinline__ void density_shells_pa(const ShellInfo &shc, const fl
         constexpr bool dense = SH < kSparseShell;
         const bool na = (float)N2 <= lim2.x, nb = (float)N2 <= lim2.y;
         if (SH >= shc.nshell || !(na || nb)) return;
-        const PShell sh = pshell<SH>(shc, 0);
+        const PShell sh = pshell<SH>(shc, seg_lo);
         float2 part = make_float2(0.f, 0.f);
         if constexpr (dense) {
 #pragma unroll 2
@@ -102,8 +128,9 @@ __device__ __forceinline__ void density_shells_pa(const ShellInfo &shc, const fl
                 float2 t, rs;
                 int ia, ib;
                 arg_p(sh, g.q, S2, nwin, t, rs, ia, ib);
-                part = p_add(part, make_float2(cubic(tex4(texv, (int)(ty & 0xffu) * n + ia), t.x),
-                                               cubic(tex4(texv, (int)(ty >> 8) * n + ib), t.y)));
+                const float4 ca = dens_coef(tab, m, texv, n, seg_lo, (int)(ty & 0xffu), ia);
+                const float4 cb = dens_coef(tab, m, texv, n, seg_lo, (int)(ty >> 8), ib);
+                part = p_add(part, make_float2(cubic(ca, t.x), cubic(cb, t.y)));
             }
         } else {
             const float ta = screen_thr(shc.nrm[SH], rc_lat, unorm.x, na);
@@ -118,8 +145,9 @@ __device__ __forceinline__ void density_shells_pa(const ShellInfo &shc, const fl
                     float2 t, rs;
                     int ia, ib;
                     arg_p(sh, g.q, S2, nwin, t, rs, ia, ib);
-                    part = p_add(part, make_float2(cubic(tex4(texv, (int)(ty & 0xffu) * n + ia), t.x),
-                                                   cubic(tex4(texv, (int)(ty >> 8) * n + ib), t.y)));
+                    const float4 ca = dens_coef(tab, m, texv, n, seg_lo, (int)(ty & 0xffu), ia);
+                    const float4 cb = dens_coef(tab, m, texv, n, seg_lo, (int)(ty >> 8), ib);
+                    part = p_add(part, make_float2(cubic(ca, t.x), cubic(cb, t.y)));
                     const int bi = k - kSparseK0;
                     if (bi < 64) {
                         const unsigned long long bit = 1ull << bi;
@@ -131,7 +159,8 @@ __device__ __forceinline__ void density_shells_pa(const ShellInfo &shc, const fl
         }
         kahan_nz(ra, part.x);
         kahan_nz(rb, part.y);
-        density_shells_pa<SH + 1>(shc, po, sA, sB, sT, slot, ui, unorm, rc_lat, lim2, S2, nwin, texv, n, ra, rb, ma, mb);
+        density_shells_pa<SH + 1>(shc, seg_lo, po, sA, sB, sT, slot, ui, unorm, rc_lat, lim2, S2, nwin, tab, m, texv, n,
+                                  ra, rb, ma, mb);
     }
 }
 
@@ -272,17 +301,24 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_density_pa(const __grid_const
 {
     using G = PTile<TX, TY, TZ>;
     extern __shared__ __align__(32) unsigned char smem[];
-    const PackedSmem sm = carve_p<TX, TY, TZ>(smem, 0, 1);
+    const int nwin = a.nseg - a.seg_lo;
+    const int n = a.nknot, m = a.amaj;
+    // the dominant species' density window plus the zero segment
+    float4 *tab = reinterpret_cast<float4 *>(smem);
+    for (int k = threadIdx.x; k <= nwin; k += G::NT) {
+        const Vec4<float> c = k < nwin ? a.al_tfv[(size_t)m * n + a.seg_lo + k] : Vec4<float>{0.f, 0.f, 0.f, 0.f};
+        tab[k] = make_float4(c.x, c.y, c.z, c.w);
+    }
+    const size_t wb = alloy_window_bytes(false, nwin);
+    const PackedSmem sm = carve_p<TX, TY, TZ>(smem, wb, 1);
     unsigned short *sT =
-        reinterpret_cast<unsigned short *>(smem + ((packed_smem_bytes(0, TX, TY, TZ, 1) + 255) & ~(size_t)255));
+        reinterpret_cast<unsigned short *>(smem + ((packed_smem_bytes(wb, TX, TY, TZ, 1) + 255) & ~(size_t)255));
     fill_rep_cache<float>(a, sm.rep);
     __syncthreads();
 
     const PThread<TX, TY, TZ> th;
     const float4 *po = &a.offp[th.p][0][0];
     const float2 S2 = p_dup(a.S);
-    const unsigned nwin = (unsigned)a.nseg;  // whole tables; segment nseg is the zero one
-    const int n = a.nknot;
     unsigned st = 0;
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         double dt_rep;
@@ -311,8 +347,8 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_density_pa(const __grid_const
             const float2 un = make_float2(sqrtf(A.x * A.x + A.z * A.z + B.x * B.x), sqrtf(A.y * A.y + A.w * A.w + B.y * B.y));
             const float la = a.rc_lat + un.x + U, lb = a.rc_lat + un.y + U;
             const float2 lim2 = make_float2(live_a ? la * la : -1.f, live_b ? lb * lb : -1.f);
-            density_shells_pa<0>(a.sh, po, cA, cB, sT, th.slot, ui, un, a.rc_lat, lim2, S2, nwin, a.tex_afv, n, ra, rb,
-                                 ma, mb);
+            density_shells_pa<0>(a.sh, a.seg_lo, po, cA, cB, sT, th.slot, ui, un, a.rc_lat, lim2, S2, (unsigned)nwin,
+                                 tab, m, a.tex_afv, n, ra, rb, ma, mb);
         }
         if (has_ra) {
             int pos = 0;

@@ -221,6 +221,7 @@ struct misa_sim {
     double *al_knots = nullptr;
     void *al_fv = nullptr, *al_fd = nullptr, *al_Fv = nullptr, *al_pv = nullptr, *al_pd = nullptr;
     int al_cap = 0;  // species the alloy arrays were allocated for
+    int amaj = 0;    // the species with the most atoms
     unsigned long long tex_afv = 0, tex_afd = 0, tex_apd = 0;  // FP32: texture objects over the alloy tables
     // captured step graph
     bool use_graph = true;
@@ -438,6 +439,8 @@ void fill_gather(misa_sim *s, GatherArgs<T> &g, bool force_pass = false)
         g.tex_apd = s->tex_apd;
         g.al_tFv = (const Vec4<T> *)s->al_Fv;
         g.al_tpv = (const Vec4<T> *)s->al_pv;
+        g.al_tfv = (const Vec4<T> *)s->al_fv;
+        g.amaj = s->amaj;
     }
 }
 
@@ -487,8 +490,10 @@ struct TileKernels {
             CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
             CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
             const int ad = (int)s->smem_alloy_d;
-            CK(cudaFuncSetAttribute(k_density_pa<TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ad));
-            CK(cudaFuncSetAttribute(k_density_pa<TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ad));
+            if (ad) {
+                CK(cudaFuncSetAttribute(k_density_pa<TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ad));
+                CK(cudaFuncSetAttribute(k_density_pa<TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ad));
+            }
             return MISA_OK;
         } else {
             CK(cudaFuncSetAttribute(k_density<T, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_density));
@@ -505,8 +510,10 @@ struct TileKernels {
             CK(cudaFuncSetAttribute(k_force_p<TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, f));
             CK(cudaFuncSetAttribute(k_force_p<TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, f));
             const int af = (int)s->smem_alloy_f;
-            CK(cudaFuncSetAttribute(k_force_pa<TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, af));
-            CK(cudaFuncSetAttribute(k_force_pa<TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, af));
+            if (af) {
+                CK(cudaFuncSetAttribute(k_force_pa<TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, af));
+                CK(cudaFuncSetAttribute(k_force_pa<TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, af));
+            }
             return MISA_OK;
         } else {
             CK(cudaFuncSetAttribute(k_force<T, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_force));
@@ -617,12 +624,17 @@ int configure(misa_sim *s, int td, int tf)
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     s->smem_density = smem_density_bytes<T>(s, (size_t)optin);
     s->smem_force = smem_force_bytes<T>(s);
+    s->smem_alloy_d = s->smem_alloy_f = 0;
     if (sizeof(T) == 4) {
+        // the alloy passes' sizes; 0 marks a shape whose alloy pass does not fit
         const TileShape &a = kTiles[td], &b = kTiles[tf];
-        s->smem_alloy_d = alloy_smem_bytes(a.tx, a.ty, a.tz);
-        s->smem_alloy_f = alloy_smem_bytes(b.tx, b.ty, b.tz);
-        if (s->smem_alloy_d > (size_t)optin || s->smem_alloy_f > (size_t)optin)
-            return fail(s, MISA_EINVAL, "tile shape exceeds the shared memory of a block (alloy passes)");
+        const int nwin = s->p.n_knots - 1 - seg_lo_of(s);
+        const size_t ad = alloy_smem_bytes(false, nwin, a.tx, a.ty, a.tz);
+        const size_t af = alloy_smem_bytes(true, nwin, b.tx, b.ty, b.tz);
+        s->smem_alloy_d = ad <= (size_t)optin ? ad : 0;
+        s->smem_alloy_f = af <= (size_t)optin ? af : 0;
+        if (s->nsp > 1 && (!s->smem_alloy_d || !s->smem_alloy_f))
+            return fail(s, MISA_EINVAL, "tile shape and table windows exceed the shared memory of a block (alloy passes)");
     }
     if (s->smem_density > (size_t)optin || s->smem_force > (size_t)optin)
         return fail(s, MISA_EINVAL, "tile shape and table window exceed the shared memory of a block");
@@ -852,6 +864,22 @@ int refresh(misa_sim *s, bool forces)
     return MISA_OK;
 }
 
+// FP32 alloy handles: whether both alloy passes of tile shape k fit in the
+// shared memory of a block (always true for one species and for FP64)
+template <typename T>
+bool alloy_fits(const misa_sim *s, int k)
+{
+    if (sizeof(T) != 4 || s->nsp <= 1) return true;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return false;
+    const TileShape &t = kTiles[k];
+    const int nwin = s->p.n_knots - 1 - seg_lo_of(s);
+    return alloy_smem_bytes(true, nwin, t.tx, t.ty, t.tz) <= (size_t)optin &&
+           alloy_smem_bytes(false, nwin, t.tx, t.ty, t.tz) <= (size_t)optin;
+}
+
 // Tile autotuner: times the density pass and the force pass of the current
 // state for every tile shape and keeps the fastest shape of each pass.
 template <typename T>
@@ -862,7 +890,7 @@ int autotune(misa_sim *s)
     float best_d = 1e30f, best_f = 1e30f;
     int kd = 0, kf = 0;
     for (int k = 0; k < kNTiles; ++k) {
-        if (!tile_ok(s->prec, kTiles[k])) continue;
+        if (!tile_ok(s->prec, kTiles[k]) || !alloy_fits<T>(s, k)) continue;
         int rc = configure<T>(s, k, k);
         if (rc) return rc;
         rc = launch_forces<T>(s, 0, false);  // warm-up
@@ -1214,8 +1242,14 @@ int set_species_impl(misa_sim *s, int nsp, const double *f, const double *F, con
     }
     std::vector<int8_t> ht((size_t)s->ns);
     CK(cudaMemcpy(ht.data(), types, (size_t)s->ns, cudaMemcpyDefault));
-    for (int8_t t : ht)
+    std::vector<long long> cnt(nsp, 0);
+    for (int8_t t : ht) {
         if (t < 0 || t >= nsp) return fail(s, MISA_EINVAL, "atom type outside [0, n_species)");
+        ++cnt[t];
+    }
+    int maj = 0;
+    for (int t = 1; t < nsp; ++t)
+        if (cnt[t] > cnt[maj]) maj = t;
     const int npair = nsp * (nsp + 1) / 2;
     if (nsp > s->al_cap) {
         const int cp = kMaxSpecies, pp = kMaxSpecies * (kMaxSpecies + 1) / 2;
@@ -1263,6 +1297,18 @@ int set_species_impl(misa_sim *s, int nsp, const double *f, const double *F, con
     }
     CK(cudaStreamSynchronize(s->st));  // ht is a host temporary
     s->nsp = nsp;
+    s->amaj = maj;
+    if (!alloy_fits<T>(s, s->tile) || !alloy_fits<T>(s, s->tile_f)) {
+        // the current shapes' alloy passes do not fit: the first shape that does
+        int k = 0;
+        while (k < kNTiles && (!tile_ok(s->prec, kTiles[k]) || !alloy_fits<T>(s, k))) ++k;
+        if (k == kNTiles) return fail(s, MISA_EINVAL, "no tile shape fits the alloy passes' shared memory");
+        int rc = configure<T>(s, k, k);
+        if (rc) return rc;
+    } else {
+        int rc = configure<T>(s, s->tile, s->tile_f);  // the alloy passes' kernel attributes
+        if (rc) return rc;
+    }
     if (s->graph) {
         cudaGraphExecDestroy(s->graph);
         s->graph = nullptr;

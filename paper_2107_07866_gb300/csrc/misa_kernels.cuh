@@ -215,8 +215,10 @@ struct GatherArgs {
     const int8_t *atype;
     const int *sid, *ra_id;  // atom id per site (-1: vacant), per run-away
     int nsp, nknot;
+    int amaj;  // the dominant species: the density pass keeps its density window in shared memory
     unsigned long long tex_afv, tex_afd, tex_apd;
     const Vec4<T> *al_tFv, *al_tpv;
+    const Vec4<T> *al_tfv;  // density values per species (the table of tex_afv)
     // neighbour offset index for this tile shape: per parity, per lattice
     // vector: (shared-memory slot displacement as int bits, 2 n_x, 2 n_y, 2 n_z)
     float4 off[2][kNVec];
