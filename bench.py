@@ -37,7 +37,7 @@ from paper_2107_07866_gb300 import synth  # noqa: E402
 METRIC = "EAM atom-steps/s at 54M atoms, FP32-force vs FP64 path; % HBM roofline"
 UNIT = "atom-steps/s"
 
-# Algorithmic work per site and pass ("Roofline"): FP32 flops with
+# Algorithmic work per site and pass: FP32 flops with
 # FMA = 2, counted from the method's arithmetic: 112 offset candidates (the
 # neighbour offset index out to rc + 2 skin), 58 pairs inside rc per atom of
 # the crystal.

@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Tolerances (BASELINE the benchmark spec): forces within 1e-12 relative for the FP64
+Tolerances: forces within 1e-12 relative for the FP64
 path and 1e-5 for the FP32 force path; the same normalised error is applied
 to densities and per-atom energies.  Normalised error of a per-atom
 quantity X: max_i |X_i - X_i^o| / max(|X_i^o|, rms_i |X^o|), the rms floor
