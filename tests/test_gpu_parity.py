@@ -163,9 +163,11 @@ def test_cascade_trajectory_with_runaways(misa, pot, oracle, opot, prec):
     assert len(allid) == len(x0) and len(np.unique(allid)) == len(x0)
 
 
-def test_nve_drift_fp32(misa, pot):
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_nve_drift(misa, pot, prec):
+    # per-atom total-energy drift below 1e-4 eV over 1000 steps of 1 fs
     n = 10
-    with misa.Sim(pot, n, precision="fp32", dt_max=1.0) as s:
+    with misa.Sim(pot, n, precision=prec, dt_max=1.0) as s:
         s.set_velocities(synth.maxwell_velocities(2 * n ** 3, 600.0, M, 0))
         pe0, ke0 = s.energies()
         es = []
@@ -173,6 +175,25 @@ def test_nve_drift_fp32(misa, pot):
             s.step(100)
             pe, ke = s.energies()
             es.append(pe + ke)
+    drift = np.max(np.abs(np.array(es) - (pe0 + ke0))) / (2 * n ** 3)
+    assert drift < 1e-4, drift
+
+
+def test_nve_drift_cascade_adaptive_dt(misa, pot):
+    # the same bound through a knock-on cascade: adaptive timestep, run-aways,
+    # hash updates every 5 steps, 1000 steps
+    n = 10
+    with misa.Sim(pot, n, precision="fp32", dt_max=1.0, dx_max=0.02, reassign_period=5) as s:
+        s.set_velocities(synth.maxwell_velocities(2 * n ** 3, 300.0, M, 11))
+        s.insert_pka(-1, 1000.0, synth.random_direction(12))
+        pe0, ke0 = s.energies()
+        es = []
+        for _ in range(10):
+            s.step(100)
+            pe, ke = s.energies()
+            es.append(pe + ke)
+        st = s.stats()
+    assert st["status"] == 0 and st["step"] == 1000
     drift = np.max(np.abs(np.array(es) - (pe0 + ke0))) / (2 * n ** 3)
     assert drift < 1e-4, drift
 
