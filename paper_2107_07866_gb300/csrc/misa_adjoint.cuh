@@ -428,15 +428,23 @@ struct GradFn {
         // unit vector is zero below r_floor: no derivative term there
         const T D = P.ex * (ljx - lix) + P.ey * (ljy - liy) + P.ez * (ljz - liz);
         const T fD = Fpi * D, hD = (T)0.5 * D;
-        const int sg = P.seg;
-        T w[6], dw[6];
-        basis6<T>(sg, P.t, a.n, a.inv_hr, w, dw);
-        for (int q = 0; q < 6; ++q) {
-            const int k = sg - 2 + q;
-            if (k < 0 || k >= a.n) continue;
-            atomicAdd(&bins[k], cw * w[q] - fD * dw[q]);          // f knots
-            atomicAdd(&bins[a.n + k], hce * w[q] - hD * dw[q]);  // phi knots
-        }
+        // Hermite weights of the segment ends' values (c0, c2) and h-scaled
+        // slopes (c1, c3), and their r derivatives; the slopes' knot stencils
+        // are applied once, after the sum over CTAs (k_adj_stencil)
+        const T t = P.t, t2 = t * t, t3 = t2 * t, ih = a.inv_hr;
+        const T c0 = 2 * t3 - 3 * t2 + 1, c1 = t3 - 2 * t2 + t, c2 = -2 * t3 + 3 * t2, c3 = t3 - t2;
+        const T d0 = (6 * t2 - 6 * t) * ih, d1 = (3 * t2 - 4 * t + 1) * ih, d2 = (-6 * t2 + 6 * t) * ih,
+                d3 = (3 * t2 - 2 * t) * ih;
+        const int sg = P.seg;  // 0 <= sg <= n - 2
+        T *Yf = bins, *Yp = bins + a.n, *Mf = bins + 3 * a.n, *Mp = bins + 4 * a.n;
+        atomicAdd(&Yf[sg], cw * c0 - fD * d0);
+        atomicAdd(&Yf[sg + 1], cw * c2 - fD * d2);
+        atomicAdd(&Mf[sg], cw * c1 - fD * d1);
+        atomicAdd(&Mf[sg + 1], cw * c3 - fD * d3);
+        atomicAdd(&Yp[sg], hce * c0 - hD * d0);
+        atomicAdd(&Yp[sg + 1], hce * c2 - hD * d2);
+        atomicAdd(&Mp[sg], hce * c1 - hD * d1);
+        atomicAdd(&Mp[sg + 1], hce * c3 - hD * d3);
     }
 };
 
@@ -475,9 +483,10 @@ __device__ __forceinline__ void embed_bins(const AdjArgs<T> &a, T *bins, T rho, 
     }
 }
 
-// gradient scatter: grid (blocks, replica); each CTA zeroes its 3n bins in
-// shared memory, scatters its atoms' pair terms with shared-memory atomics,
-// then writes the bins to partial[cta][3n] (FP64)
+// gradient scatter: grid (blocks, replica); each CTA zeroes its 5n bins in
+// shared memory ([0, n) f values, [n, 2n) phi values, [2n, 3n) F knots, [3n,
+// 4n) f slopes, [4n, 5n) phi slopes), scatters its atoms' pair terms with
+// shared-memory atomics, then writes the bins to partial[cta][5n] (FP64)
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_grad(AdjArgs<T> a, double *partial)
 {
@@ -486,7 +495,7 @@ __global__ void __launch_bounds__(256) k_adj_grad(AdjArgs<T> a, double *partial)
     const int r = blockIdx.y;
     const RepDesc rd = a.reps[r];
     const int nra = a.sc[r].n_ra;
-    const int nb = 3 * a.n;
+    const int nb = 5 * a.n;
     for (int k = threadIdx.x; k < nb; k += blockDim.x) bins[k] = (T)0;
     __syncthreads();
     const double Nr = (double)rd.ns;
@@ -532,6 +541,36 @@ __global__ void __launch_bounds__(256) k_adj_reduce(const double *partial, int n
         double t = rows[0][threadIdx.x];
         for (int y = 1; y < 8; ++y) t += rows[y][threadIdx.x];
         grad[k] = t;
+    }
+}
+
+// h * slope of knot k = sum_j slope_weight(k, j) y_j: the knot slopes of
+// the spline (4th-order central differences inside, 2nd order at the two
+// outer knots of each end)
+__device__ __forceinline__ double slope_weight(int k, int j, int n)
+{
+    if (k == 0) return j == 0 ? -1.5 : j == 1 ? 2.0 : j == 2 ? -0.5 : 0.0;
+    if (k == n - 1) return j == n - 1 ? 1.5 : j == n - 2 ? -2.0 : j == n - 3 ? 0.5 : 0.0;
+    if (k == 1 || k == n - 2) return j == k + 1 ? 0.5 : j == k - 1 ? -0.5 : 0.0;
+    const int d = j - k;
+    return d == -2 ? 1.0 / 12.0 : d == -1 ? -8.0 / 12.0 : d == 1 ? 8.0 / 12.0 : d == 2 ? -1.0 / 12.0 : 0.0;
+}
+
+// Knot gradient from the summed bins (sum[5n], layout of k_adj_grad):
+// d/dy_j of the f and phi tables = value bin j + sum over the slopes k
+// within two knots of j of slope bin k * slope_weight(k, j); F knots as
+// summed.
+__global__ void k_adj_stencil(const double *sum, int n, double *grad)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 3 * n; q += gridDim.x * blockDim.x) {
+        double g = sum[q];
+        if (q < 2 * n) {
+            const int tab = q / n, j = q - tab * n;
+            const double *M = sum + (size_t)(3 + tab) * n;
+            for (int k = j - 2; k <= j + 2; ++k)
+                if (k >= 0 && k < n) g += M[k] * slope_weight(k, j, n);
+        }
+        grad[q] = g;
     }
 }
 
