@@ -157,6 +157,7 @@ __device__ __forceinline__ void visit_site(const A &a, const RepDesc &rd, int nr
     const long long q = ls / (2 * rd.nx);
     const int cy = (int)(q % rd.ny), cz = (int)(q / rd.ny);
     const int p = x2 & 1;
+#pragma unroll 4
     for (int k = 0; k < a.nvec; ++k) {
         const LVec o = c_lvec.v[k];
         const int tx = wrapi(x2 + o.x, 2 * rd.nx);
