@@ -103,9 +103,11 @@ __device__ __forceinline__ bool adj_pair(const A &a, int nx, int ny, int nz, T d
         const T rs = rsqrt_approx(rr2);
         r = rr2 * rs;
         inv = P.floor_hit ? (T)0 : rs;
-    } else {
-        r = sqrt(P.floor_hit ? a.rfloor2 : r2);
-        inv = P.floor_hit ? (T)0 : (T)1 / r;
+    } else {  // FP32 seed and Newton steps (rsqrt_nr): no FP64 square root or division
+        const T rr2 = P.floor_hit ? a.rfloor2 : r2;
+        const T rs = rsqrt_nr(rr2);
+        r = rr2 * rs;
+        inv = P.floor_hit ? (T)0 : rs;
     }
     P.r = r;
     P.ex = rx * inv;
@@ -123,14 +125,10 @@ __device__ __forceinline__ bool adj_pair(const A &a, int nx, int ny, int nz, T d
         const T fl = floor(x);
         P.seg = sp.xint + (int)fl;
         P.t = x - fl;
-    } else {
-        const double nn = sqrt((double)n2);
-        const double x0 = nn * (double)a.S;
-        const double xi = floor(x0);
-        const T dr = q / (r + (T)nn);
-        const T x = (T)(x0 - xi) + dr * a.S;
+    } else {  // FP64: r S carries the full precision t needs
+        const T x = r * a.S;
         const T fl = floor(x);
-        P.seg = (int)xi + (int)fl;
+        P.seg = (int)fl;
         P.t = x - fl;
     }
     if (P.seg < 0) {

@@ -52,9 +52,24 @@ struct Arith<float> {
     }
 };
 
+// 1/sqrt(x) in FP64 for x in FP32's normal range (pair distances squared):
+// an FP32 seed (conversions on the integer pipe) and two Newton steps
+// y <- y - y (x y^2 - 1) / 2, each doubling the correct bits (24 -> 48 ->
+// full precision, a few ulps of rounding).  FP64 runs at a small fraction
+// of the FP32 rate on GB300; this takes 8 FP64 operations where an IEEE
+// square root and division take several times that.
+__device__ __forceinline__ double rsqrt_nr(double x)
+{
+    double y = f2d_bits(rsqrtf(d2f_bits(x)));
+    double h = fma(x * y, y, -1.0);
+    y = fma(-0.5 * y, h, y);
+    h = fma(x * y, y, -1.0);
+    return fma(-0.5 * y, h, y);
+}
+
 template <>
 struct Arith<double> {
-    static __device__ __forceinline__ double rsqrt(double x) { return 1.0 / sqrt(x); }
+    static __device__ __forceinline__ double rsqrt(double x) { return rsqrt_nr(x); }
     static __device__ __forceinline__ int split(double x, double &t)
     {
         double fl = floor(x);
@@ -427,8 +442,8 @@ __device__ __forceinline__ int shell_arg(const ShellRegs<T> &sh, T q, T S, int s
         t = __fsub_rn(x, fl);
         return min(max(__float_as_int(y) + sh.xoff, seglo), nseg1);
     } else {
-        const double r = sqrt(r2);
-        rinv = 1.0 / r;
+        rinv = rsqrt_nr(r2);
+        const double r = r2 * rinv;
         const double x = r * S;
         const double fl = floor(x);
         t = x - fl;
@@ -459,9 +474,7 @@ __device__ __forceinline__ void direct_arg(T r2, T S, T rfloor2, int &seg, T &t,
     r2 = floor_hit ? rfloor2 : r2;
     T rs = Arith<T>::rsqrt(r2);
     rinv = rs;
-    T r;
-    if constexpr (sizeof(T) == 4) r = r2 * rs;
-    else r = sqrt(r2);
+    const T r = r2 * rs;
     seg = Arith<T>::split(r * S, t);
 }
 
