@@ -486,16 +486,23 @@ __device__ __forceinline__ void embed_bins(const AdjArgs<T> &a, T *bins, T rho, 
 // shared memory ([0, n) f values, [n, 2n) phi values, [2n, 3n) F knots, [3n,
 // 4n) f slopes, [4n, 5n) phi slopes), scatters its atoms' pair terms with
 // shared-memory atomics, then writes the bins to partial[cta][5n] (FP64)
+// FP32 bins in two copies, one per half warp: shared-memory FP32 atomics
+// that collide within a warp are several times slower than distinct ones
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_grad(AdjArgs<T> a, double *partial)
+constexpr int kBinCopies = sizeof(T) == 4 ? 2 : 1;
+template <typename T>
+constexpr int kGradThreads = sizeof(T) == 4 ? 1024 : 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kGradThreads<T>) k_adj_grad(AdjArgs<T> a, double *partial)
 {
     extern __shared__ __align__(16) unsigned char bin_smem[];
-    T *bins = reinterpret_cast<T *>(bin_smem);
     const int r = blockIdx.y;
     const RepDesc rd = a.reps[r];
     const int nra = a.sc[r].n_ra;
     const int nb = 5 * a.n;
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) bins[k] = (T)0;
+    for (int k = threadIdx.x; k < kBinCopies<T> * nb; k += blockDim.x) reinterpret_cast<T *>(bin_smem)[k] = (T)0;
+    T *bins = reinterpret_cast<T *>(bin_smem) + (kBinCopies<T> == 2 && (threadIdx.x & 16) ? nb : 0);
     __syncthreads();
     const double Nr = (double)rd.ns;
     const T ce = (T)(2.0 * (a.Etot[r] - a.Eref[r]) / (Nr * Nr));
@@ -520,7 +527,9 @@ __global__ void __launch_bounds__(256) k_adj_grad(AdjArgs<T> a, double *partial)
     }
     __syncthreads();
     double *out = partial + ((size_t)r * gridDim.x + blockIdx.x) * nb;
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) out[k] = (double)bins[k];
+    const T *b0 = reinterpret_cast<const T *>(bin_smem);
+    for (int k = threadIdx.x; k < nb; k += blockDim.x)
+        out[k] = kBinCopies<T> == 2 ? (double)b0[k] + (double)b0[nb + k] : (double)b0[k];
 }
 
 // grad[k] = sum over CTAs of partial[cta][k] in a fixed order: a block of

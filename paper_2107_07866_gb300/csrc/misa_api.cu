@@ -1334,7 +1334,8 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
         }
         s->dl = dalloc(s, sizeof(T) * s->ns);
         s->ra_dl = dalloc(s, sizeof(T) * capt);
-        int gx = (s->nsm * 2 + s->nrep - 1) / s->nrep;
+        // FP32: one 1024-thread CTA per SM (two bin copies); FP64: two 256-thread CTAs
+        int gx = ((sizeof(T) == 4 ? s->nsm : s->nsm * 2) + s->nrep - 1) / s->nrep;
         s->adj_cta = gx < 1 ? 1 : gx;
         s->adj_partial = (double *)dalloc(s, sizeof(double) * 5 * n * (size_t)s->adj_cta * s->nrep);
         s->adj_sum = (double *)dalloc(s, sizeof(double) * 5 * n);
@@ -1343,9 +1344,11 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
         s->adj_fref = (double *)dalloc(s, sizeof(double) * 3 * s->ns);
         if (!s->dl || !s->ra_dl || !s->adj_partial || !s->adj_sum || !s->adj_grad || !s->adj_eref || !s->adj_fref)
             return fail(s, MISA_EOOM, "adjoint work arrays");
-        CK(cudaFuncSetAttribute(k_adj_grad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(T) * 5 * n)));
+        CK(cudaFuncSetAttribute(k_adj_grad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(T) * 5 * n * kBinCopies<T>)));
     }
-    if ((size_t)5 * n * sizeof(T) > 227u * 1024u) return fail(s, MISA_EINVAL, "too many knots for the gradient bins");
+    if ((size_t)5 * n * sizeof(T) * kBinCopies<T> > 227u * 1024u)
+        return fail(s, MISA_EINVAL, "too many knots for the gradient bins");
     // forward: rho, F', E_i, forces of the current positions
     int rc = launch_forces<T>(s, 0, true);
     if (rc) return rc;
@@ -1398,7 +1401,8 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
     k_adj_lambda<T><<<dim3(nb, s->nrep), 256, 0, s->st>>>(a, s->partial);
     k_sum_stage2<<<s->nrep, 1024, 0, s->st>>>(s->partial, nb, s->red_out + s->nrep);  // sum |F - Fref|^2
     k_adj_dl<T><<<site_grid(s), 256, 0, s->st>>>(a);
-    k_adj_grad<T><<<dim3(s->adj_cta, s->nrep), 256, sizeof(T) * 5 * n, s->st>>>(a, s->adj_partial);
+    k_adj_grad<T><<<dim3(s->adj_cta, s->nrep), kGradThreads<T>, sizeof(T) * 5 * n * kBinCopies<T>, s->st>>>(
+        a, s->adj_partial);
     k_adj_reduce<<<(5 * n + 31) / 32, dim3(32, 8), 0, s->st>>>(s->adj_partial, s->adj_cta * s->nrep, 5 * n, s->adj_sum);
     k_adj_stencil<<<(3 * n + 255) / 256, 256, 0, s->st>>>(s->adj_sum, n, s->adj_grad);
     s->launches += 9;
