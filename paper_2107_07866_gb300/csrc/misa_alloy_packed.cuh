@@ -392,8 +392,13 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_density_pa(const __grid_const
 // force pass + closing half kick with species
 // ---------------------------------------------------------------------------
 
+// Two CTAs per SM for tiles of up to 512 threads: the pass waits on texture
+// latency, and more resident warps hide more of it.
+template <int TX, int TY, int TZ>
+constexpr int kForcePaBlocks = TX * TY * TZ <= 512 ? 2 : 1;
+
 template <int TX, int TY, int TZ, bool ENERGY>
-__global__ void __launch_bounds__(TX *TY *TZ, 1) k_force_pa(const __grid_constant__ GatherArgs<float> a)
+__global__ void __launch_bounds__(TX *TY *TZ, kForcePaBlocks<TX, TY, TZ>) k_force_pa(const __grid_constant__ GatherArgs<float> a)
 {
     using G = PTile<TX, TY, TZ>;
     extern __shared__ __align__(32) unsigned char smem[];

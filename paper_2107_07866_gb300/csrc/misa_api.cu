@@ -553,8 +553,10 @@ struct TileKernels {
         } else if constexpr (kF32) {
             constexpr int nt = TX * TY * TZ;
             if (s->nsp > 1) {  // alloys
-                if (energy) k_force_pa<TX, TY, TZ, true><<<grid, nt, s->smem_alloy_f, s->st>>>(g);
-                else k_force_pa<TX, TY, TZ, false><<<grid, nt, s->smem_alloy_f, s->st>>>(g);
+                const int blocks = kForcePaBlocks<TX, TY, TZ>;
+                const int g2 = g.ntiles < blocks * s->nsm ? g.ntiles : blocks * s->nsm;
+                if (energy) k_force_pa<TX, TY, TZ, true><<<g2, nt, s->smem_alloy_f, s->st>>>(g);
+                else k_force_pa<TX, TY, TZ, false><<<g2, nt, s->smem_alloy_f, s->st>>>(g);
                 return;
             }
             if (energy) k_force_p<TX, TY, TZ, true><<<grid, nt, s->smem_force, s->st>>>(g);
