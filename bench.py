@@ -578,7 +578,9 @@ def run_gpu(args):
     step_s = el_ms / 1e3 / args.steps
     sha = kernel_source_sha()
     l1 = None
-    if NCU_WAVEFRONTS["source_sha"] == sha and alloy is None:
+    if NCU_WAVEFRONTS["source_sha"] == sha and alloy is None and not batched:
+        # per-site wavefronts of the single-box crystal (2M-atom capture); not
+        # carried over to the batch of small boxes
         # one L1 data-pipe wavefront per SM per clock at the sampled SM clock
         clk_hz = (clocks.get("sm_mhz") or 2070.0) * 1e6
         pipe = 152 * clk_hz
