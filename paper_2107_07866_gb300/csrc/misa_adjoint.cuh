@@ -14,10 +14,13 @@
 //   F knots:   sum over atoms of          c_e w_k(rho_i) - dw_k(rho_i) Dl_i
 // where D = d r_ij / d eps along lambda and Dl_i = sum_j f'(r_ij) D.
 // Kernels: lambda (+ force-loss sums), Dl gather, gradient scatter into
-// per-CTA bins in shared memory (in the handle's precision: FP32 bins take
-// native shared-memory atomics and half the space; their rounding, ~1e-6 of
-// a bin, is far below the FP32 gradient's own error), one ordered FP64
-// reduction over CTAs.  Pair arithmetic in the precision T of the handle.
+// per-CTA bins in shared memory (in the handle's precision; FP32 bins in two
+// copies, one per half warp, since shared FP32 atomics that collide within a
+// warp are slow; their rounding, ~1e-6 of a bin, is far below the FP32
+// gradient's own error).  A pair adds its Hermite weights to the value and
+// slope bins of its segment's two end knots; one ordered FP64 reduction over
+// CTAs, then the slope bins reach the knots through the slopes' difference
+// stencils.  Pair arithmetic in the precision T of the handle.
 #pragma once
 
 #include "misa_md.cuh"

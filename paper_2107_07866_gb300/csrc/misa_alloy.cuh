@@ -7,11 +7,13 @@
 // along r_hat (Eq. eam_force_ij).  Species are held per atom id, so atom
 // moves between the site array and the run-away list need no bookkeeping.
 //
-// One thread per site (and one per run-away), neighbours through the offset
-// index and the run-away list (run-aways only from tiles flagged as within
-// reach of one), spline tables read from global memory through L1, sums
-// compensated in FP32 (plain in FP64) as in the single-type passes.  These passes serve correctness for any number of types; the
-// single-type path keeps the packed FP32 gathers.
+// This file holds the alloy passes of the FP64 path (one thread per site)
+// and, for both precisions, those of the run-away atoms (one warp per
+// run-away): neighbours through the offset index and the run-away list
+// (run-aways only from tiles flagged as within reach of one), spline tables
+// read from global memory through L1, sums compensated in FP32 (plain in
+// FP64) as in the single-type passes.  The FP32 path's array atoms go
+// through the packed tile gathers of misa_alloy_packed.cuh.
 #pragma once
 
 #include "misa_adjoint.cuh"
