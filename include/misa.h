@@ -257,9 +257,14 @@ int misa_set_tables(misa_sim *s, const double *f_knots, const double *phi_knots,
  * Host or device pointers.  Types stay with the atoms; with one species the
  * single-type tables and gathers are used.  Recomputes the forces of the
  * current positions and drops a captured step graph; synchronises;
- * MISA_EINVAL for a type outside [0, n_species).  Alloy passes run one
- * thread per site with tables in global memory; misa_loss_grad and
- * misa_save keep to one type.  misa_set_tables returns to one type. */
+ * MISA_EINVAL for a type outside [0, n_species) or when no tile shape fits
+ * the alloy passes' shared memory.  FP32 handles run the packed tile
+ * gathers with the species of every staged site, the most populous
+ * species' density window in shared memory and the other tables through
+ * the texture path (the tile shapes are re-chosen if the current ones do not
+ * fit); FP64 handles run one thread per site with tables in global memory.
+ * misa_loss_grad and misa_save keep to one type.  misa_set_tables returns
+ * to one type. */
 int misa_set_species(misa_sim *s, int n_species, const double *f_knots, const double *F_knots,
                      const double *phi_knots, const int8_t *types);
 
