@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(kGradThreads<T>) k_adj_grad(AdjArgs<T> a, doub
 // 32 x 8 threads takes 32 knots; thread row y sums CTAs y, y + 8, ... in
 // order, then the 8 row sums are added in row order.  Launch with blockDim
 // (32, 8) and ceil(nb / 32) blocks.
-__global__ void __launch_bounds__(256) k_adj_reduce(const double *partial, int ncta, int nb, double *grad)
+static __global__ void __launch_bounds__(256) k_adj_reduce(const double *partial, int ncta, int nb, double *grad)
 {
     __shared__ double rows[8][33];
     const int k = blockIdx.x * 32 + threadIdx.x;
@@ -571,7 +571,7 @@ __device__ __forceinline__ double slope_weight(int k, int j, int n)
 // d/dy_j of the f and phi tables = value bin j + sum over the slopes k
 // within two knots of j of slope bin k * slope_weight(k, j); F knots as
 // summed.
-__global__ void k_adj_stencil(const double *sum, int n, double *grad)
+static __global__ void k_adj_stencil(const double *sum, int n, double *grad)
 {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 3 * n; q += gridDim.x * blockDim.x) {
         double g = sum[q];

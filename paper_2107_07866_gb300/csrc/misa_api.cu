@@ -16,6 +16,7 @@
 #include "misa_packed.cuh"
 #include "misa_alloy.cuh"
 #include "misa_alloy_packed.cuh"
+#include "misa_tiles.cuh"
 
 using namespace misa;
 
@@ -126,22 +127,6 @@ __global__ void k_selftest_site(unsigned long long n, unsigned long long *bad)
 
 constexpr double kAccUnit = 9.6485332123310018e-3;  // 1 eV/(A amu) in A/fs^2 (CODATA 2018)
 constexpr double kRfloor = 1e-4;                      // A
-
-struct TileShape {
-    int tx, ty, tz;
-};
-constexpr TileShape kTiles[] = {{8, 8, 8}, {8, 8, 4}, {8, 4, 4}, {16, 8, 4}, {8, 8, 16}, {8, 8, 12}, {16, 8, 8}};
-constexpr int kNTiles = sizeof(kTiles) / sizeof(kTiles[0]);
-
-// Shapes each precision's gathers are built for: FP64 runs one thread per
-// site (2 tx ty tz <= 1024); FP32 runs two sites per thread folded in z
-// (tz even, tx ty tz <= 1024); each parity fills whole warps.
-constexpr bool tile_ok(int prec, const TileShape &t)
-{
-    const int cells = t.tx * t.ty * t.tz;
-    if (prec == MISA_FP64) return 2 * cells <= 1024 && cells % 32 == 0;
-    return t.tz % 2 == 0 && cells <= 1024 && (cells / 2) % 32 == 0;
-}
 
 std::string g_create_error;
 
@@ -473,113 +458,20 @@ size_t smem_force_bytes(misa_sim *s)
         return gather_smem_bytes<T>(0, ts.tx, ts.ty, ts.tz, 1);
 }
 
-// one instantiation of the tile kernels per tile shape: FP32 the packed
-// two-sites-per-thread gathers, FP64 one thread per site
-template <typename T, int TX, int TY, int TZ>
-struct TileKernels {
-    static constexpr bool kF32 = sizeof(T) == 4;
-    static constexpr bool kBuilt = kF32 ? (TZ % 2 == 0 && TX * TY * TZ <= 1024) : (2 * TX * TY * TZ <= 1024);
-    static int attrs_density(misa_sim *s)
-    {
-        if constexpr (!kBuilt) {
-            return MISA_EINVAL;
-        } else if constexpr (kF32) {
-            const int d = (int)s->smem_density;
-            CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
-            CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
-            CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
-            CK(cudaFuncSetAttribute(k_density_p<TX, TY, TZ, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
-            const int ad = (int)s->smem_alloy_d;
-            if (ad) {
-                CK(cudaFuncSetAttribute(k_density_pa<TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ad));
-                CK(cudaFuncSetAttribute(k_density_pa<TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ad));
-            }
-            return MISA_OK;
-        } else {
-            CK(cudaFuncSetAttribute(k_density<T, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_density));
-            CK(cudaFuncSetAttribute(k_density<T, TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_density));
-            return MISA_OK;
-        }
-    }
-    static int attrs_force(misa_sim *s)
-    {
-        if constexpr (!kBuilt) {
-            return MISA_EINVAL;
-        } else if constexpr (kF32) {
-            const int f = (int)s->smem_force;
-            CK(cudaFuncSetAttribute(k_force_p<TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, f));
-            CK(cudaFuncSetAttribute(k_force_p<TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, f));
-            const int af = (int)s->smem_alloy_f;
-            if (af) {
-                CK(cudaFuncSetAttribute(k_force_pa<TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, af));
-                CK(cudaFuncSetAttribute(k_force_pa<TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, af));
-            }
-            return MISA_OK;
-        } else {
-            CK(cudaFuncSetAttribute(k_force<T, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_force));
-            CK(cudaFuncSetAttribute(k_force<T, TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_force));
-            return MISA_OK;
-        }
-    }
-    static void density(misa_sim *s, const GatherArgs<T> &g, int grid, bool energy)
-    {
-        if constexpr (!kBuilt) {
-            return;
-        } else if constexpr (kF32) {
-            constexpr int nt = TX * TY * TZ;
-            if (s->nsp > 1) {  // alloys
-                if (energy) k_density_pa<TX, TY, TZ, true><<<grid, nt, s->smem_alloy_d, s->st>>>(g);
-                else k_density_pa<TX, TY, TZ, false><<<grid, nt, s->smem_alloy_d, s->st>>>(g);
-                return;
-            }
-            const size_t b = s->smem_density;
-            if (s->dens_db) {
-                if (energy) k_density_p<TX, TY, TZ, true, true><<<grid, nt, b, s->st>>>(g);
-                else k_density_p<TX, TY, TZ, false, true><<<grid, nt, b, s->st>>>(g);
-            } else {
-                if (energy) k_density_p<TX, TY, TZ, true, false><<<grid, nt, b, s->st>>>(g);
-                else k_density_p<TX, TY, TZ, false, false><<<grid, nt, b, s->st>>>(g);
-            }
-        } else {
-            constexpr int nt = 2 * TX * TY * TZ;
-            if (energy) k_density<T, TX, TY, TZ, true><<<grid, nt, s->smem_density, s->st>>>(g);
-            else k_density<T, TX, TY, TZ, false><<<grid, nt, s->smem_density, s->st>>>(g);
-        }
-    }
-    static void force(misa_sim *s, const GatherArgs<T> &g, int grid, bool energy)
-    {
-        if constexpr (!kBuilt) {
-            return;
-        } else if constexpr (kF32) {
-            constexpr int nt = TX * TY * TZ;
-            if (s->nsp > 1) {  // alloys
-                const int blocks = kForcePaBlocks<TX, TY, TZ>;
-                const int g2 = g.ntiles < blocks * s->nsm ? g.ntiles : blocks * s->nsm;
-                if (energy) k_force_pa<TX, TY, TZ, true><<<g2, nt, s->smem_alloy_f, s->st>>>(g);
-                else k_force_pa<TX, TY, TZ, false><<<g2, nt, s->smem_alloy_f, s->st>>>(g);
-                return;
-            }
-            if (energy) k_force_p<TX, TY, TZ, true><<<grid, nt, s->smem_force, s->st>>>(g);
-            else k_force_p<TX, TY, TZ, false><<<grid, nt, s->smem_force, s->st>>>(g);
-        } else {
-            constexpr int nt = 2 * TX * TY * TZ;
-            if (energy) k_force<T, TX, TY, TZ, true><<<grid, nt, s->smem_force, s->st>>>(g);
-            else k_force<T, TX, TY, TZ, false><<<grid, nt, s->smem_force, s->st>>>(g);
-        }
-    }
-};
-
-// kTiles order: {8,8,8}, {8,8,4}, {8,4,4}, {16,8,4}, {8,8,16}, {8,8,12}, {16,8,8}
-#define MISA_TILE_DISPATCH(T, idx, CALL)                      \
-    switch (idx) {                                            \
-    case 0: TileKernels<T, 8, 8, 8>::CALL; break;             \
-    case 1: TileKernels<T, 8, 8, 4>::CALL; break;             \
-    case 2: TileKernels<T, 8, 4, 4>::CALL; break;             \
-    case 3: TileKernels<T, 16, 8, 4>::CALL; break;            \
-    case 4: TileKernels<T, 8, 8, 16>::CALL; break;            \
-    case 5: TileKernels<T, 8, 8, 12>::CALL; break;            \
-    default: TileKernels<T, 16, 8, 8>::CALL; break;           \
-    }
+// the handle's side of a tile launch (misa_tiles.cuh)
+TileLaunch tile_launch(const misa_sim *s)
+{
+    TileLaunch L;
+    L.st = s->st;
+    L.smem_density = s->smem_density;
+    L.smem_force = s->smem_force;
+    L.smem_alloy_d = s->smem_alloy_d;
+    L.smem_alloy_f = s->smem_alloy_f;
+    L.nsm = s->nsm;
+    L.nsp = s->nsp;
+    L.dens_db = s->dens_db;
+    return L;
+}
 
 // Tile counts of every replica for one tile shape and the global tile ->
 // replica map; the tile fields of reps are overwritten.
@@ -640,10 +532,8 @@ int configure(misa_sim *s, int td, int tf)
     }
     if (s->smem_density > (size_t)optin || s->smem_force > (size_t)optin)
         return fail(s, MISA_EINVAL, "tile shape and table window exceed the shared memory of a block");
-    int arc = MISA_OK;
-    MISA_TILE_DISPATCH(T, td, attrs_density(s) == MISA_OK ? (void)0 : (void)(arc = MISA_ECUDA));
-    MISA_TILE_DISPATCH(T, tf, attrs_force(s) == MISA_OK ? (void)0 : (void)(arc = MISA_ECUDA));
-    if (arc) return fail(s, arc, s->err.empty() ? "tile kernel attributes" : s->err);
+    CK(tile_attrs<T>(td, false, tile_launch(s)));
+    CK(tile_attrs<T>(tf, true, tile_launch(s)));
     CK(cudaFuncSetAttribute(k_ra_sort<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)(sizeof(unsigned long long) * kSortMax)));
     if (s->graph) {
@@ -673,14 +563,14 @@ template <typename T>
 void launch_density(misa_sim *s, const GatherArgs<T> &g, bool energy)
 {
     const int grid = s->ntiles < s->nsm ? s->ntiles : s->nsm;
-    MISA_TILE_DISPATCH(T, s->tile, density(s, g, grid, energy));
+    tile_density<T>(s->tile, tile_launch(s), g, grid, energy);
 }
 
 template <typename T>
 void launch_force(misa_sim *s, const GatherArgs<T> &g, bool energy)
 {
     const int grid = s->ntiles_f < s->nsm ? s->ntiles_f : s->nsm;
-    MISA_TILE_DISPATCH(T, s->tile_f, force(s, g, grid, energy));
+    tile_force<T>(s->tile_f, tile_launch(s), g, grid, energy);
 }
 
 template <typename T>

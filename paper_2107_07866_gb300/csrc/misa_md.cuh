@@ -869,7 +869,7 @@ __global__ void k_sum_stage1(MdArgs<T> m, int kind, double *partial)
     }
 }
 
-__global__ void k_sum_stage2(const double *partial, int n, double *out)
+static __global__ void k_sum_stage2(const double *partial, int n, double *out)
 {
     __shared__ double sw[32];
     const double *pr = partial + (size_t)blockIdx.x * n;
