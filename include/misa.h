@@ -276,8 +276,11 @@ int misa_set_species(misa_sim *s, int n_species, const double *f_knots, const do
  * (Eq. eam_base for E, Eq. eam_force_ij for F).  grad (3 n_knots doubles,
  * host or device; may be NULL) receives d loss / d knot in the order f knots,
  * phi knots, F knots.  Pair arithmetic and the per-CTA shared-memory bins
- * in the handle's precision, one ordered FP64 reduction over CTAs.
- * Synchronises. */
+ * (5 n_knots values: the pair terms go to the values and slopes of their
+ * segment's end knots) in the handle's precision, one ordered FP64
+ * reduction over CTAs.  MISA_EINVAL for a handle with several species or
+ * when the bins exceed a block's shared memory (n_knots > 11622 for FP32,
+ * > 5811 for FP64).  Synchronises. */
 int misa_loss_grad(misa_sim *s, const double *Fref, const double *Eref, double *loss, double *grad);
 
 /* Number of built gather tile shapes, and the shape of each (cells). */

@@ -489,23 +489,22 @@ __device__ __forceinline__ void embed_bins(const AdjArgs<T> &a, T *bins, T rho, 
 // shared memory ([0, n) f values, [n, 2n) phi values, [2n, 3n) F knots, [3n,
 // 4n) f slopes, [4n, 5n) phi slopes), scatters its atoms' pair terms with
 // shared-memory atomics, then writes the bins to partial[cta][5n] (FP64)
-// FP32 bins in two copies, one per half warp: shared-memory FP32 atomics
-// that collide within a warp are several times slower than distinct ones
-template <typename T>
-constexpr int kBinCopies = sizeof(T) == 4 ? 2 : 1;
+// copies = 2: the bins in two copies, one per half warp (shared-memory FP32
+// atomics that collide within a warp are several times slower than distinct
+// ones); 1 when two copies do not fit.
 template <typename T>
 constexpr int kGradThreads = sizeof(T) == 4 ? 1024 : 256;
 
 template <typename T>
-__global__ void __launch_bounds__(kGradThreads<T>) k_adj_grad(AdjArgs<T> a, double *partial)
+__global__ void __launch_bounds__(kGradThreads<T>) k_adj_grad(AdjArgs<T> a, double *partial, int copies)
 {
     extern __shared__ __align__(16) unsigned char bin_smem[];
     const int r = blockIdx.y;
     const RepDesc rd = a.reps[r];
     const int nra = a.sc[r].n_ra;
     const int nb = 5 * a.n;
-    for (int k = threadIdx.x; k < kBinCopies<T> * nb; k += blockDim.x) reinterpret_cast<T *>(bin_smem)[k] = (T)0;
-    T *bins = reinterpret_cast<T *>(bin_smem) + (kBinCopies<T> == 2 && (threadIdx.x & 16) ? nb : 0);
+    for (int k = threadIdx.x; k < copies * nb; k += blockDim.x) reinterpret_cast<T *>(bin_smem)[k] = (T)0;
+    T *bins = reinterpret_cast<T *>(bin_smem) + (copies == 2 && (threadIdx.x & 16) ? nb : 0);
     __syncthreads();
     const double Nr = (double)rd.ns;
     const T ce = (T)(2.0 * (a.Etot[r] - a.Eref[r]) / (Nr * Nr));
@@ -532,7 +531,7 @@ __global__ void __launch_bounds__(kGradThreads<T>) k_adj_grad(AdjArgs<T> a, doub
     double *out = partial + ((size_t)r * gridDim.x + blockIdx.x) * nb;
     const T *b0 = reinterpret_cast<const T *>(bin_smem);
     for (int k = threadIdx.x; k < nb; k += blockDim.x)
-        out[k] = kBinCopies<T> == 2 ? (double)b0[k] + (double)b0[nb + k] : (double)b0[k];
+        out[k] = copies == 2 ? (double)b0[k] + (double)b0[nb + k] : (double)b0[k];
 }
 
 // grad[k] = sum over CTAs of partial[cta][k] in a fixed order: a block of

@@ -1218,6 +1218,10 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
     if (s->nsp > 1) return fail(s, MISA_EINVAL, "the knot gradient is built for one atom type");
     const int n = s->p.n_knots;
     const size_t capt = (size_t)s->cap * s->nrep;
+    // FP32: two bin copies per CTA when they fit, else one
+    const size_t bin_bytes = sizeof(T) * 5 * (size_t)n;
+    const int copies = sizeof(T) == 4 && 2 * bin_bytes <= 227u * 1024u ? 2 : 1;
+    if (bin_bytes > 227u * 1024u) return fail(s, MISA_EINVAL, "too many knots for the gradient bins");
     if (!s->dl) {
         for (int d = 0; d < 3; ++d) {
             s->lam[d] = dalloc(s, sizeof(T) * s->ns);
@@ -1236,11 +1240,8 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
         s->adj_fref = (double *)dalloc(s, sizeof(double) * 3 * s->ns);
         if (!s->dl || !s->ra_dl || !s->adj_partial || !s->adj_sum || !s->adj_grad || !s->adj_eref || !s->adj_fref)
             return fail(s, MISA_EOOM, "adjoint work arrays");
-        CK(cudaFuncSetAttribute(k_adj_grad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(T) * 5 * n * kBinCopies<T>)));
+        CK(cudaFuncSetAttribute(k_adj_grad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bin_bytes * copies)));
     }
-    if ((size_t)5 * n * sizeof(T) * kBinCopies<T> > 227u * 1024u)
-        return fail(s, MISA_EINVAL, "too many knots for the gradient bins");
     // forward: rho, F', E_i, forces of the current positions
     int rc = launch_forces<T>(s, 0, true);
     if (rc) return rc;
@@ -1293,8 +1294,8 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
     k_adj_lambda<T><<<dim3(nb, s->nrep), 256, 0, s->st>>>(a, s->partial);
     k_sum_stage2<<<s->nrep, 1024, 0, s->st>>>(s->partial, nb, s->red_out + s->nrep);  // sum |F - Fref|^2
     k_adj_dl<T><<<site_grid(s), 256, 0, s->st>>>(a);
-    k_adj_grad<T><<<dim3(s->adj_cta, s->nrep), kGradThreads<T>, sizeof(T) * 5 * n * kBinCopies<T>, s->st>>>(
-        a, s->adj_partial);
+    k_adj_grad<T><<<dim3(s->adj_cta, s->nrep), kGradThreads<T>, bin_bytes * copies, s->st>>>(a, s->adj_partial,
+                                                                                             copies);
     k_adj_reduce<<<(5 * n + 31) / 32, dim3(32, 8), 0, s->st>>>(s->adj_partial, s->adj_cta * s->nrep, 5 * n, s->adj_sum);
     k_adj_stencil<<<(3 * n + 255) / 256, 256, 0, s->st>>>(s->adj_sum, n, s->adj_grad);
     s->launches += 9;
