@@ -81,3 +81,18 @@ def test_create_rejects_bad_parameters_without_a_gpu(libmisa):
     with pytest.raises(misa.MisaError) as e:
         misa.Sim(pot, 8, skin=1.5, torch_memory=False)
     assert e.value.code == misa.MISA_EINVAL
+
+
+def test_build_covers_every_source():
+    # every CUDA translation unit under csrc/ is compiled, every header is a
+    # rebuild dependency (a stale library would be loaded otherwise)
+    import os
+    from paper_2107_07866_gb300 import build
+    csrc = os.path.join(build.PKG, "csrc")
+    units = {os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith(".cu")}
+    heads = {os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith(".cuh")}
+    assert units == set(build.SOURCES)
+    assert heads <= set(build.DEPS) and units <= set(build.DEPS)
+    for src in build.SOURCES:
+        cmd = build.compile_command(src, "x.o")
+        assert "-gencode=arch=compute_103a,code=sm_103a" in cmd and "-c" in cmd
