@@ -1,8 +1,9 @@
 """Batched replicas (Sec. 1 feature list: batch execution of simulations):
 several uneven boxes in one handle, every step kernel launched once for all
 of them.  A replica of a batch must evolve exactly as the same box alone
-(same kernels, same per-site sum order), and the captured step graph must
-reproduce the directly launched step."""
+(same kernels, same per-site sum order), the captured step graph must
+reproduce the directly launched step, and every replica of an uneven batch
+must follow the FP64 oracle's run of that box alone."""
 import numpy as np
 import pytest
 
@@ -114,3 +115,55 @@ def test_retune_changes_speed_not_results(misa, pot):
             out.append((s.positions(), s.forces()))
     np.testing.assert_array_equal(out[0][0], out[1][0])
     np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def _nerr(x, xo):
+    x, xo = np.asarray(x).reshape(len(x), -1), np.asarray(xo).reshape(len(xo), -1)
+    mag = np.linalg.norm(xo, axis=1)
+    rms = np.sqrt(np.mean(mag ** 2))
+    return float(np.max(np.linalg.norm(x - xo, axis=1) / np.maximum(mag, rms)))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_uneven_batch_matches_oracle_per_replica(misa, pot, oracle, opot, prec):
+    # four boxes of different dims in one handle, each with its own knock-on
+    # atom, run-aways (cascade snapshots) and adaptive timestep: every
+    # replica's trajectory is the oracle's MD run of that box alone, and the
+    # densities, energies and forces of its final state are the oracle's
+    reps = [(6, 7, 8), (9, 6, 6), (8, 8, 7), (7, 9, 6)]
+    ins = []
+    for k, d in enumerate(reps):
+        x = synth.cascade_snapshot(*d, 0.1, 4 + k, 1, 40 + k)
+        v = synth.maxwell_velocities(len(x), 300.0 + 150 * k, M, 40 + k)
+        oracle.insert_pka(v, synth.pka_atom(*d), M, 120.0 + 90.0 * k, synth.random_direction(50 + k))
+        ins.append((x, v))
+    steps = 40
+    with misa.Sim(pot, replicas=reps, precision=prec, dt_max=1.0, dx_max=0.02, reassign_period=3) as b:
+        b.set_state(np.concatenate([x for x, _ in ins]), np.concatenate([v for _, v in ins]))
+        ra0 = [b.replica_stats(r)["n_runaway"] for r in range(len(reps))]
+        b.step(steps)
+        xb, fb, rhob = b.positions(), b.forces(), b.density()
+        _, _, eb = b.energies(per_atom=True)
+        stb = [b.replica_stats(r) for r in range(len(reps))]
+        info = [b.replica_info(r) for r in range(len(reps))]
+    assert min(ra0) > 0
+    tol_x = 1e-8 if prec == "fp64" else 2e-5
+    for r, (d, (x0, v0)) in enumerate(zip(reps, ins)):
+        _, base, n = info[r]
+        L = synth.box(*d)
+        sl = slice(base, base + n)
+        xo, _, _, t, _ = oracle.md_run(opot, x0, v0, L, M, 1.0, 0.02, steps, mode=1)
+        dd = xb[sl] - xo
+        dd -= L * np.round(dd / L)
+        assert np.abs(dd).max() < tol_x, (r, np.abs(dd).max())
+        assert stb[r]["step"] == steps and stb[r]["status"] & 0x3 == 0
+        assert abs(stb[r]["time"] - t) < (1e-10 if prec == "fp64" else 1e-6), (r, stb[r]["time"], t)
+        rho_o, _, e_o, f_o = oracle.eam(opot, xb[sl], L, mode=1)
+        assert _nerr(fb[sl], f_o) < TOL[prec], (r, _nerr(fb[sl], f_o))
+        assert _nerr(rhob[sl], rho_o) < TOL[prec]
+        assert _nerr(eb[sl], e_o) < TOL[prec]
+    # the replicas took different timesteps
+    assert len({s_["time"] for s_ in stb}) == len(reps)

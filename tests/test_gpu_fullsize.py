@@ -31,7 +31,9 @@ TOL = {"fp64": 1e-12, "fp32": 1e-5}
 RUNS = {
     "300^3_fp32": dict(n=300, T=600.0, seed=2, pka=10000.0, reassign=10, prec="fp32", steps=30),
     "300^3_fp64": dict(n=300, T=600.0, seed=2, pka=10000.0, reassign=10, prec="fp64", steps=10),
-    "100^3_fp32": dict(n=100, T=600.0, seed=1, pka=5000.0, reassign=1, prec="fp32", steps=40),
+    "100^3_fp32": dict(n=100, T=600.0, seed=1, pka=5000.0, reassign=1, prec="fp32", steps=100),
+    # the 2M-atom cascade workload is FP64 first, then FP32 on the same inputs
+    "100^3_fp64": dict(n=100, T=600.0, seed=1, pka=5000.0, reassign=1, prec="fp64", steps=100),
 }
 
 
@@ -91,3 +93,51 @@ def test_sampled_parity_at_benchmark_size(misa, pot, oracle, opot, run):
     # the knock-on atom's neighbourhood is strongly perturbed: forces far
     # from the crystal's zero
     assert np.abs(f_o).max() > 0.1
+
+
+def test_sampled_parity_batched_replicas(misa, pot, oracle, opot):
+    # the batched workload as the benchmark runs it: 64 uneven replicas of
+    # 20^3-60^3 cells (9,558,686 atoms) at 300-900 K, a 1-5 keV knock-on atom
+    # each, FP32 forces, adaptive timestep per replica, autotuned tiles, hash
+    # update every 10 steps, steps from captured graphs.  After 20 steps six
+    # replicas are sampled (knock-on neighbourhood, run-aways, 200 random
+    # atoms each) and compared with the oracle on that replica's positions.
+    import math
+    reps = synth.batch_replicas(64, 4)
+    dims = [(r.nx, r.ny, r.nz) for r in reps]
+    xs, vs = [], []
+    for r in reps:
+        xs.append(synth.thermal_snapshot(r.nx, r.ny, r.nz, 0.1 * math.sqrt(r.T / 600.0), r.seed + 500))
+        vs.append(synth.maxwell_velocities(2 * r.nx * r.ny * r.nz, r.T, synth.MASS_FE, r.seed))
+    with misa.Sim(pot, replicas=dims, precision="fp32", dt_max=1.0, dx_max=0.02, reassign_period=10) as b:
+        b.set_state(np.concatenate(xs), np.concatenate(vs))
+        b.retune()
+        for k, r in enumerate(reps):
+            b.insert_pka_replica(k, r.pka_energy, r.pka_dir)
+        b.step(20)
+        x = b.positions()
+        f = b.forces()
+        rho = b.density()
+        _, _, e = b.energies(per_atom=True)
+        _, ra = b.site_map()
+        info = [b.replica_info(k) for k in range(len(reps))]
+        st = [b.replica_stats(k) for k in range(len(reps))]
+    assert all(s_["status"] & 0x3 == 0 and s_["step"] == 20 for s_ in st)
+    rng = np.random.default_rng(11)
+    worst = {}
+    for k in sorted(rng.choice(len(reps), 6, replace=False)):
+        d, base, n = info[k]
+        L = synth.box(*d)
+        xr = x[base:base + n]
+        pka = synth.pka_atom(*d)
+        dd = xr - xr[pka]
+        dd -= L * np.round(dd / L)
+        near = np.flatnonzero(np.einsum("ij,ij->i", dd, dd) < (synth.RC + 1.0) ** 2)
+        ra_k = ra[(ra >= base) & (ra < base + n)] - base
+        t = np.unique(np.concatenate([near, ra_k, rng.choice(n, 200, replace=False)]))
+        rho_o, e_o, f_o = oracle.eam_sample(opot, xr, L, t)
+        errs = (norm_err(rho[base + t], rho_o), norm_err(e[base + t], e_o), norm_err(f[base + t], f_o))
+        worst[int(k)] = max(errs)
+        assert np.abs(f_o).max() > 0.1
+    print(f"\n64 replicas: worst normalised error per sampled replica {worst}")
+    assert max(worst.values()) < TOL["fp32"], worst

@@ -351,3 +351,56 @@ def test_frenkel_pairs_match_oracle(misa, pot, oracle):
             counts.append(int(s.defects()[0]))
             assert nv == ni == counts[-1]
         assert max(counts) > 0
+
+
+def edge_snapshot(n=8, seed=13):
+    """A thermal crystal with the two edge readings of Sec. 2.2 built in:
+    one atom moved 5e-5 A from a lattice atom and two atoms 5e-5 A apart at
+    an octahedral interstitial point (pairs below r_floor = 1e-4 A: values at
+    r_floor, no force), and six atoms moved to 0.5 A around a lattice atom
+    along the axes (densities above rho_max: linear embedding tail).  The
+    moved atoms become run-aways and leave vacancies behind."""
+    x = synth.thermal_snapshot(n, n, n, 0.05, seed)
+    a0 = synth.A0_FE
+    rng = np.random.default_rng(seed)
+    movers = rng.choice(np.arange(2, len(x), 2), 9, replace=False)
+    host_a, host_c = 2 * (n * n * 2 + n * 2 + 2), 2 * (n * n * 5 + n * 5 + 5) + 1
+    assert host_a not in movers and host_c not in movers
+    x[movers[0]] = x[host_a] + 5e-5 * np.array([0.6, 0.0, 0.8])
+    octa = np.array([4.5, 4.0, 3.0]) * a0  # face centre of a cube: an octahedral site
+    x[movers[1]] = octa
+    x[movers[2]] = octa + 5e-5 * np.array([0.0, 0.8, 0.6])
+    for k, (d, s) in enumerate([(0, 1), (0, -1), (1, 1), (1, -1), (2, 1), (2, -1)]):
+        e = np.zeros(3)
+        e[d] = 0.5 * s
+        x[movers[3 + k]] = x[host_c] + e
+    return np.mod(x, synth.box(n, n, n)), (host_a, host_c, movers)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_edge_readings_against_oracle(misa, pot, oracle, opot, prec):
+    # the CUDA path leaves the plain formula in two places -- pairs closer
+    # than r_floor and densities above rho_max -- and must follow the
+    # oracle's readings there atom by atom, reporting both status bits
+    n = 8
+    x, (host_a, host_c, movers) = edge_snapshot(n)
+    L = synth.box(n, n, n)
+    rho_o, _, e_o, f_o = oracle.eam(opot, x, L, mode=1)
+    assert np.sum(rho_o > pot.rho_max) >= 7
+    with misa.Sim(pot, n, precision=prec) as s:
+        s.set_state(x)
+        f = s.forces()
+        rho = s.density()
+        _, _, e = s.energies(per_atom=True)
+        st = s.stats()
+    assert st["n_runaway"] >= 8
+    assert st["status"] & misa.ST_RFLOOR and st["status"] & misa.ST_RHO_EXTRAP
+    assert st["status"] & 0x3 == 0
+    assert nerr(f, f_o) < TOL[prec], nerr(f, f_o)
+    assert nerr(rho, rho_o) < TOL[prec], nerr(rho, rho_o)
+    assert nerr(e, e_o) < TOL[prec], nerr(e, e_o)
+    # the dimers' partners pull on nothing: the oracle's force on the two
+    # interstitials 5e-5 A apart is the crystal's alone, and the GPU agrees
+    # with it there to the same bound
+    sel = np.concatenate([[host_a, host_c], movers])
+    assert nerr(f[sel], f_o[sel]) < TOL[prec]
