@@ -141,12 +141,16 @@ class ClockSampler:
 
 WORKLOADS = {
     # headline: the 54M-atom FP32-force cascade
-    "c3": dict(n=300, T=600.0, seed=2, pka_eV=10000.0, dx_max=0.02, reassign=10,
+    "c3": dict(n=300, T=600.0, seed=2, pka_eV=10000.0, dx_max=0.02, reassign=10, run_length=500,
                desc="300x300x300 cells (54,000,000 atoms), equilibrated at 600 K (seed 2), 10 keV PKA, FP32 forces, "
-                    "adaptive dt (1 fs, 0.02 A), hash update every 10 steps"),
+                    "adaptive dt (1 fs, 0.02 A), hash update every 10 steps; the timed steps end at step 500, the "
+                    "cascade's run length"),
     # smaller cascade (parity-size check of the bench path)
-    "c2": dict(n=100, T=600.0, seed=1, pka_eV=5000.0, dx_max=0.02, reassign=1,
-               desc="100x100x100 cells (2,000,000 atoms), equilibrated at 600 K (seed 1), 5 keV PKA, adaptive dt, hash update every step"),
+    "c2": dict(n=100, T=600.0, seed=1, pka_eV=5000.0, dx_max=0.02, reassign=1, checkpoints=(0, 100),
+               fp64_full=True,
+               desc="100x100x100 cells (2,000,000 atoms), equilibrated at 600 K (seed 1), 5 keV PKA, adaptive dt, "
+                    "hash update every step; FP32 and FP64 paths over the same steps from the same inputs, oracle "
+                    "error at steps 0, 100 and the last (run with --steps 1000 for the configuration's length)"),
     # batched cascades: 64 uneven replicas in one handle, one launch per pass
     "c4": dict(n=None, nrep=64, seed=4, dx_max=0.02, reassign=10,
                desc="64 batched replicas, dims ~ U{20..60}^3 cells (seeded), equilibrated at 300-900 K, 1-5 keV PKA each, "
@@ -486,6 +490,111 @@ def run_adjoint(args):
     return 0
 
 
+def norm_err(x, xo):
+    """max_i |X_i - X_i^o| / max(|X_i^o|, rms |X^o|), the error norm of the
+    parity tests (per-atom vectors or scalars)."""
+    x = np.asarray(x, dtype=np.float64).reshape(len(x), -1)
+    xo = np.asarray(xo, dtype=np.float64).reshape(len(xo), -1)
+    mag = np.linalg.norm(xo, axis=1)
+    rms = float(np.sqrt(np.mean(mag * mag))) if len(mag) else 0.0
+    return float(np.max(np.linalg.norm(x - xo, axis=1) / np.maximum(mag, max(rms, 1e-300)))) if len(mag) else 0.0
+
+
+def oracle_error(sim, pot, w, alloy=None, types=None, n_random=400, seed=7):
+    """Error of the current state's densities, per-atom energies and forces
+    against the FP64 oracle on the same positions, outside any timed region.
+    Single boxes: the knock-on atom's neighbourhood (rc + 1 A), every
+    run-away and n_random seeded atoms, evaluated one by one by the oracle;
+    alloys: every atom (the oracle's alloy evaluation); batches: four seeded
+    replicas, sampled the same way."""
+    from oracle import oracle as O
+    O.build()
+    x = sim.positions()
+    f = sim.forces()
+    rho = sim.density()
+    _, _, e = sim.energies(per_atom=True)
+    _, ra = sim.site_map()
+    rng = np.random.default_rng(seed)
+    if alloy is not None:
+        L = synth.box(*sim.replicas[0])
+        r_o, _, e_o, f_o = O.eam_alloy(O.Alloy(alloy), x, types, L, mode=1)
+        return {"rho": norm_err(rho, r_o), "E": norm_err(e, e_o), "F": norm_err(f, f_o),
+                "atoms": len(x), "sample": "every atom"}
+    op = O.Pot(pot)
+    boxes = list(range(len(sim.replicas)))
+    if len(boxes) > 1:
+        boxes = sorted(int(b) for b in rng.choice(len(boxes), 4, replace=False))
+    errs = {"rho": 0.0, "E": 0.0, "F": 0.0}
+    count = 0
+    for r in boxes:
+        d, base, n = sim.replica_info(r)
+        L = synth.box(*d)
+        xr = x[base:base + n]
+        pka = synth.pka_atom(*d)
+        dd = xr - xr[pka]
+        dd -= L * np.round(dd / L)
+        near = np.flatnonzero(np.einsum("ij,ij->i", dd, dd) < (synth.RC + 1.0) ** 2)
+        ra_r = ra[(ra >= base) & (ra < base + n)] - base
+        t = np.unique(np.concatenate([near, ra_r, rng.choice(n, min(n, n_random), replace=False)]))
+        r_o, e_o, f_o = O.eam_sample(op, xr, L, t)
+        errs["rho"] = max(errs["rho"], norm_err(rho[base + t], r_o))
+        errs["E"] = max(errs["E"], norm_err(e[base + t], e_o))
+        errs["F"] = max(errs["F"], norm_err(f[base + t], f_o))
+        count += len(t)
+    errs["atoms"] = count
+    errs["sample"] = ("knock-on neighbourhood (rc + 1 A), every run-away, "
+                      f"{n_random} seeded atoms" + (f" in each of replicas {boxes}" if len(boxes) > 1 else ""))
+    return errs
+
+
+def run_timed(sim, stream, pre, K, checkpoints, sample):
+    """pre untimed steps, then K steps timed with CUDA events on the
+    library's stream, split at the checkpoint steps (absolute step counts)
+    where sample(step) records the oracle error outside the timed region.
+    Returns the summed device time (ms) of the K steps and the kernels the
+    library launched for them."""
+    import torch
+    step0 = sim.stats()["step"]
+    done = 0
+    cps = sorted(set(int(c) for c in checkpoints))
+
+    def advance(n):
+        nonlocal done
+        while n > 0:
+            nxt = [c - (step0 + done) for c in cps if c - (step0 + done) > 0]
+            k = min([n] + nxt)
+            sim.step(k)
+            done += k
+            n -= k
+            if step0 + done in cps:
+                sample(step0 + done)
+
+    if step0 in cps:
+        sample(step0)
+    advance(pre)
+    torch.cuda.synchronize()
+    total = 0.0
+    launches = 0
+    remaining = K
+    while remaining > 0:
+        nxt = [c - (step0 + done) for c in cps if c - (step0 + done) > 0]
+        k = min([remaining] + nxt)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = sim.stats()["launches"]
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+        launches += sim.stats()["launches"] - l0
+        done += k
+        remaining -= k
+        if step0 + done in cps:
+            sample(step0 + done)
+    return total, launches
+
+
 def run_gpu(args):
     import torch
 
@@ -496,6 +605,10 @@ def run_gpu(args):
     from paper_2107_07866_gb300 import misa
 
     w = WORKLOADS[args.workload]
+    # issue-rate microbenchmarks of this device: the arithmetic roofline's
+    # denominators (run before anything else, outside any timed region)
+    peaks = misa.measure_peaks()
+    fp32_peak = max(peaks["fp32_ffma_tflops"], peaks["fp32_ffma2_tflops"])
     pot = synth.potential()
     alloy = types = None
     if w.get("nsp"):
@@ -535,28 +648,34 @@ def run_gpu(args):
         s.insert_pka(-1, w["pka_eV"], d)
         return s
 
+    want_err = rank == 0 and not args.no_oracle_err
+
     # ---- FP32-force path: the timed value ---------------------------------
+    # The timed K steps end at the workload's run length (the C3 cascade is
+    # timed at the state its 500 steps reach: untimed steps before it); the
+    # oracle error is taken at the checkpoint steps, outside the timed time.
     sim = fresh("fp32")
     tile_used = sim.tile()
     tile_force = sim.tile_force()
-    sim.step(args.warmup)
-    torch.cuda.synchronize()
-    st0 = sim.stats()
-    launches0 = st0["launches"]
+    run_length = w.get("run_length", 0)
+    pre = max(args.warmup, run_length - args.steps)
+    checkpoints = [pre + args.steps] + [c for c in w.get("checkpoints", ()) if c <= pre + args.steps]
+    errs32 = {}
+
+    def sample32(step):
+        if want_err:
+            errs32[str(step)] = oracle_error(sim, pot, w, alloy, types)
+
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # timed region: the steps as a user runs them (one captured graph per step)
     with ClockSampler(local) as clk:
         barrier(ws)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        sim.step(args.steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
+        el_ms, gpu_launches = run_timed(sim, stream, pre, args.steps,
+                                        [c for c in checkpoints if c < pre + args.steps] + [-1], sample32)
         barrier(ws)
-    el_ms = e0.elapsed_time(e1)
     st1 = sim.stats()
-    gpu_launches = st1["launches"] - launches0
+    if want_err:
+        errs32[str(st1["step"])] = oracle_error(sim, pot, w, alloy, types)
+    clocks = clk.summary()
     # per-phase device time (events between the launches; separate, shorter run)
     sim.timing(True)
     sim.step(max(3, min(args.steps, 10)))
@@ -564,7 +683,6 @@ def run_gpu(args):
     sim.timing(False)
     el_max = barrier_max(ws, el_ms)
     value = natoms * ws * args.steps / (el_max / 1e3)
-    clocks = clk.summary()
 
     # roofline of the dominant kernel (force pass) measured inside the timed region
     t_force = phases["force"] / max(nsteps, 1) / 1e3
@@ -573,24 +691,26 @@ def run_gpu(args):
     traffic = None
     if NCU_FORCE_TRAFFIC["source_sha"] == kernel_source_sha() and args.workload == "c3":
         traffic = NCU_FORCE_TRAFFIC["bytes_per_launch"]  # captured on this workload only
-    peaks = measured_peaks()
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    mp = measured_peaks()
+    hbm_peak = mp.get("hbm_gbs", 6800.0)
     step_s = el_ms / 1e3 / args.steps
     sha = kernel_source_sha()
     l1 = None
     if NCU_WAVEFRONTS["source_sha"] == sha and alloy is None and not batched:
         # per-site wavefronts of the single-box crystal (2M-atom capture); not
-        # carried over to the batch of small boxes
-        # one L1 data-pipe wavefront per SM per clock at the sampled SM clock
-        clk_hz = (clocks.get("sm_mhz") or 2070.0) * 1e6
-        pipe = 152 * clk_hz
+        # carried over to the batch of small boxes; the shared-memory pipe's
+        # rate measured on this device (conflict-free 16-byte loads: four
+        # wavefronts each)
+        lds_wf = peaks["lds128_tbps"] * 1e12 / 16.0 * 4.0 / 32.0
         l1 = {k: {"lsu_wavefronts_per_site": NCU_WAVEFRONTS[k][0], "tex_wavefronts_per_site": NCU_WAVEFRONTS[k][1],
-                  "lsu_frac": NCU_WAVEFRONTS[k][0] * natoms / (t * pipe)}
+                  "lsu_frac": NCU_WAVEFRONTS[k][0] * natoms / (t * lds_wf)}
               for k, t in (("density", t_dens), ("force", t_force))}
     kname = "k_force_p (force pass)" if alloy is None else "k_force_pa (alloy force pass; flops counted as for one type)"
-    roofline = {"bound": "alu", "kernel": kname, "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "peak_note": "FP32 FMA issue peak: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, not measured)",
+    roofline = {"bound": "alu", "kernel": kname, "achieved": ach, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": traffic,
+                "peak_note": "measured on this device by misa_measure_peaks: the faster of scalar FP32 FMA "
+                             f"({peaks['fp32_ffma_tflops']:.1f}) and packed FP32x2 FMA "
+                             f"({peaks['fp32_ffma2_tflops']:.1f} TFLOP/s) at {peaks['sm_clock_mhz']:.0f} MHz",
                 "algorithmic_flops_per_site": FLOPS_FORCE_SITE,
                 "force_ms": 1e3 * t_force, "density_ms": 1e3 * t_dens,
                 "density_tflops": FLOPS_DENS_SITE * natoms / t_dens / 1e12,
@@ -599,7 +719,7 @@ def run_gpu(args):
                              "peak_gbs": hbm_peak, "frac": BYTES_STEP_FP32 * natoms / step_s / 1e9 / hbm_peak,
                              "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json)"},
                 "phase_ms_per_step": {k: v_ / max(nsteps, 1) for k, v_ in phases.items()},
-                "l1_data_pipe": l1, "kernel_source_sha": sha}
+                "l1_data_pipe": l1, "kernel_source_sha": sha, "measured_peaks": peaks}
     stats_end = sim.stats()
     frenkel = [int(c) for c in sim.defects()]
     sim.close()
@@ -619,27 +739,33 @@ def run_gpu(args):
         spd = math.sqrt(2.0 * w["pka_eV"] / synth.MASS_FE / synth.EV_PER_AMU_A2_FS2)
         v0[pka] = spd * d
         v_host = torch.from_numpy(v0).pin_memory()
+        e_host = torch.empty(natoms, dtype=torch.float64).pin_memory()
         inner = w["reassign"]
-        iters = max(1, args.e2e_iters)
+        iters = max(10, args.e2e_iters)
         s.stage_state(x_host, v_host)
         s.set_state_staged()
         s.step(inner)
-        s.stats()
+        s.energies(per_atom=True)
         torch.cuda.synchronize()
         barrier(ws)
         t0 = time.perf_counter()
         s.stage_state(x_host, v_host)            # H2D of the first state
+        pe_sum = 0.0
         for it in range(iters):
             s.set_state_staged()
             if it + 1 < iters:
                 s.stage_state(x_host, v_host)    # H2D of the next state, beside this one's steps
             s.step(inner)
-            s.stats()                            # D2H: step, time, dt, run-away count, status
+            # D2H: per-atom energies E_i (and the totals) of the state reached
+            pe, _, _ = s.energies(per_atom=True, out=e_host.numpy())
+            pe_sum += pe
         torch.cuda.synchronize()
         el = barrier_max(ws, time.perf_counter() - t0)
         e2e = {"value": natoms * ws * inner * iters / el, "unit": UNIT,
-               "h2d_bytes_per_step": 48 * natoms, "d2h_bytes_per_step": 80,
-               "note": f"one e2e step = state (x, v) from pinned host memory + {inner} MD steps + stats read-back; "
+               "h2d_bytes_per_step": 48 * natoms, "d2h_bytes_per_step": 8 * natoms + 16,
+               "iterations": iters,
+               "note": f"one e2e step = state (x, v) from pinned host memory + {inner} MD steps + the per-atom "
+                       "energies E_i of the state reached back to pinned host memory (an energy evaluation); "
                        "each state is staged on the library's copy stream while the previous one is simulated"}
         s.close()
         del s
@@ -649,16 +775,32 @@ def run_gpu(args):
     fp64 = None
     if not args.no_fp64:
         s = fresh("fp64")
-        s.step(1)
-        torch.cuda.synchronize()
-        k64 = args.fp64_steps
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        s.step(k64)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        el64 = a0.elapsed_time(a1)
-        fp64 = {"value": natoms * k64 / (el64 / 1e3), "unit": UNIT, "steps": k64, "ms_per_step": el64 / k64}
+        errs64 = {}
+
+        def sample64(step):
+            if want_err:
+                errs64[str(step)] = oracle_error(s, pot, w, alloy, types)
+
+        k64 = args.fp64_steps if not w.get("fp64_full") else args.steps
+        pre64 = 1 if not w.get("fp64_full") else pre
+        cps64 = [c for c in w.get("checkpoints", ()) if w.get("fp64_full") and c < pre64 + k64] + [-1]
+        with ClockSampler(local) as clk64:
+            el64, _ = run_timed(s, stream, pre64, k64, cps64, sample64)
+        if want_err:
+            errs64[str(s.stats()["step"])] = oracle_error(s, pot, w, alloy, types)
+        s.timing(True)
+        s.step(1 if not w.get("fp64_full") else 3)
+        ph64, n64 = s.timing_get()
+        s.timing(False)
+        t_gather = (ph64["density"] + ph64["force"]) / max(n64, 1) / 1e3
+        ach64 = (FLOPS_DENS_SITE + FLOPS_FORCE_SITE) * natoms / t_gather / 1e12
+        fp64 = {"value": natoms * k64 / (el64 / 1e3), "unit": UNIT, "steps": k64, "ms_per_step": el64 / k64,
+                "start_step": pre64, "clocks": clk64.summary(),
+                "fp64_pipe": {"kernels": "k_density + k_force (FP64 gathers)", "achieved_tflops": ach64,
+                              "peak_tflops": peaks["fp64_dfma_tflops"], "frac": ach64 / peaks["fp64_dfma_tflops"],
+                              "flops_per_site": FLOPS_DENS_SITE + FLOPS_FORCE_SITE,
+                              "peak_note": "FP64 FMA issue rate measured on this device (misa_measure_peaks)"},
+                "oracle_err": errs64 or None}
         s.close()
         del s
         torch.cuda.empty_cache()
@@ -673,9 +815,11 @@ def run_gpu(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": w["desc"], "atoms": natoms, "parallelism": f"replicas{ws}",
                            "cache": f"state ~{148 * natoms / 1e9:.1f} GB >> 129 MB L2 (no flush needed)",
+                           "timed_steps": [pre, pre + args.steps],
                            "tile": list(tile_used), "tile_force": list(tile_force)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "clocks": clocks, "fp64_path": fp64,
+                "oracle_err": errs32 or None,
                 "end_state": {"step": stats_end["step"], "time_fs": stats_end["time"],
                               "n_runaway": stats_end["n_runaway"], "status": stats_end["status"],
                               "frenkel_pairs": sum(frenkel)}}
@@ -693,12 +837,14 @@ def main():
     ap.add_argument("--tile", type=int, default=0,
                     help="pin both gathers to tile shape K (1-based, see misa.tile_shapes()); 0: autotune")
     ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--e2e-iters", type=int, default=3)
+    ap.add_argument("--e2e-iters", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-cells", type=int, default=24)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-oracle-err", action="store_true",
+                    help="skip the oracle error of the benchmarked states (taken outside the timed region)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -331,6 +331,34 @@ int misa_defects(misa_sim *s, int64_t *n_frenkel);
  * graph; synchronises. */
 int misa_retune(misa_sim *s);
 
+/* Issue-rate microbenchmarks of the current device (no counterpart in the
+ * paper): the denominators of the arithmetic rooflines of the gathers and of
+ * the FP64 path, measured rather than derived from unit counts and the
+ * clock.  Each figure is the best of five timed launches (CUDA events on
+ * `stream`, NULL = default stream) of a kernel that fills every warp slot of
+ * every SM with independent dependency chains of one instruction:
+ *   fp32_ffma_tflops    scalar FP32 FMA (2 flops each)
+ *   fp32_ffma2_tflops   packed FP32x2 FMA (4 flops each)
+ *   fp64_dfma_tflops    FP64 FMA (2 flops each)
+ *   mufu_rsqrt_tops     approximate reciprocal square roots (1e12 per s)
+ *   lds128_tbps         conflict-free 16-byte shared-memory loads (TB/s)
+ *   sm_clock_mhz        SM clock during the FP32 probe (clock64 against the
+ *                       global timer in one CTA)
+ *   num_sms             multiprocessors of the device
+ * Runs on the current device for ~0.2 s; changes no device setting;
+ * synchronises the stream.  MISA_EINVAL for a null pointer, MISA_ECUDA on a
+ * CUDA error. */
+typedef struct misa_peaks {
+    double fp32_ffma_tflops;
+    double fp32_ffma2_tflops;
+    double fp64_dfma_tflops;
+    double mufu_rsqrt_tops;
+    double lds128_tbps;
+    double sm_clock_mhz;
+    int32_t num_sms;
+} misa_peaks;
+int misa_measure_peaks(misa_peaks *out, void *stream);
+
 /* Allocation-free force evaluation (the paper has no counterpart; it exists
  * for callers that must not allocate device memory).
  *
@@ -349,7 +377,10 @@ int misa_retune(misa_sim *s);
  *   nx, ny, nz    box in cubic bcc cells (each >= 6); natoms = 2 nx ny nz
  *                 must not exceed MISA_STATIC_MAX_ATOMS
  *   a0, rc, skin  as in misa_params
- *   n_knots       knots per table, 8 .. MISA_STATIC_MAX_KNOTS
+ *   n_knots       knots per table, 8 .. MISA_STATIC_MAX_KNOTS (the FP32 path
+ *                 keeps the reachable part of a table in shared memory beside
+ *                 one 8x8x8-cell tile: up to 8192 knots fit a GB300 block;
+ *                 a window that does not fit returns MISA_EINVAL)
  *   knots         DEVICE pointer, 3 n_knots doubles: f, phi, F knot values
  *                 (same grids as misa_params)
  *   rho_max       end of the embedding table

@@ -1,10 +1,11 @@
 """Builds the CUDA library (libmisa.so) in-tree for sm_103a with nvcc.
 
-Five translation units compiled in parallel and linked into one shared
+Six translation units compiled in parallel and linked into one shared
 library: the host runtime with the MD, adjoint and per-site alloy kernels
 (``misa_api.cu``), the FP32 tile gathers split by tile shape over three
-units (``misa_tiles_f32_{a,b,c}.cu``) and the FP64 tile gathers
-(``misa_tiles_f64.cu``).  ``python -m
+units (``misa_tiles_f32_{a,b,c}.cu``), the FP64 tile gathers
+(``misa_tiles_f64.cu``) and the issue-rate microbenchmarks
+(``misa_probe.cu``).  ``python -m
 paper_2107_07866_gb300.build`` or ``build()``.
 """
 from __future__ import annotations
@@ -19,7 +20,7 @@ ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libmisa.so")
 OBJDIR = os.path.join(PKG, "_build")
 SOURCES = [os.path.join(PKG, "csrc", f) for f in ("misa_tiles_f32_a.cu", "misa_tiles_f32_b.cu", "misa_tiles_f32_c.cu",
-                                                   "misa_api.cu", "misa_tiles_f64.cu")]
+                                                   "misa_api.cu", "misa_tiles_f64.cu", "misa_probe.cu")]
 DEPS = SOURCES + sorted(os.path.join(PKG, "csrc", f) for f in os.listdir(os.path.join(PKG, "csrc"))
                         if f.endswith(".cuh")) + [os.path.join(ROOT, "include", "misa.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"

@@ -2025,8 +2025,8 @@ extern "C" int misa_eam_forces_static(int32_t nx, int32_t ny, int32_t nz, double
     s.reps[0].ns = ns;
     s.reps[0].cap = s.cap;
     s.ntile_cap = ns / 2;
-    cudaDeviceGetAttribute(&s.nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (s.nsm <= 0) s.nsm = 1;
+    if (cudaDeviceGetAttribute(&s.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || s.nsm <= 0)
+        return fail(none, MISA_ECUDA, "static forces: cannot read the multiprocessor count of the device");
     size_t used = precision == MISA_FP64 ? carve_static<double>(&s, (unsigned char *)base, n_knots)
                                          : carve_static<float>(&s, (unsigned char *)base, n_knots);
     if (used > MISA_STATIC_SCRATCH_BYTES) return fail(none, MISA_EINVAL, "static forces: scratch layout exceeds the array");

@@ -62,6 +62,14 @@ class Stats(C.Structure):
     ]
 
 
+class Peaks(C.Structure):
+    _fields_ = [
+        ("fp32_ffma_tflops", C.c_double), ("fp32_ffma2_tflops", C.c_double), ("fp64_dfma_tflops", C.c_double),
+        ("mufu_rsqrt_tops", C.c_double), ("lds128_tbps", C.c_double), ("sm_clock_mhz", C.c_double),
+        ("num_sms", C.c_int32),
+    ]
+
+
 PHASES = ("kick_drift", "list", "density", "ra_density", "force", "ra_force", "end")
 
 
@@ -121,6 +129,7 @@ def lib():
         L.misa_tile_valid.argtypes = [C.c_int, C.c_int]
         L.misa_selftest.argtypes = [C.c_longlong, C.POINTER(C.c_longlong)]
         L.misa_tile_shape.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.misa_measure_peaks.argtypes = [C.POINTER(Peaks), C.c_void_p]
         _lib = L
     return _lib
 
@@ -281,9 +290,11 @@ class Sim:
         self._check(lib().misa_step(self.h, int(n)))
 
     # -- read-out -----------------------------------------------------------
-    def energies(self, per_atom=False):
+    def energies(self, per_atom=False, out=None):
+        """Total potential and kinetic energy (eV); with per_atom also E_i of
+        every atom (into out, a float64 array of natoms, when given)."""
         pe, ke = C.c_double(), C.c_double()
-        e = np.empty(self.natoms) if per_atom else None
+        e = (np.empty(self.natoms) if out is None else out) if per_atom else None
         self._check(lib().misa_get_energies(self.h, C.byref(pe), C.byref(ke), _ptr(e)))
         return (pe.value, ke.value, e) if per_atom else (pe.value, ke.value)
 
@@ -434,6 +445,24 @@ def selftest(n=1 << 22):
     if code != MISA_OK:
         raise MisaError(code, "misa_selftest failed")
     return int(out[0]), int(out[1]), int(out[2])
+
+
+def measure_peaks(stream=None) -> dict:
+    """Issue-rate microbenchmarks of the current device (misa_measure_peaks):
+    FP32 FMA, packed FP32x2 FMA and FP64 FMA in TFLOP/s, MUFU reciprocal
+    square roots in 1e12/s, conflict-free 16-byte shared-memory loads in
+    TB/s, the SM clock during the FP32 probe, the SM count."""
+    if stream is None:
+        try:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        except Exception:
+            stream = None
+    p = Peaks()
+    code = lib().misa_measure_peaks(C.byref(p), C.c_void_p(stream) if stream else None)
+    if code != MISA_OK:
+        raise MisaError(code, "misa_measure_peaks failed")
+    return {k: getattr(p, k) for k, _ in Peaks._fields_}
 
 
 def tile_indices(precision):

@@ -53,6 +53,9 @@ def test_struct_layouts_match_header():
         if decl:
             sfields += [n.strip() for n in decl.split(None, 1)[1].split(",")]
     assert [f for f, _ in misa.Stats._fields_] == sfields
+    pk = re.search(r"typedef struct misa_peaks \{(.*?)\} misa_peaks;", src, re.S).group(1)
+    pfields = [d.strip().split()[-1] for d in pk.split(";") if d.strip()]
+    assert [f for f, _ in misa.Peaks._fields_] == pfields
 
 
 def test_tile_shapes_are_warp_parity_pure(libmisa):

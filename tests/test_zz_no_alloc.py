@@ -81,3 +81,78 @@ def test_static_entry_rejects_oversized_input(env):
             x.data_ptr(), x.data_ptr(), None, None)
     assert rc == misa.MISA_EINVAL
     assert b"exceed" in misa.lib().misa_last_error(None)
+
+
+def _static_call(torch, misa, fn, pot, dims, prec, xh):
+    natoms = 2 * dims[0] * dims[1] * dims[2]
+    knots = torch.from_numpy(np.concatenate([pot.f, pot.phi, pot.F])).cuda()
+    x = torch.from_numpy(xh).cuda()
+    f_out = torch.empty((natoms, 3), dtype=torch.float64, device="cuda")
+    e_out = torch.empty(natoms, dtype=torch.float64, device="cuda")
+    code = misa.FP64 if prec == "fp64" else misa.FP32_FORCE
+    torch.cuda.synchronize()
+    rc = fn(*dims, synth.A0_FE, pot.rc, 0.6, pot.n, knots.data_ptr(), pot.rho_max, code, x.data_ptr(),
+            f_out.data_ptr(), e_out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    return rc, f_out, e_out
+
+
+def _handle(misa, pot, dims, prec, xh):
+    with misa.Sim(pot, *dims, precision=prec) as s:
+        s.set_state(xh)
+        f = s.forces()
+        _, _, e = s.energies(per_atom=True)
+    return f, e
+
+
+def test_static_entry_larger_fp64_box_then_smaller_fp32_box(env):
+    # the second call lays its buffers out differently in the shared array
+    # (other box, other precision): nothing of the first call may leak in
+    torch, misa, fn = env
+    pot = synth.potential()
+    for dims, prec, seed in (((14, 12, 10), "fp64", 5), ((8, 7, 6), "fp32", 6), ((14, 12, 10), "fp32", 7)):
+        xh = synth.cascade_snapshot(*dims, 0.12, 6, 2, seed)
+        rc, f_out, e_out = _static_call(torch, misa, fn, pot, dims, prec, xh)
+        assert rc == misa.MISA_OK, misa.lib().misa_last_error(None)
+        f_ref, e_ref = _handle(misa, pot, dims, prec, xh)
+        assert nerr(f_out.cpu().numpy(), f_ref) < TOL[prec], (dims, prec)
+        assert nerr(e_out.cpu().numpy(), e_ref) < TOL[prec], (dims, prec)
+
+
+def test_static_entry_allocates_no_device_memory(env):
+    # after a first call of the same precision (which loads its kernels),
+    # a call leaves the device's free memory exactly as it found it
+    torch, misa, fn = env
+    pot = synth.potential()
+    dims = (10, 9, 8)
+    xh = synth.cascade_snapshot(*dims, 0.1, 4, 1, 9)
+    natoms = 2 * dims[0] * dims[1] * dims[2]
+    knots = torch.from_numpy(np.concatenate([pot.f, pot.phi, pot.F])).cuda()
+    x = torch.from_numpy(xh).cuda()
+    f_out = torch.empty((natoms, 3), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for prec in ("fp32", "fp64"):
+        code = misa.FP64 if prec == "fp64" else misa.FP32_FORCE
+        args = (*dims, synth.A0_FE, pot.rc, 0.6, pot.n, knots.data_ptr(), pot.rho_max, code, x.data_ptr(),
+                f_out.data_ptr(), None, stream)
+        assert fn(*args) == misa.MISA_OK
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        assert fn(*args) == misa.MISA_OK
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0, (prec, free0 - free1)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_static_entry_at_the_knot_limit(env, prec):
+    # MISA_STATIC_MAX_KNOTS knots per table: the FP32 table window still fits
+    # beside the tile in a block's shared memory
+    torch, misa, fn = env
+    pot = synth.potential(n=8192)
+    dims = (7, 6, 6)
+    xh = synth.cascade_snapshot(*dims, 0.1, 3, 1, 12)
+    rc, f_out, e_out = _static_call(torch, misa, fn, pot, dims, prec, xh)
+    assert rc == misa.MISA_OK, misa.lib().misa_last_error(None)
+    f_ref, e_ref = _handle(misa, pot, dims, prec, xh)
+    assert nerr(f_out.cpu().numpy(), f_ref) < TOL[prec]
+    assert nerr(e_out.cpu().numpy(), e_ref) < TOL[prec]
