@@ -147,7 +147,7 @@ WORKLOADS = {
                     "cascade's run length"),
     # smaller cascade (parity-size check of the bench path)
     "c2": dict(n=100, T=600.0, seed=1, pka_eV=5000.0, dx_max=0.02, reassign=1, checkpoints=(0, 100),
-               fp64_full=True,
+               fp64_full=True, ra_scan=True,
                desc="100x100x100 cells (2,000,000 atoms), equilibrated at 600 K (seed 1), 5 keV PKA, adaptive dt, "
                     "hash update every step; FP32 and FP64 paths over the same steps from the same inputs, oracle "
                     "error at steps 0, 100 and the last (run with --steps 1000 for the configuration's length)"),
@@ -698,12 +698,13 @@ def run_gpu(args):
     l1 = None
     if NCU_WAVEFRONTS["source_sha"] == sha and alloy is None and not batched:
         # per-site wavefronts of the single-box crystal (2M-atom capture); not
-        # carried over to the batch of small boxes; the shared-memory pipe's
-        # rate measured on this device (conflict-free 16-byte loads: four
-        # wavefronts each)
-        lds_wf = peaks["lds128_tbps"] * 1e12 / 16.0 * 4.0 / 32.0
+        # carried over to the batch of small boxes; ncu's peak of the shared-
+        # memory data pipe is one wavefront per SM per clock (at the sampled
+        # SM clock)
+        clk_hz = (clocks.get("sm_mhz") or 2070.0) * 1e6
+        pipe = peaks["num_sms"] * clk_hz
         l1 = {k: {"lsu_wavefronts_per_site": NCU_WAVEFRONTS[k][0], "tex_wavefronts_per_site": NCU_WAVEFRONTS[k][1],
-                  "lsu_frac": NCU_WAVEFRONTS[k][0] * natoms / (t * lds_wf)}
+                  "lsu_frac": NCU_WAVEFRONTS[k][0] * natoms / (t * pipe)}
               for k, t in (("density", t_dens), ("force", t_force))}
     kname = "k_force_p (force pass)" if alloy is None else "k_force_pa (alloy force pass; flops counted as for one type)"
     roofline = {"bound": "alu", "kernel": kname, "achieved": ach, "peak": fp32_peak,
@@ -726,6 +727,31 @@ def run_gpu(args):
     del sim
     torch.cuda.empty_cache()
 
+    # ---- run-away load: per-phase times of the same box with 10^2..10^4
+    # interstitial atoms (a developed cascade's run-away count) -------------
+    ra_load = None
+    if w.get("ra_scan") and not args.no_ra_scan:
+        ra_load = []
+        for nint in (100, 1000, 10000):
+            s = misa.Sim(pot, n, precision="fp32", dt_max=1.0, dx_max=w["dx_max"], reassign_period=w["reassign"],
+                         tile=args.tile, runaway_capacity=16384)
+            xi = synth.interstitial_snapshot(n, n, n, thermal_sigma(w["T"]), nint, w["seed"] + 900)
+            s.set_state(xi, v)
+            if not args.tile:
+                s.retune()
+            s.step(3)
+            s.timing(True)
+            s.step(10)
+            ph, ns_ = s.timing_get()
+            s.timing(False)
+            st_ = s.stats()
+            ra_load.append({"interstitials": nint, "n_runaway": st_["n_runaway"], "status": st_["status"],
+                            "ms_per_step": sum(ph.values()) / ns_,
+                            "phase_ms_per_step": {k: v_ / ns_ for k, v_ in ph.items()}})
+            s.close()
+            del s
+            torch.cuda.empty_cache()
+
     # ---- e2e through the C ABI with host buffers ----------------------------
     e2e = None
     if not args.no_e2e:
@@ -740,7 +766,7 @@ def run_gpu(args):
         v0[pka] = spd * d
         v_host = torch.from_numpy(v0).pin_memory()
         e_host = torch.empty(natoms, dtype=torch.float64).pin_memory()
-        inner = w["reassign"]
+        inner = max(10, w["reassign"])
         iters = max(10, args.e2e_iters)
         s.stage_state(x_host, v_host)
         s.set_state_staged()
@@ -819,7 +845,7 @@ def run_gpu(args):
                            "tile": list(tile_used), "tile_force": list(tile_force)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "clocks": clocks, "fp64_path": fp64,
-                "oracle_err": errs32 or None,
+                "oracle_err": errs32 or None, "runaway_load": ra_load,
                 "end_state": {"step": stats_end["step"], "time_fs": stats_end["time"],
                               "n_runaway": stats_end["n_runaway"], "status": stats_end["status"],
                               "frenkel_pairs": sum(frenkel)}}
@@ -843,6 +869,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ra-scan", action="store_true", help="skip the run-away load scan (c2)")
     ap.add_argument("--no-oracle-err", action="store_true",
                     help="skip the oracle error of the benchmarked states (taken outside the timed region)")
     args = ap.parse_args()

@@ -309,8 +309,9 @@ int misa_tile_valid(int precision, int index);
 
 /* Tile shapes in use (1-based indices) by the density pass and by the force
  * pass.  With misa_params.tile = 0 the autotuner times both passes of the
- * initial state for every shape built for the precision and keeps the
- * fastest shape of each pass; otherwise both passes use misa_params.tile. */
+ * initial state for every shape built for the precision whose table window
+ * and staged tile fit the shared memory of a block, and keeps the fastest
+ * shape of each pass; otherwise both passes use misa_params.tile. */
 int misa_tile_current(const misa_sim *s);
 int misa_tile_current_force(const misa_sim *s);
 

@@ -756,18 +756,22 @@ int refresh(misa_sim *s, bool forces)
     return MISA_OK;
 }
 
-// FP32 alloy handles: whether both alloy passes of tile shape k fit in the
-// shared memory of a block (always true for one species and for FP64)
+// FP32 handles: whether the passes of tile shape k fit in the shared memory
+// of a block -- the table window beside one staged tile (single-type passes;
+// both alloy passes with several species); always true for FP64, whose
+// tables stay in global memory
 template <typename T>
-bool alloy_fits(const misa_sim *s, int k)
+bool shape_fits(const misa_sim *s, int k)
 {
-    if (sizeof(T) != 4 || s->nsp <= 1) return true;
+    if (sizeof(T) != 4) return true;
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return false;
     const TileShape &t = kTiles[k];
     const int nwin = s->p.n_knots - 1 - seg_lo_of(s);
+    if (packed_smem_bytes(sizeof(float4) * (size_t)(nwin + 1), t.tx, t.ty, t.tz, 1) > (size_t)optin) return false;
+    if (s->nsp <= 1) return true;
     return alloy_smem_bytes(true, nwin, t.tx, t.ty, t.tz) <= (size_t)optin &&
            alloy_smem_bytes(false, nwin, t.tx, t.ty, t.tz) <= (size_t)optin;
 }
@@ -782,7 +786,7 @@ int autotune(misa_sim *s)
     float best_d = 1e30f, best_f = 1e30f;
     int kd = 0, kf = 0;
     for (int k = 0; k < kNTiles; ++k) {
-        if (!tile_ok(s->prec, kTiles[k]) || !alloy_fits<T>(s, k)) continue;
+        if (!tile_ok(s->prec, kTiles[k]) || !shape_fits<T>(s, k)) continue;
         int rc = configure<T>(s, k, k);
         if (rc) return rc;
         rc = launch_forces<T>(s, 0, false);  // warm-up
@@ -902,7 +906,11 @@ int create_impl(misa_sim *s)
             *out[q] = to;
         }
     }
-    const int t0 = s->p.tile > 0 ? s->p.tile - 1 : 0;
+    // a fixed shape as asked (MISA_EINVAL if it does not fit); with the
+    // autotuner the first built shape that fits starts
+    int t0 = s->p.tile > 0 ? s->p.tile - 1 : 0;
+    if (s->p.tile == 0)
+        while (t0 + 1 < kNTiles && (!tile_ok(s->prec, kTiles[t0]) || !shape_fits<T>(s, t0))) ++t0;
     int rc = configure<T>(s, t0, t0);
     if (rc) return rc;
     MdArgs<T> m = md_args<T>(s);
@@ -1190,10 +1198,10 @@ int set_species_impl(misa_sim *s, int nsp, const double *f, const double *F, con
     CK(cudaStreamSynchronize(s->st));  // ht is a host temporary
     s->nsp = nsp;
     s->amaj = maj;
-    if (!alloy_fits<T>(s, s->tile) || !alloy_fits<T>(s, s->tile_f)) {
+    if (!shape_fits<T>(s, s->tile) || !shape_fits<T>(s, s->tile_f)) {
         // the current shapes' alloy passes do not fit: the first shape that does
         int k = 0;
-        while (k < kNTiles && (!tile_ok(s->prec, kTiles[k]) || !alloy_fits<T>(s, k))) ++k;
+        while (k < kNTiles && (!tile_ok(s->prec, kTiles[k]) || !shape_fits<T>(s, k))) ++k;
         if (k == kNTiles) return fail(s, MISA_EINVAL, "no tile shape fits the alloy passes' shared memory");
         int rc = configure<T>(s, k, k);
         if (rc) return rc;

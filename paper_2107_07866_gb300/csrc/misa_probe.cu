@@ -113,27 +113,30 @@ __global__ void __launch_bounds__(kThreads) k_mufu(int iters)
     if (s == -1.2345f) g_sink_f = s;
 }
 
-// 16-byte loads, lane l of a warp reading word group l: eight lanes cover
-// all 32 banks once per quarter warp (conflict-free, 4 wavefronts a warp)
+// 16-byte loads: the 32 lanes of a warp read 32 consecutive 16-byte words
+// (eight lanes cover all 32 banks once per quarter warp: conflict-free, four
+// wavefronts a warp), at addresses that move every iteration so that no
+// load can be hoisted or merged
+constexpr int kLdsWords = 2048;
 __global__ void __launch_bounds__(kThreads) k_lds(int iters)
 {
-    __shared__ uint4 buf[kThreads + 32 * kChains];
-    for (int q = threadIdx.x; q < kThreads + 32 * kChains; q += kThreads)
-        buf[q] = make_uint4(q, q * 3u, q * 5u, q * 7u);
+    __shared__ uint4 buf[kLdsWords];
+    for (int q = threadIdx.x; q < kLdsWords; q += kThreads) buf[q] = make_uint4(q, q * 3u, q * 5u, q * 7u);
     __syncthreads();
     uint4 acc = make_uint4(0, 0, 0, 0);
-    const unsigned base = threadIdx.x;
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const unsigned base = (unsigned)__cvta_generic_to_shared(buf);
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
         for (int k = 0; k < kChains; ++k) {
+            const unsigned word = (lane + 32u * (warp + (unsigned)(kChains * it + k))) & (kLdsWords - 1);
             uint4 v;
-            const unsigned addr = (unsigned)__cvta_generic_to_shared(&buf[base + 32 * k]);
             asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
                          : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                         : "r"(addr));
-            acc.x ^= v.x;
+                         : "r"(base + 16u * word));
+            acc.x += v.x;
             acc.y ^= v.y;
-            acc.z ^= v.z;
+            acc.z += v.z;
             acc.w ^= v.w;
         }
     }

@@ -320,6 +320,27 @@ def cascade_snapshot(nx, ny, nz, sigma: float, n_interstitial: int, n_close: int
     return np.mod(x, L)
 
 
+def interstitial_snapshot(nx, ny, nz, sigma: float, n_interstitial: int, seed: int, a0=A0_FE) -> np.ndarray:
+    """Thermal snapshot with n_interstitial atoms moved to distinct
+    octahedral interstitial points (cube edge centres, a0/2 from two lattice
+    atoms) of random cells: each leaves a vacancy and becomes a run-away.
+    Needs no distance search, so it scales to millions of atoms and
+    thousands of interstitials (a cascade's run-away load)."""
+    g = _rng(seed)
+    x = thermal_snapshot(nx, ny, nz, sigma, seed + 1, a0)
+    n = x.shape[0]
+    movers = g.choice(n, size=n_interstitial, replace=False)
+    ncell = nx * ny * nz
+    slots = g.choice(3 * ncell, size=n_interstitial, replace=False)  # (cell, axis of the edge)
+    cell, axis = slots // 3, slots % 3
+    cz, rest = cell // (nx * ny), cell % (nx * ny)
+    cy, cx = rest // nx, rest % nx
+    p = np.stack([cx, cy, cz], axis=1).astype(np.float64)
+    p[np.arange(n_interstitial), axis] += 0.5
+    x[movers] = p * a0
+    return np.mod(x, box(nx, ny, nz, a0))
+
+
 # ---------------------------------------------------------------------------
 # batched cascades and fitting snapshots
 # ---------------------------------------------------------------------------
