@@ -721,6 +721,24 @@ def run_gpu(args):
                              "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json)"},
                 "phase_ms_per_step": {k: v_ / max(nsteps, 1) for k, v_ in phases.items()},
                 "l1_data_pipe": l1, "kernel_source_sha": sha, "measured_peaks": peaks}
+    # the density pass with Newton's third law inside tiles, on the same
+    # state (its own autotuned tile shape), beside the full-neighbour pass
+    newton3 = None
+    if alloy is None and not args.no_newton3:
+        sim.set_density_variant(1)
+        if not args.tile:
+            sim.retune()
+        sim.step(2)
+        sim.timing(True)
+        sim.step(max(3, min(args.steps, 10)))
+        ph3, n3s = sim.timing_get()
+        sim.timing(False)
+        newton3 = {"density_ms": ph3["density"] / max(n3s, 1), "full_neighbour_density_ms": 1e3 * t_dens,
+                   "tile": list(sim.tile()),
+                   "speedup": 1e3 * t_dens / (ph3["density"] / max(n3s, 1)),
+                   "note": "density pass with each in-tile dense-shell pair evaluated once (Sec. 4.2 halving), "
+                           "pairs reaching outside the tile evaluated by the site; same state, steps after the timed ones"}
+        sim.set_density_variant(0)
     stats_end = sim.stats()
     frenkel = [int(c) for c in sim.defects()]
     sim.close()
@@ -845,7 +863,7 @@ def run_gpu(args):
                            "tile": list(tile_used), "tile_force": list(tile_force)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "clocks": clocks, "fp64_path": fp64,
-                "oracle_err": errs32 or None, "runaway_load": ra_load,
+                "oracle_err": errs32 or None, "runaway_load": ra_load, "newton3_density": newton3,
                 "end_state": {"step": stats_end["step"], "time_fs": stats_end["time"],
                               "n_runaway": stats_end["n_runaway"], "status": stats_end["status"],
                               "frenkel_pairs": sum(frenkel)}}
@@ -870,6 +888,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ra-scan", action="store_true", help="skip the run-away load scan (c2)")
+    ap.add_argument("--no-newton3", action="store_true", help="skip the Newton-3 density-pass comparison")
     ap.add_argument("--no-oracle-err", action="store_true",
                     help="skip the oracle error of the benchmarked states (taken outside the timed region)")
     args = ap.parse_args()

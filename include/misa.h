@@ -315,6 +315,21 @@ int misa_tile_valid(int precision, int index);
 int misa_tile_current(const misa_sim *s);
 int misa_tile_current_force(const misa_sim *s);
 
+/* Density-pass variant of an FP32 single-type handle.
+ *   0  full-neighbour gather (default): every site evaluates all its pairs.
+ *   1  Newton's third law inside a tile (Sec. 4.2's halving of the pair
+ *      work): each dense-shell pair of two sites of one tile is evaluated
+ *      once and its density handed to the partner through shared memory
+ *      (no atomics); pairs that reach outside the tile are evaluated by the
+ *      site itself.  Per-site sums keep a fixed order, so results do not
+ *      depend on the tile shape; they differ from variant 0 in the last FP32
+ *      bits (another summation order).
+ * The force pass is the full-neighbour gather either way.  Recomputes the
+ * forces of the current positions; drops a captured step graph;
+ * synchronises.  MISA_EINVAL for another variant, for variant 1 on an FP64
+ * or alloy handle, or when no tile shape fits the pass's shared memory. */
+int misa_set_density_variant(misa_sim *s, int32_t variant);
+
 /* Wigner-Seitz defect count of every replica (Sec. 5.1, the vacancy and
  * interstitial counts behind the Frenkel-pair curves): each atom belongs to
  * the cell of its nearest site -- an array atom to its own site, a run-away

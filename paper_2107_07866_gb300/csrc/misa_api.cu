@@ -13,6 +13,7 @@
 
 #include "misa.h"
 #include "misa_adjoint.cuh"
+#include "misa_newton3.cuh"
 #include "misa_packed.cuh"
 #include "misa_alloy.cuh"
 #include "misa_alloy_packed.cuh"
@@ -190,6 +191,7 @@ struct misa_sim {
     size_t smem_density = 0, smem_force = 0;
     size_t smem_alloy_d = 0, smem_alloy_f = 0;  // FP32 alloy passes (density, force tile shape)
     bool dens_db = false;  // FP32 density pass double-buffers its tiles
+    bool dens_n3 = false;  // FP32 density pass with Newton's third law inside tiles
     long long launches = 0;
     // phase timing
     bool timing = false;
@@ -438,6 +440,11 @@ size_t smem_density_bytes(misa_sim *s, size_t optin)
     const size_t nwin = (size_t)(s->p.n_knots - 1 - seg_lo_of(s));
     if constexpr (sizeof(T) == 4) {
         const size_t tb = sizeof(float4) * (nwin + 1);
+        if (s->dens_n3) {  // plus the exchange buffer of the Newton-3 pass
+            const size_t two = n3_smem_bytes(tb, ts.tx, ts.ty, ts.tz, 2);
+            s->dens_db = two <= optin;
+            return s->dens_db ? two : n3_smem_bytes(tb, ts.tx, ts.ty, ts.tz, 1);
+        }
         const size_t two = packed_smem_bytes(tb, ts.tx, ts.ty, ts.tz, 2);
         s->dens_db = two <= optin;
         return s->dens_db ? two : packed_smem_bytes(tb, ts.tx, ts.ty, ts.tz, 1);
@@ -470,6 +477,7 @@ TileLaunch tile_launch(const misa_sim *s)
     L.nsm = s->nsm;
     L.nsp = s->nsp;
     L.dens_db = s->dens_db;
+    L.dens_n3 = s->dens_n3;
     return L;
 }
 
@@ -770,7 +778,9 @@ bool shape_fits(const misa_sim *s, int k)
         return false;
     const TileShape &t = kTiles[k];
     const int nwin = s->p.n_knots - 1 - seg_lo_of(s);
-    if (packed_smem_bytes(sizeof(float4) * (size_t)(nwin + 1), t.tx, t.ty, t.tz, 1) > (size_t)optin) return false;
+    const size_t tb = sizeof(float4) * (size_t)(nwin + 1);
+    if (packed_smem_bytes(tb, t.tx, t.ty, t.tz, 1) > (size_t)optin) return false;
+    if (s->dens_n3 && n3_smem_bytes(tb, t.tx, t.ty, t.tz, 1) > (size_t)optin) return false;
     if (s->nsp <= 1) return true;
     return alloy_smem_bytes(true, nwin, t.tx, t.ty, t.tz) <= (size_t)optin &&
            alloy_smem_bytes(false, nwin, t.tx, t.ty, t.tz) <= (size_t)optin;
@@ -1577,6 +1587,36 @@ int misa_retune(misa_sim *s)
     if (!s) return MISA_EINVAL;
     if (s->p.tile != 0) return MISA_OK;
     int rc = s->prec == MISA_FP64 ? autotune<double>(s) : autotune<float>(s);
+    if (rc) return rc;
+    return check_status(s);
+}
+
+int misa_set_density_variant(misa_sim *s, int32_t variant)
+{
+    if (!s) return MISA_EINVAL;
+    if (variant != 0 && variant != 1)
+        return fail(s, MISA_EINVAL, "density variant: 0 (full neighbour) or 1 (Newton's third law inside tiles)");
+    if (variant == 1 && (s->prec != MISA_FP32_FORCE || s->nsp > 1))
+        return fail(s, MISA_EINVAL, "the Newton-3 density pass is built for single-type FP32 handles");
+    if (s->prec != MISA_FP32_FORCE || s->dens_n3 == (variant == 1)) return MISA_OK;
+    const bool old = s->dens_n3;
+    s->dens_n3 = variant == 1;
+    int td = s->tile;
+    if (!shape_fits<float>(s, td)) {
+        td = 0;
+        while (td < kNTiles && (!tile_ok(s->prec, kTiles[td]) || !shape_fits<float>(s, td))) ++td;
+        if (td == kNTiles) {
+            s->dens_n3 = old;
+            return fail(s, MISA_EINVAL, "no tile shape fits the Newton-3 density pass's shared memory");
+        }
+    }
+    int rc = configure<float>(s, td, s->tile_f);
+    if (rc) {
+        s->dens_n3 = old;
+        configure<float>(s, s->tile, s->tile_f);
+        return rc;
+    }
+    rc = refresh<float>(s, true);  // the current positions' forces through the new pass
     if (rc) return rc;
     return check_status(s);
 }

@@ -35,6 +35,7 @@ struct TileLaunch {
     int nsm;                            // SMs of the device
     int nsp;                            // species (> 1: the alloy passes run)
     bool dens_db;                       // FP32 density pass double-buffers its tiles
+    bool dens_n3;                       // FP32 density pass with Newton's third law inside tiles
 };
 
 // Per shape K (an index into kTiles): dynamic shared-memory attributes of

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "misa_alloy_packed.cuh"
+#include "misa_newton3.cuh"
 #include "misa_packed.cuh"
 #include "misa_tiles.cuh"
 
@@ -29,10 +30,17 @@ struct TileKernels {
             return cudaErrorInvalidValue;
         } else if constexpr (kF32) {
             const size_t d = L.smem_density;
-            if (e == cudaSuccess) e = smem(k_density_p<TX, TY, TZ, false, true>, d);
-            if (e == cudaSuccess) e = smem(k_density_p<TX, TY, TZ, true, true>, d);
-            if (e == cudaSuccess) e = smem(k_density_p<TX, TY, TZ, false, false>, d);
-            if (e == cudaSuccess) e = smem(k_density_p<TX, TY, TZ, true, false>, d);
+            if (L.dens_n3) {
+                if (e == cudaSuccess) e = smem(k_density_n3<TX, TY, TZ, false, true>, d);
+                if (e == cudaSuccess) e = smem(k_density_n3<TX, TY, TZ, true, true>, d);
+                if (e == cudaSuccess) e = smem(k_density_n3<TX, TY, TZ, false, false>, d);
+                if (e == cudaSuccess) e = smem(k_density_n3<TX, TY, TZ, true, false>, d);
+            } else {
+                if (e == cudaSuccess) e = smem(k_density_p<TX, TY, TZ, false, true>, d);
+                if (e == cudaSuccess) e = smem(k_density_p<TX, TY, TZ, true, true>, d);
+                if (e == cudaSuccess) e = smem(k_density_p<TX, TY, TZ, false, false>, d);
+                if (e == cudaSuccess) e = smem(k_density_p<TX, TY, TZ, true, false>, d);
+            }
             if (L.smem_alloy_d) {
                 if (e == cudaSuccess) e = smem(k_density_pa<TX, TY, TZ, false>, L.smem_alloy_d);
                 if (e == cudaSuccess) e = smem(k_density_pa<TX, TY, TZ, true>, L.smem_alloy_d);
@@ -75,6 +83,16 @@ struct TileKernels {
                 return;
             }
             const size_t b = L.smem_density;
+            if (L.dens_n3) {
+                if (L.dens_db) {
+                    if (energy) k_density_n3<TX, TY, TZ, true, true><<<grid, nt, b, L.st>>>(g);
+                    else k_density_n3<TX, TY, TZ, false, true><<<grid, nt, b, L.st>>>(g);
+                } else {
+                    if (energy) k_density_n3<TX, TY, TZ, true, false><<<grid, nt, b, L.st>>>(g);
+                    else k_density_n3<TX, TY, TZ, false, false><<<grid, nt, b, L.st>>>(g);
+                }
+                return;
+            }
             if (L.dens_db) {
                 if (energy) k_density_p<TX, TY, TZ, true, true><<<grid, nt, b, L.st>>>(g);
                 else k_density_p<TX, TY, TZ, false, true><<<grid, nt, b, L.st>>>(g);

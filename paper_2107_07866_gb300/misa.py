@@ -130,6 +130,7 @@ def lib():
         L.misa_selftest.argtypes = [C.c_longlong, C.POINTER(C.c_longlong)]
         L.misa_tile_shape.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.misa_measure_peaks.argtypes = [C.POINTER(Peaks), C.c_void_p]
+        L.misa_set_density_variant.argtypes = [C.c_void_p, C.c_int32]
         _lib = L
     return _lib
 
@@ -380,6 +381,11 @@ class Sim:
         pe, ke = np.empty(n), np.empty(n)
         self._check(lib().misa_replica_energies(self.h, pe.ctypes.data_as(_D), ke.ctypes.data_as(_D)))
         return pe, ke
+
+    def set_density_variant(self, variant):
+        """0: full-neighbour density pass; 1: Newton's third law inside tiles
+        (FP32 single-type handles)."""
+        self._check(lib().misa_set_density_variant(self.h, int(variant)))
 
     def set_graphs(self, enable=True):
         self._check(lib().misa_set_graphs(self.h, 1 if enable else 0))

@@ -404,3 +404,57 @@ def test_edge_readings_against_oracle(misa, pot, oracle, opot, prec):
     # with it there to the same bound
     sel = np.concatenate([[host_a, host_c], movers])
     assert nerr(f[sel], f_o[sel]) < TOL[prec]
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_newton3_density_variant_against_oracle(misa, pot, oracle_results, case):
+    # the density pass with Newton's third law inside tiles (Sec. 4.2's pair
+    # halving, no atomics): every tile shape bitwise equal to every other, and
+    # densities, energies and forces within the FP32 bound of the oracle
+    x, dims, rho_o, e_o, f_o = oracle_results[case]
+    ref = None
+    for t in misa.tile_indices("fp32"):
+        with misa.Sim(pot, *dims, precision="fp32", tile=t) as s:
+            s.set_density_variant(1)
+            s.set_state(x)
+            f = s.forces()
+            rho = s.density()
+            _, _, e = s.energies(per_atom=True)
+            st = s.stats()
+        assert st["status"] & 0x3 == 0
+        assert nerr(f, f_o) < TOL["fp32"], (t, nerr(f, f_o))
+        assert nerr(rho, rho_o) < TOL["fp32"], (t, nerr(rho, rho_o))
+        assert nerr(e, e_o) < TOL["fp32"], (t, nerr(e, e_o))
+        if ref is None:
+            ref = (f, rho, e)
+        else:
+            for a_, b_ in zip(ref, (f, rho, e)):
+                np.testing.assert_array_equal(a_, b_)
+
+
+def test_newton3_density_variant_trajectory(misa, pot, oracle, opot):
+    # the cascade trajectory of test_cascade_trajectory_with_runaways through
+    # the Newton-3 density pass, and the variant switched back and forth
+    n = 8
+    x0 = synth.cascade_snapshot(n, n, n, 0.1, 6, 2, 11)
+    v0 = synth.maxwell_velocities(len(x0), 600.0, M, 4)
+    oracle.insert_pka(v0, synth.pka_atom(n, n, n), M, 300.0, synth.random_direction(9))
+    L = synth.box(n, n, n)
+    with misa.Sim(pot, n, precision="fp32", dt_max=1.0, dx_max=0.02, reassign_period=3) as s:
+        s.set_state(x0, v0)
+        s.set_density_variant(1)
+        s.step(30)
+        s.set_density_variant(0)
+        s.set_density_variant(1)
+        s.step(30)
+        x = s.positions()
+        st = s.stats()
+    xo, _, _, t, _ = oracle.md_run(opot, x0, v0, L, M, 1.0, 0.02, 60, mode=1)
+    dd = x - xo
+    dd -= L * np.round(dd / L)
+    assert np.abs(dd).max() < 2e-5, np.abs(dd).max()
+    assert abs(st["time"] - t) < 1e-6 and st["status"] & 0x3 == 0
+    with misa.Sim(pot, n, precision="fp64") as s:
+        with pytest.raises(misa.MisaError) as e:
+            s.set_density_variant(1)
+        assert e.value.code == misa.MISA_EINVAL
