@@ -67,6 +67,7 @@ struct AdjArgs {
     int nvec;                        // offsets within rc + 2 skin (prefix of kLVec)
     const int *tile_flag;            // null: every site scans the run-away list
     int tx, ty, tz;
+    const int *ra_toff, *ra_tcnt, *ra_tlist;  // per-tile run-away index of that map (or null)
     SplitN2 split[kMaxN2 + 1];
 };
 
@@ -170,14 +171,24 @@ __device__ __forceinline__ void visit_site(const A &a, const RepDesc &rd, int nr
         if (adj_pair<T>(a, o.x, o.y, o.z, a.ux[t] - uix, a.uy[t] - uiy, a.uz[t] - uiz, false, t, P)) fn(P);
     }
     if (nra == 0) return;
+    // the run-aways of the site's tile index entry (list order), else the
+    // whole list
+    const int *jl = nullptr;
+    int nj = nra;
     if (a.tile_flag) {
         const int tl = rd.tile_base + ((cz / a.tz) * rd.nty + cy / a.ty) * rd.ntx + (x2 >> 1) / a.tx;
-        if (!a.tile_flag[tl]) return;
+        const int f = a.tile_flag[tl];
+        if (!f) return;
+        if (f == 1 && a.ra_tlist) {
+            jl = a.ra_tlist + a.ra_toff[tl];
+            nj = a.ra_tcnt[tl];
+        }
     }
     int X, Y, Z;
     site_lat(ls, rd.nx, rd.ny, X, Y, Z);
     const int Lx = 2 * rd.nx, Ly = 2 * rd.ny, Lz = 2 * rd.nz;
-    for (int j = 0; j < nra; ++j) {
+    for (int jq = 0; jq < nj; ++jq) {
+        const int j = jl ? jl[jq] : jq;
         const int g = rd.ra_base + j;
         int Xj, Yj, Zj;
         site_lat(a.ra_home[g], rd.nx, rd.ny, Xj, Yj, Zj);
@@ -225,7 +236,17 @@ __device__ __forceinline__ void visit_ra(const A &a, const RepDesc &rd, int nra,
             fn(P);
     }
     const int Lx = 2 * rd.nx, Ly = 2 * rd.ny, Lz = 2 * rd.nz;
-    for (int k = lane; k < nra; k += 32) {
+    // the other run-aways: the home tile's index entry (lane l takes the list
+    // indices k = l mod 32, ascending), else the whole list
+    const int *kl = nullptr;
+    if (a.tile_flag && a.ra_tlist) {
+        const int tl = rd.tile_base + ((hcz / a.tz) * rd.nty + hcy / a.ty) * rd.ntx + hcx / a.tx;
+        if (a.tile_flag[tl] == 1) kl = a.ra_tlist + a.ra_toff[tl];
+        if (kl) nra = a.ra_tcnt[tl];
+    }
+    for (int kq = kl ? 0 : lane; kq < nra; kq += kl ? 1 : 32) {
+        const int k = kl ? kl[kq] : kq;
+        if (kl && (k & 31) != lane) continue;
         if (k == jl) continue;
         const int gk = rd.ra_base + k;
         int Xk, Yk, Zk;

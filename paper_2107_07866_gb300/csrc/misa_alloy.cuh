@@ -50,6 +50,7 @@ struct AlloyArgs {
     int kick, energy, nvec;
     const int *tile_flag;
     int tx, ty, tz;
+    const int *ra_toff, *ra_tcnt, *ra_tlist;  // per-tile run-away index of the density map
     SplitN2 split[kMaxN2 + 1];
 };
 

@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_density_pa(const __grid_const
             const Vec4<float> ua{A.x, A.z, B.x, 0.f}, ub{A.y, A.w, B.y, 0.f};
             while (true) {
                 __syncthreads();
-                const int cnt = stage_runaways<float, TX, TY, TZ, false>(a, L, nra, pos, sm.rh, sm.ru, sm.st);
+                const int cnt = stage_runaways<float, TX, TY, TZ, false>(a, L, tile, nra, pos, sm.rh, sm.ru, sm.st);
                 if (cnt == 0) break;
                 if (live_a) ra_density_site_a(a, L, cnt, sm.rh, sm.ru, ua, sx, sy, sza, ra, st);
                 if (live_b) ra_density_site_a(a, L, cnt, sm.rh, sm.ru, ub, sx, sy, szb, rb, st);
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(TX *TY *TZ, kForcePaBlocks<TX, TY, TZ>) k_forc
             const Vec4<float> ua{A.x, A.z, B.x, B.z}, ub{A.y, A.w, B.y, B.w};
             while (true) {
                 __syncthreads();
-                const int cnt = stage_runaways<float, TX, TY, TZ, true>(a, L, nra, pos, sm.rh, sm.ru, sm.st);
+                const int cnt = stage_runaways<float, TX, TY, TZ, true>(a, L, tile, nra, pos, sm.rh, sm.ru, sm.st);
                 if (cnt == 0) break;
                 if (live_a) ra_force_site_a<ENERGY>(a, L, cnt, sm.rh, sm.ru, ua, si.ta, sx, sy, sza, fa, ea, st);
                 if (live_b) ra_force_site_a<ENERGY>(a, L, cnt, sm.rh, sm.ru, ub, si.tb, sx, sy, szb, fb, eb, st);

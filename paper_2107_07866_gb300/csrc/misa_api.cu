@@ -157,6 +157,11 @@ struct misa_sim {
     int tile_f = 0, ntiles_f = 0;
     RepDesc *reps_fd = nullptr;
     int *tile_rep_f = nullptr, *tile_flag_f = nullptr;
+    // per-tile run-away index of each map (0 density, 1 force): counts,
+    // segment offsets, fill cursors, tiles with run-aways, [cursor, count],
+    // and the segments of sorted list indices (rt_cap entries)
+    int *rt_cnt[2] = {}, *rt_off[2] = {}, *rt_fill[2] = {}, *rt_nz[2] = {}, *rt_aux[2] = {}, *rt_list[2] = {};
+    long long rt_cap = 0;
     double *u[3] = {}, *v[3] = {};
     void *s[3] = {};  // precision-T shadow of u (FP32 path) or alias of u
     void *a[3] = {};
@@ -375,6 +380,9 @@ void fill_gather(misa_sim *s, GatherArgs<T> &g, bool force_pass = false)
     g.ra_ux = (const T *)s->ra_s[0]; g.ra_uy = (const T *)s->ra_s[1]; g.ra_uz = (const T *)s->ra_s[2];
     g.ra_fp = (const T *)s->ra_fp;
     g.tile_flag = force_pass ? s->tile_flag_f : s->tile_flag;
+    g.ra_toff = s->rt_off[force_pass ? 1 : 0];
+    g.ra_tcnt = s->rt_cnt[force_pass ? 1 : 0];
+    g.ra_tlist = s->rt_list[force_pass ? 1 : 0];
     g.sc = s->sc;
     g.acc_conv = kAccUnit / s->p.mass;
     g.kick = 1;
@@ -551,19 +559,36 @@ int configure(misa_sim *s, int td, int tf)
     return MISA_OK;
 }
 
-// Run-away tile flags of both passes' tile shapes.
+// Per-tile run-away index of both passes' tile maps (sets their tile
+// flags): count, allocate segments, fill, sort each segment into list order.
 template <typename T>
 int mark_tiles(misa_sim *s)
 {
     MdArgs<T> m = md_args<T>(s);
-    CK(cudaMemsetAsync(s->tile_flag, 0, sizeof(int) * (size_t)s->ntiles, s->st));
-    CK(cudaMemsetAsync(s->tile_flag_f, 0, sizeof(int) * (size_t)s->ntiles_f, s->st));
-    k_mark_tiles<T><<<list_grid(s), 256, 0, s->st>>>(m);
-    const TileShape &tf = kTiles[s->tile_f];
-    m.reps = s->reps_fd;
-    m.tile_flag = s->tile_flag_f;
-    m.tx = tf.tx; m.ty = tf.ty; m.tz = tf.tz;
-    k_mark_tiles<T><<<list_grid(s), 256, 0, s->st>>>(m);
+    RaTileMaps Ms;
+    int nt = 0;
+    for (int k = 0; k < 2; ++k) {
+        const TileShape &ts = kTiles[k ? s->tile_f : s->tile];
+        RaTileMap &M = Ms.m[k];
+        M.reps = k ? s->reps_fd : s->reps_d;
+        M.tx = ts.tx; M.ty = ts.ty; M.tz = ts.tz;
+        M.ntiles = k ? s->ntiles_f : s->ntiles;
+        M.flag = k ? s->tile_flag_f : s->tile_flag;
+        M.cnt = s->rt_cnt[k]; M.off = s->rt_off[k]; M.fill = s->rt_fill[k]; M.list = s->rt_list[k];
+        M.nz = s->rt_nz[k]; M.aux = s->rt_aux[k];
+        M.cap = (int)s->rt_cap;
+        nt = nt > M.ntiles ? nt : M.ntiles;
+    }
+    // the two maps' counts and cursors are contiguous (one allocation)
+    CK(cudaMemsetAsync(s->rt_cnt[0], 0, sizeof(int) * (size_t)s->ntile_cap * 2, s->st));
+    CK(cudaMemsetAsync(s->rt_aux[0], 0, sizeof(int) * 4, s->st));
+    const dim3 lg((s->cap + 255) / 256 < 64 ? (s->cap + 255) / 256 : 64, s->nrep);
+    k_ra_tcount<T><<<lg, 256, 0, s->st>>>(m, Ms);
+    const int tb = (nt + 255) / 256;
+    k_ra_toff<<<tb < 1024 ? tb : 1024, 256, 0, s->st>>>(Ms);
+    k_ra_tfill<T><<<lg, 256, 0, s->st>>>(m, Ms);
+    k_ra_tsort<<<dim3(s->nsm, 2), 32 * kRaSortWarps, 0, s->st>>>(Ms);
+    s->launches += 4;
     return MISA_OK;
 }
 
@@ -620,6 +645,7 @@ AlloyArgs<T> alloy_args(misa_sim *s, int kick, bool energy)
     while (nsh < kLVec.nshell && kLVec.shell_n2[nsh] <= roff * roff) ++nsh;
     a.nvec = kLVec.shell_begin[nsh];
     a.tile_flag = s->tile_flag;
+    a.ra_toff = s->rt_off[0]; a.ra_tcnt = s->rt_cnt[0]; a.ra_tlist = s->rt_list[0];
     const TileShape &ts = kTiles[s->tile];
     a.tx = ts.tx; a.ty = ts.ty; a.tz = ts.tz;
     fill_split(a.split, half / hr);
@@ -677,14 +703,17 @@ int launch_forces(misa_sim *s, int kick, bool energy, bool step_marks = false)
     ra.ra_ax = (T *)s->ra_a[0]; ra.ra_ay = (T *)s->ra_a[1]; ra.ra_az = (T *)s->ra_a[2];
     ra.ra_vx = s->ra_v[0]; ra.ra_vy = s->ra_v[1]; ra.ra_vz = s->ra_v[2];
     ra.energy = energy ? 1 : 0;
+    ra.tx = kTiles[s->tile].tx; ra.ty = kTiles[s->tile].ty; ra.tz = kTiles[s->tile].tz;
+    // one warp per run-away: enough warps for a full list
+    const int rab = (s->cap + 7) / 8 < 16 ? 16 : ((s->cap + 7) / 8 > 512 ? 512 : (s->cap + 7) / 8);
     if (step_marks) mark(s);  // end of the list phase
     launch_density<T>(s, gd, energy);
     if (step_marks) mark(s);
-    k_ra_gather<T, 0><<<dim3(16, s->nrep), 256, 0, s->st>>>(ra);
+    k_ra_gather<T, 0><<<dim3(rab, s->nrep), 256, 0, s->st>>>(ra);
     if (step_marks) mark(s);
     launch_force<T>(s, gf, energy);
     if (step_marks) mark(s);
-    k_ra_gather<T, 1><<<dim3(16, s->nrep), 256, 0, s->st>>>(ra);
+    k_ra_gather<T, 1><<<dim3(rab, s->nrep), 256, 0, s->st>>>(ra);
     if (step_marks) mark(s);
     s->launches += 6;
     CK(cudaGetLastError());
@@ -842,6 +871,24 @@ int create_impl(misa_sim *s)
     s->reps_fd = (RepDesc *)dalloc(s, sizeof(RepDesc) * s->nrep);
     s->tile_rep_f = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap);
     s->tile_flag_f = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap);
+    // a run-away is staged by at most 3 tiles per axis (7-cell window, tiles
+    // of at least 4 cells)
+    s->rt_cap = 27LL * s->cap * s->nrep;
+    if (s->rt_cap > 0x7FFFFFFFLL) s->rt_cap = 0x7FFFFFFFLL;
+    // counts and cursors of both maps in one block each (one memset per step)
+    int *cnt2 = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap * 2);
+    int *aux2 = (int *)dalloc(s, sizeof(int) * 4);
+    if (!cnt2 || !aux2) return fail(s, MISA_EOOM, "device allocation failed (run-away tile index)");
+    for (int k = 0; k < 2; ++k) {
+        s->rt_cnt[k] = cnt2 + (size_t)k * s->ntile_cap;
+        s->rt_aux[k] = aux2 + 2 * k;
+        s->rt_off[k] = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap);
+        s->rt_fill[k] = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap);
+        s->rt_nz[k] = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap);
+        s->rt_list[k] = (int *)dalloc(s, sizeof(int) * (size_t)s->rt_cap);
+        if (!s->rt_off[k] || !s->rt_fill[k] || !s->rt_nz[k] || !s->rt_list[k])
+            return fail(s, MISA_EOOM, "device allocation failed (run-away tile index)");
+    }
     s->sid = (int *)dalloc(s, sizeof(int) * ns);
     s->claim = (int *)dalloc(s, sizeof(int) * ns);
     for (int d = 0; d < 3; ++d) {
@@ -1906,11 +1953,13 @@ namespace {
 constexpr size_t kStaticAlign = 256;
 // upper bound of the carve below for either precision: per site <= 160 B,
 // per run-away slot <= 512 B, per knot <= 160 B, two flags and two map
-// entries per cell (density and force tile maps), two replica tables, the
-// scalars, and the alignment padding
+// entries per cell (density and force tile maps), the two maps' run-away
+// index (four ints per cell, 27 entries per run-away slot), two replica
+// tables, the scalars, and the alignment padding
 constexpr size_t kStaticNeed = 160ull * MISA_STATIC_MAX_ATOMS + 512ull * MISA_STATIC_RUNAWAY_CAP +
                                160ull * MISA_STATIC_MAX_KNOTS + 16ull * (MISA_STATIC_MAX_ATOMS / 2) +
-                               sizeof(DevScalars) + 2 * sizeof(RepDesc) + 96 * kStaticAlign;
+                               2 * (16ull * (MISA_STATIC_MAX_ATOMS / 2) + 8 + 4 * 27ull * MISA_STATIC_RUNAWAY_CAP) +
+                               sizeof(DevScalars) + 2 * sizeof(RepDesc) + 128 * kStaticAlign;
 static_assert(kStaticNeed <= MISA_STATIC_SCRATCH_BYTES, "static scratch too small");
 
 }  // namespace
@@ -1982,6 +2031,17 @@ size_t carve_static(misa_sim *s, unsigned char *base, int nk)
     s->reps_fd = c.take<RepDesc>(1);
     s->tile_flag_f = c.take<int>(ns / 2);
     s->tile_rep_f = c.take<int>(ns / 2);
+    s->rt_cap = 27LL * (long long)cap;
+    int *cnt2 = c.take<int>(ns);  // ntile_cap = ns / 2 per map
+    int *aux2 = c.take<int>(4);
+    for (int k = 0; k < 2; ++k) {
+        s->rt_cnt[k] = cnt2 + (size_t)k * (ns / 2);
+        s->rt_aux[k] = aux2 + 2 * k;
+        s->rt_off[k] = c.take<int>(ns / 2);
+        s->rt_fill[k] = c.take<int>(ns / 2);
+        s->rt_nz[k] = c.take<int>(ns / 2);
+        s->rt_list[k] = c.take<int>((size_t)s->rt_cap);
+    }
     return c.off;
 }
 

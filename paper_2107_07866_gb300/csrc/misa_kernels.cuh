@@ -221,6 +221,10 @@ struct GatherArgs {
     // force pass evaluates only those.  mask_ok = 0: evaluate all of them.
     unsigned long long *bmask;
     int mask_ok;
+    // per-tile run-away index of this pass's tile map: tile t stages the
+    // sorted list indices [ra_toff[t], ra_toff[t] + ra_tcnt[t]) of ra_tlist
+    // when tile_flag[t] == 1 (2: the index overflowed, scan the whole list)
+    const int *ra_toff, *ra_tcnt, *ra_tlist;
     unsigned long long tex_f, tex_d0, tex_d1;  // texture objects over tab_f, tab_d0, tab_d1
     // alloys (several species; null / zero for one): species per atom id,
     // run-away atom ids, and the per-species tables (nknot entries each, the
@@ -340,68 +344,104 @@ __device__ __forceinline__ T stage_tile(const GatherArgs<T> &a, const TileLoc &L
     return (T)(sqrtf(sred[32]) * 1.000001f);
 }
 
+// Home lattice coordinates of run-away j of replica rd (home site h)
+// relative to the tile origin (c0x, c0y, c0z) of a tx x ty x tz tile -- the
+// nearest periodic image to the tile centre -- and whether its home cell
+// lies within 3 cells of the tile (reach rc + skin + the Wigner-Seitz
+// radius): the run-aways a tile stages.
+__device__ __forceinline__ bool ra_in_tile_rt(const RepDesc &rd, int h, int c0x, int c0y, int c0z, int tx, int ty,
+                                              int tz, int &hx, int &hy, int &hz)
+{
+    const int x2 = h % (2 * rd.nx);
+    const int rest = h / (2 * rd.nx);
+    const int cy = rest % rd.ny, cz = rest / rd.ny;
+    const int par = x2 & 1, cx = x2 >> 1;
+    int dx = cx - c0x - tx / 2, dy = cy - c0y - ty / 2, dz = cz - c0z - tz / 2;
+    dx -= rd.nx * (int)floorf((dx + 0.5f * rd.nx) / rd.nx);
+    dy -= rd.ny * (int)floorf((dy + 0.5f * rd.ny) / rd.ny);
+    dz -= rd.nz * (int)floorf((dz + 0.5f * rd.nz) / rd.nz);
+    dx += tx / 2; dy += ty / 2; dz += tz / 2;
+    hx = 2 * dx + par;
+    hy = 2 * dy + par;
+    hz = 2 * dz + par;
+    return dx >= -3 && dx < tx + 3 && dy >= -3 && dy < ty + 3 && dz >= -3 && dz < tz + 3;
+}
+
+template <int TX, int TY, int TZ>
+__device__ __forceinline__ bool ra_in_tile(const RepDesc &rd, int h, int c0x, int c0y, int c0z, int &hx, int &hy,
+                                           int &hz)
+{
+    return ra_in_tile_rt(rd, h, c0x, c0y, c0z, TX, TY, TZ, hx, hy, hz);
+}
+
 // Stages the next chunk of the replica's run-away atoms whose home cell lies
-// within 3 cells of the tile (reach rc + skin + the Wigner-Seitz radius), in
-// list order, as (home lattice coords relative to the tile origin, u, F').
-// Warp 0 scans; returns the staged count (block-uniform).
+// within 3 cells of the tile, in list order, as (home lattice coords
+// relative to the tile origin, u, F').  A tile with an index entry
+// (tile_flag 1) copies its sorted entries; otherwise warp 0 scans the whole
+// list.  Returns the staged count (block-uniform); pos advances, reaching
+// nra when nothing is left.
 template <typename T, int TX, int TY, int TZ, bool WITH_FP>
-__device__ __forceinline__ int stage_runaways(const GatherArgs<T> &a, const TileLoc &L, int nra, int &pos, int4 *sRh,
-                                              Vec4<T> *sRu, RaStage *st)
+__device__ __forceinline__ int stage_runaways(const GatherArgs<T> &a, const TileLoc &L, int tile, int nra, int &pos,
+                                              int4 *sRh, Vec4<T> *sRu, RaStage *st)
 {
     const RepDesc &rd = L.rd;
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         int cnt = 0;
         int p0 = pos;
-        while (p0 < nra && cnt < kRaChunk) {
-            const int j = p0 + lane;
-            bool take = false;
-            int hx = 0, hy = 0, hz = 0;
-            if (j < nra) {
-                const int h = a.ra_home[rd.ra_base + j];
-                const int x2 = h % (2 * rd.nx);
-                const int rest = h / (2 * rd.nx);
-                const int cy = rest % rd.ny, cz = rest / rd.ny;
-                const int par = x2 & 1, cx = x2 >> 1;
-                int dx = cx - L.c0x - TX / 2, dy = cy - L.c0y - TY / 2, dz = cz - L.c0z - TZ / 2;
-                // nearest periodic image to the tile centre
-                dx -= rd.nx * (int)floorf((dx + 0.5f * rd.nx) / rd.nx);
-                dy -= rd.ny * (int)floorf((dy + 0.5f * rd.ny) / rd.ny);
-                dz -= rd.nz * (int)floorf((dz + 0.5f * rd.nz) / rd.nz);
-                dx += TX / 2; dy += TY / 2; dz += TZ / 2;
-                take = dx >= -3 && dx < TX + 3 && dy >= -3 && dy < TY + 3 && dz >= -3 && dz < TZ + 3;
-                hx = 2 * dx + par;
-                hy = 2 * dy + par;
-                hz = 2 * dz + par;
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, take);
-            const int room = kRaChunk - cnt;
-            const int rank = __popc(bal & ((1u << lane) - 1u));
-            if (take && rank < room) {
-                // w: the run-away's species (alloys)
-                sRh[cnt + rank] = make_int4(hx, hy, hz, a.atype ? (int)a.atype[a.ra_id[rd.ra_base + j]] : 0);
+        if (a.tile_flag[tile] == 1) {
+            // the tile's index entries: list indices in ascending order
+            const int n = a.ra_tcnt[tile], off = a.ra_toff[tile];
+            cnt = min(n - p0, kRaChunk);
+            for (int q = lane; q < cnt; q += 32) {
+                const int j = a.ra_tlist[off + p0 + q];
+                int hx, hy, hz;
+                ra_in_tile<TX, TY, TZ>(rd, a.ra_home[rd.ra_base + j], L.c0x, L.c0y, L.c0z, hx, hy, hz);
+                sRh[q] = make_int4(hx, hy, hz, a.atype ? (int)a.atype[a.ra_id[rd.ra_base + j]] : 0);
                 Vec4<T> u;
                 u.x = a.ra_ux[rd.ra_base + j];
                 u.y = a.ra_uy[rd.ra_base + j];
                 u.z = a.ra_uz[rd.ra_base + j];
                 u.w = WITH_FP ? a.ra_fp[rd.ra_base + j] : (T)0;
-                sRu[cnt + rank] = u;
+                sRu[q] = u;
             }
-            const int ntake = __popc(bal);
-            if (ntake <= room) {
-                cnt += ntake;
-                p0 += 32;
-            } else {
-                // chunk full: resume at the first lane that did not fit
-                unsigned b = bal;
-                for (int q = 0; q < room; ++q) b &= b - 1;
-                p0 += __ffs(b) - 1;
-                cnt += room;
+            p0 = p0 + cnt >= n ? nra : p0 + cnt;
+        } else {
+            while (p0 < nra && cnt < kRaChunk) {
+                const int j = p0 + lane;
+                bool take = false;
+                int hx = 0, hy = 0, hz = 0;
+                if (j < nra) take = ra_in_tile<TX, TY, TZ>(rd, a.ra_home[rd.ra_base + j], L.c0x, L.c0y, L.c0z, hx, hy, hz);
+                const unsigned bal = __ballot_sync(0xffffffffu, take);
+                const int room = kRaChunk - cnt;
+                const int rank = __popc(bal & ((1u << lane) - 1u));
+                if (take && rank < room) {
+                    // w: the run-away's species (alloys)
+                    sRh[cnt + rank] = make_int4(hx, hy, hz, a.atype ? (int)a.atype[a.ra_id[rd.ra_base + j]] : 0);
+                    Vec4<T> u;
+                    u.x = a.ra_ux[rd.ra_base + j];
+                    u.y = a.ra_uy[rd.ra_base + j];
+                    u.z = a.ra_uz[rd.ra_base + j];
+                    u.w = WITH_FP ? a.ra_fp[rd.ra_base + j] : (T)0;
+                    sRu[cnt + rank] = u;
+                }
+                const int ntake = __popc(bal);
+                if (ntake <= room) {
+                    cnt += ntake;
+                    p0 += 32;
+                } else {
+                    // chunk full: resume at the first lane that did not fit
+                    unsigned b = bal;
+                    for (int q = 0; q < room; ++q) b &= b - 1;
+                    p0 += __ffs(b) - 1;
+                    cnt += room;
+                }
             }
+            if (p0 > nra) p0 = nra;
         }
         if (lane == 0) {
             st->cnt = cnt;
-            st->next = p0 < nra ? p0 : nra;
+            st->next = p0;
         }
     }
     __syncthreads();
@@ -782,6 +822,13 @@ __device__ __forceinline__ RaPair<T> ra_pair(const GatherArgs<T> &a, const RepDe
     while (ny_ < -rd.ny) ny_ += Ly;
     while (nz_ > rd.nz) nz_ -= Lz;
     while (nz_ < -rd.nz) nz_ += Lz;
+    // a run-away lies within the Wigner-Seitz radius sqrt(5)/2 of its home
+    // and an array atom within the skin (< 0.64 lattice units) of its site,
+    // so a pair inside rc has every component of n below rc + 1.76: the
+    // integer test rejects the staged run-aways out of reach exactly
+    const int K = (int)(a.rc_lat + (T)1.8);
+    P.in = false;
+    if (abs(nx_) > K || abs(ny_) > K || abs(nz_) > K) return P;
     const T dx = uj.x - ui.x, dy = uj.y - ui.y, dz = uj.z - ui.z;
     const T qq = (dx + (T)(2 * nx_)) * dx + (dy + (T)(2 * ny_)) * dy + (dz + (T)(2 * nz_)) * dz;
     const T r2 = (T)(nx_ * nx_ + ny_ * ny_ + nz_ * nz_) + qq;
@@ -871,7 +918,7 @@ __global__ void __launch_bounds__(2 * TX * TY * TZ, 1) k_density(const __grid_co
             const int sx = 2 * lx + p, sy = 2 * ly + p, sz = 2 * lz + p;
             while (true) {
                 __syncthreads();
-                const int cnt = stage_runaways<T, TX, TY, TZ, false>(a, L, nra, pos, sm.rh, sm.ru, sm.st);
+                const int cnt = stage_runaways<T, TX, TY, TZ, false>(a, L, tile, nra, pos, sm.rh, sm.ru, sm.st);
                 if (cnt == 0) break;
                 if (live) {
                     for (int j = 0; j < cnt; ++j) {
@@ -1016,7 +1063,7 @@ __global__ void __launch_bounds__(2 * TX * TY * TZ, 1) k_force(const __grid_cons
             const int sx = 2 * lx + p, sy = 2 * ly + p, sz = 2 * lz + p;
             while (true) {
                 __syncthreads();
-                const int cnt = stage_runaways<T, TX, TY, TZ, true>(a, L, nra, pos, sm.rh, sm.ru, sm.st);
+                const int cnt = stage_runaways<T, TX, TY, TZ, true>(a, L, tile, nra, pos, sm.rh, sm.ru, sm.st);
                 if (cnt == 0) break;
                 if (live) {
                     for (int j = 0; j < cnt; ++j) {

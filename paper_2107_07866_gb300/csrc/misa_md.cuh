@@ -414,37 +414,169 @@ __global__ void __launch_bounds__(1024) k_ra_sort(MdArgs<T> m)
     }
 }
 
-// Marks every tile within 3 cells of a run-away's home cell: those tiles'
-// CTAs scan the run-away list.  tile_flag is zeroed before.
+// ---------------------------------------------------------------------------
+// per-tile run-away index (the "run-away bucket" of every tile of a map)
+// ---------------------------------------------------------------------------
+// A tile stages the run-aways whose home cell lies within 3 cells of it
+// (ra_in_tile).  Rather than every tile scanning the whole list, each tile
+// gets the sorted list indices of its run-aways: count (atomics), segment
+// allocation, fill (atomics), then a per-tile sort restores list order, so
+// a tile stages exactly the entries, in exactly the order, the scan would.
+// tile_flag: 0 no run-away, 1 indexed, 2 scan the list (the index ran out
+// of room or a segment is too long to sort).
+
+constexpr int kRaSortSeg = 1024;  // longest segment a warp sorts
+
+struct RaTileMap {
+    const RepDesc *reps;  // the map's replica table (tile counts of its shape)
+    int tx, ty, tz;
+    int ntiles;
+    int *flag, *cnt, *off, *fill, *list;
+    int *nz;     // tiles with run-aways (compact)
+    int *aux;    // [0] segment cursor, [1] nz count
+    int cap;     // list entries
+};
+
+// calls f(global tile) for every tile of rd whose staged set holds a
+// run-away with home site h
+template <typename F>
+__device__ __forceinline__ void for_ra_tiles(const RepDesc &rd, int h, int tx, int ty, int tz, F f)
+{
+    int x2 = h % (2 * rd.nx);
+    int q = h / (2 * rd.nx);
+    int c[3] = {x2 >> 1, q % rd.ny, q / rd.ny};
+    int nn[3] = {rd.nx, rd.ny, rd.nz};
+    int tt[3] = {tx, ty, tz};
+    int tl[3][8], nt[3];
+    for (int d = 0; d < 3; ++d) {
+        nt[d] = 0;
+        int w = nn[d] < 7 ? nn[d] : 7;
+        for (int o = 0; o < w; ++o) {
+            int cc = wrapi(c[d] - 3 + o, nn[d]);
+            int t = cc / tt[d];
+            bool seen = false;
+            for (int k = 0; k < nt[d]; ++k) seen |= (tl[d][k] == t);
+            if (!seen) tl[d][nt[d]++] = t;
+        }
+    }
+    for (int a = 0; a < nt[2]; ++a)
+        for (int b = 0; b < nt[1]; ++b)
+            for (int e = 0; e < nt[0]; ++e) f(rd.tile_base + (tl[2][a] * rd.nty + tl[1][b]) * rd.ntx + tl[0][e], tl[0][e],
+                                              tl[1][b], tl[2][a]);
+}
+
+// the stage predicate of tile (tix, tiy, tiz) of a tx x ty x tz map (the
+// enumeration above is a superset for small boxes)
+__device__ __forceinline__ bool ra_takes_rt(const RepDesc &rd, int h, int tx, int ty, int tz, int tix, int tiy, int tiz)
+{
+    int hx, hy, hz;
+    return ra_in_tile_rt(rd, h, tix * tx, tiy * ty, tiz * tz, tx, ty, tz, hx, hy, hz);
+}
+
+struct RaTileMaps {
+    RaTileMap m[2];  // density pass's map, force pass's map
+};
+
+// The tiles of map M that stage a run-away with home site h: the
+// enumeration, filtered by the stage predicate where a box is too small for
+// the two to agree (an axis of fewer than tile + 6 cells).
+template <typename F>
+__device__ __forceinline__ void for_staging_tiles(const RepDesc &rd, const RaTileMap &M, int h, F f)
+{
+    const bool exact = rd.nx >= M.tx + 6 && rd.ny >= M.ty + 6 && rd.nz >= M.tz + 6;
+    for_ra_tiles(rd, h, M.tx, M.ty, M.tz, [&](int t, int tix, int tiy, int tiz) {
+        if (exact || ra_takes_rt(rd, h, M.tx, M.ty, M.tz, tix, tiy, tiz)) f(t);
+    });
+}
+
+// grid.y = replica; both maps
 template <typename T>
-__global__ void k_mark_tiles(MdArgs<T> m)
+__global__ void k_ra_tcount(MdArgs<T> m, RaTileMaps Ms)
 {
     const int r = blockIdx.y;
-    const RepDesc rd = m.reps[r];
     const int n = m.sc[r].n_ra;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        int h = m.ra_home[rd.ra_base + j];
-        int x2 = h % (2 * rd.nx);
-        int q = h / (2 * rd.nx);
-        int c[3] = {x2 >> 1, q % rd.ny, q / rd.ny};
-        int nn[3] = {rd.nx, rd.ny, rd.nz};
-        int tt[3] = {m.tx, m.ty, m.tz};
-        int tl[3][8], nt[3];
-        for (int d = 0; d < 3; ++d) {
-            nt[d] = 0;
-            int w = nn[d] < 7 ? nn[d] : 7;
-            for (int o = 0; o < w; ++o) {
-                int cc = wrapi(c[d] - 3 + o, nn[d]);
-                int t = cc / tt[d];
-                bool seen = false;
-                for (int k = 0; k < nt[d]; ++k) seen |= (tl[d][k] == t);
-                if (!seen) tl[d][nt[d]++] = t;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const RaTileMap &M = Ms.m[k];
+            const RepDesc rd = M.reps[r];
+            for_staging_tiles(rd, M, m.ra_home[rd.ra_base + j], [&](int t) { atomicAdd(&M.cnt[t], 1); });
+        }
+    }
+}
+
+// segment of every tile with run-aways; its flag; the fill cursors reset
+static __global__ void k_ra_toff(RaTileMaps Ms)
+{
+    for (int k = 0; k < 2; ++k) {
+        const RaTileMap &M = Ms.m[k];
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < M.ntiles; t += gridDim.x * blockDim.x) {
+            const int c = M.cnt[t];
+            int flag = 0;
+            if (c > 0) {
+                const int o = atomicAdd(&M.aux[0], c);
+                M.off[t] = o;
+                flag = (o + c <= M.cap && c <= kRaSortSeg) ? 1 : 2;
+                if (flag == 1 && c > 1) M.nz[atomicAdd(&M.aux[1], 1)] = t;
+            }
+            M.flag[t] = flag;
+            M.fill[t] = 0;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_ra_tfill(MdArgs<T> m, RaTileMaps Ms)
+{
+    const int r = blockIdx.y;
+    const int n = m.sc[r].n_ra;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const RaTileMap &M = Ms.m[k];
+            const RepDesc rd = M.reps[r];
+            for_staging_tiles(rd, M, m.ra_home[rd.ra_base + j], [&](int t) {
+                if (M.flag[t] == 1) M.list[M.off[t] + atomicAdd(&M.fill[t], 1)] = j;
+            });
+        }
+    }
+}
+
+// one warp per tile with two or more entries: bitonic sort of its segment
+// in shared memory (ascending list index = list order)
+constexpr int kRaSortWarps = 4;
+static __global__ void __launch_bounds__(32 * kRaSortWarps) k_ra_tsort(RaTileMaps Ms)
+{
+    __shared__ int buf[kRaSortWarps][kRaSortSeg];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int *b = buf[w];
+    const RaTileMap &M = Ms.m[blockIdx.y];
+    const int nz = M.aux[1];
+    for (int q = blockIdx.x * kRaSortWarps + w; q < nz; q += gridDim.x * kRaSortWarps) {
+        const int t = M.nz[q];
+        const int c = M.cnt[t], o = M.off[t];
+        int P = 32;
+        while (P < c) P <<= 1;
+        for (int i = lane; i < P; i += 32) b[i] = i < c ? M.list[o + i] : 0x7FFFFFFF;
+        __syncwarp();
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int i = lane; i < P; i += 32) {
+                    const int l = i ^ jj;
+                    if (l > i) {
+                        const int x = b[i], y = b[l];
+                        const bool up = (i & k) == 0;
+                        if ((x > y) == up) {
+                            b[i] = y;
+                            b[l] = x;
+                        }
+                    }
+                }
+                __syncwarp();
             }
         }
-        for (int a = 0; a < nt[2]; ++a)
-            for (int b = 0; b < nt[1]; ++b)
-                for (int e = 0; e < nt[0]; ++e)
-                    m.tile_flag[rd.tile_base + (tl[2][a] * rd.nty + tl[1][b]) * rd.ntx + tl[0][e]] = 1;
+        for (int i = lane; i < c; i += 32) M.list[o + i] = b[i];
+        __syncwarp();
     }
 }
 
@@ -462,6 +594,7 @@ struct RaGatherArgs {
     T *ra_ax, *ra_ay, *ra_az;
     double *ra_vx, *ra_vy, *ra_vz;
     int energy;
+    int tx, ty, tz;  // tile shape of g's map (its per-tile run-away index)
 };
 
 template <typename T>
@@ -538,7 +671,18 @@ __global__ void __launch_bounds__(256) k_ra_gather(const __grid_constant__ RaGat
                 }
             }
         }
-        for (int k = lane; k < n; k += 32) {
+        // the other run-aways: those of the home tile's index entry (every
+        // run-away within rc of this one is among them), else the whole
+        // list; either way lane l takes the list indices k = l mod 32 in
+        // ascending order, so the sums do not depend on the index
+        const int tix = hcx / ra.tx, tiy = hcy / ra.ty, tiz = hcz / ra.tz;
+        const int tl = rd.tile_base + (tiz * rd.nty + tiy) * rd.ntx + tix;
+        const bool indexed = a.tile_flag[tl] == 1;
+        const int nk = indexed ? a.ra_tcnt[tl] : (n + 31 - lane) / 32;
+        const int *klist = indexed ? a.ra_tlist + a.ra_toff[tl] : nullptr;
+        for (int kq = 0; kq < nk; ++kq) {
+            const int k = indexed ? klist[kq] : lane + 32 * kq;
+            if (indexed && (k & 31) != lane) continue;
             if (k == j) continue;
             int Xk, Yk, Zk;
             site_lat(a.ra_home[B + k], rd.nx, rd.ny, Xk, Yk, Zk);

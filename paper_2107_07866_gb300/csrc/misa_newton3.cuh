@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_density_n3(const __grid_const
             const Vec4<float> ua{A.x, A.z, B.x, 0.f}, ub{A.y, A.w, B.y, 0.f};
             while (true) {
                 __syncthreads();
-                const int cnt = stage_runaways<float, TX, TY, TZ, false>(a, L, nra, pos, sm.rh, sm.ru, sm.st);
+                const int cnt = stage_runaways<float, TX, TY, TZ, false>(a, L, tile, nra, pos, sm.rh, sm.ru, sm.st);
                 if (cnt == 0) break;
                 if (live_a) ra_density_site(a, L, cnt, sm.rh, sm.ru, ua, sx, sy, sza, ra, st);
                 if (live_b) ra_density_site(a, L, cnt, sm.rh, sm.ru, ub, sx, sy, szb, rb, st);

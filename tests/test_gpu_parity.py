@@ -458,3 +458,31 @@ def test_newton3_density_variant_trajectory(misa, pot, oracle, opot):
         with pytest.raises(misa.MisaError) as e:
             s.set_density_variant(1)
         assert e.value.code == misa.MISA_EINVAL
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_runaway_index_with_many_interstitials(misa, pot, oracle, opot, prec):
+    # 1,100 atoms on octahedral interstitial points of a 12^3-cell box: the
+    # per-tile run-away index of a large tile overflows its sortable segment
+    # (the tile scans the whole list), small tiles are indexed; every tile
+    # shape gives bitwise the same result, and the oracle's
+    n, nint = 12, 1100
+    x = synth.interstitial_snapshot(n, n, n, 0.05, nint, 21)
+    L = synth.box(n, n, n)
+    rho_o, _, e_o, f_o = oracle.eam(opot, x, L, mode=1)
+    ref = None
+    for t in misa.tile_indices(prec):
+        with misa.Sim(pot, n, precision=prec, tile=t) as s:
+            s.set_state(x)
+            f = s.forces()
+            rho = s.density()
+            _, _, e = s.energies(per_atom=True)
+            st = s.stats()
+        assert st["n_runaway"] == nint and st["status"] & 0x3 == 0
+        assert nerr(f, f_o) < TOL[prec], (t, nerr(f, f_o))
+        assert nerr(rho, rho_o) < TOL[prec] and nerr(e, e_o) < TOL[prec]
+        if ref is None:
+            ref = (f, rho, e)
+        else:
+            for a_, b_ in zip(ref, (f, rho, e)):
+                np.testing.assert_array_equal(a_, b_)
