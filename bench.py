@@ -66,9 +66,15 @@ NCU_WAVEFRONTS = {"source_sha": "8041a34556cc9d5e", "density": (27.3, 16.4), "fo
 
 
 def kernel_source_sha():
+    """Hash of every CUDA source and header of the library (the ncu figures
+    below are valid only for the sources they were captured on)."""
     h = hashlib.sha256()
-    for f in ("misa_common.cuh", "misa_kernels.cuh", "misa_packed.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2107_07866_gb300", "csrc", f), "rb").read())
+    d = os.path.join(ROOT, "paper_2107_07866_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "misa.h"), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -657,7 +663,7 @@ def run_gpu(args):
     sim = fresh("fp32")
     tile_used = sim.tile()
     tile_force = sim.tile_force()
-    run_length = w.get("run_length", 0)
+    run_length = w.get("run_length", 0) if args.run_length is None else args.run_length
     pre = max(args.warmup, run_length - args.steps)
     checkpoints = [pre + args.steps] + [c for c in w.get("checkpoints", ()) if c <= pre + args.steps]
     errs32 = {}
@@ -887,6 +893,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--run-length", type=int, default=None,
+                    help="step at which the timed steps end (default: the workload's; 0: right after warm-up)")
     ap.add_argument("--no-ra-scan", action="store_true", help="skip the run-away load scan (c2)")
     ap.add_argument("--no-newton3", action="store_true", help="skip the Newton-3 density-pass comparison")
     ap.add_argument("--no-oracle-err", action="store_true",

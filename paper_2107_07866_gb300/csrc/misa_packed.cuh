@@ -549,35 +549,6 @@ struct PThread {
     }
 };
 
-// This thread's sites in the tile at L, packed: in a tile cut by the box
-// edge the threads of each parity take the cells inside the box in order
-// ((x, y, z') over the cut extents), so that whole warps stay busy and the
-// threads left over have no site (a full tile keeps the PThread mapping).
-// in_a / in_b: the thread's two sites exist.
-template <int TX, int TY, int TZ>
-struct PCells {
-    PThread<TX, TY, TZ> c;
-    bool in_a, in_b;
-    __device__ __forceinline__ PCells(const TileLoc &L, const PThread<TX, TY, TZ> &th) : c(th)
-    {
-        using G = PTile<TX, TY, TZ>;
-        const int vx = min(TX, L.rd.nx - L.c0x), vy = min(TY, L.rd.ny - L.c0y), vz = min(TZ, L.rd.nz - L.c0z);
-        const int vh = min(G::HZ, vz);
-        if (vx == TX && vy == TY && vh == G::HZ) {
-            in_a = true;
-            in_b = L.c0z + th.lz + G::HZ < L.rd.nz;
-            return;
-        }
-        const int q = threadIdx.x % G::PER_PAR;
-        in_a = q < vx * vy * vh;
-        c.lx = q % vx;
-        c.ly = (q / vx) % vy;
-        c.lz = in_a ? q / (vx * vy) : 0;
-        in_b = in_a && c.lz + G::HZ < vz;
-        c.slot = c.p * G::PLANE + ((c.lz + 2) * G::SY + (c.ly + 2)) * G::SX + (c.lx + 2);
-    }
-};
-
 __device__ __forceinline__ long long site_of(const TileLoc &L, int lx, int ly, int lz, int p)
 {
     return L.rd.site_base + (((long long)(L.c0z + lz) * L.rd.ny + (L.c0y + ly)) * L.rd.nx + (L.c0x + lx)) * 2 + p;
@@ -602,10 +573,10 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_density_p(const __grid_consta
     fill_rep_cache<float>(a, sm.rep);
     __syncthreads();
 
-    const PThread<TX, TY, TZ> th0;
+    const PThread<TX, TY, TZ> th;
     // offset records read from the kernel parameters (constant bank): warp-
     // uniform, so they stay off the shared-memory pipe
-    const float4 *po = &a.offp[th0.p][0][0];
+    const float4 *po = &a.offp[th.p][0][0];
     const float2 S2 = p_dup(a.S);
     unsigned st = 0;
     int buf = 0;
@@ -634,9 +605,9 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_density_p(const __grid_consta
             U = stage_tile_p<TX, TY, TZ, false>(a, L, cA, sm.red);
         }
         const bool has_ra = a.tile_flag[tile] != 0 && nra > 0;
-        const PCells<TX, TY, TZ> pc(L, th0);
-        const PThread<TX, TY, TZ> &th = pc.c;
-        const bool in_a = pc.in_a, in_b = pc.in_b;
+        const bool in_xy = (L.c0x + th.lx < L.rd.nx) && (L.c0y + th.ly < L.rd.ny);
+        const bool in_a = in_xy && (L.c0z + th.lz < L.rd.nz);
+        const bool in_b = in_xy && (L.c0z + th.lz + G::HZ < L.rd.nz);
         const float4 A = cA[th.slot], B = cB[th.slot];
         PairSites ui;
         ui.ux = make_float2(A.x, A.y);
@@ -718,10 +689,10 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_force_p(const __grid_constant
     fill_rep_cache<float>(a, sm.rep);
     __syncthreads();
 
-    const PThread<TX, TY, TZ> th0;
+    const PThread<TX, TY, TZ> th;
     // offset records read from the kernel parameters (constant bank): warp-
     // uniform, so they stay off the shared-memory pipe
-    const float4 *po = &a.offp[th0.p][0][0];
+    const float4 *po = &a.offp[th.p][0][0];
     const float2 S2 = p_dup(a.S);
     const float conv = (float)a.acc_conv;
     unsigned st = 0;
@@ -745,9 +716,9 @@ __global__ void __launch_bounds__(TX *TY *TZ, 1) k_force_p(const __grid_constant
         const float U = tile_umax_p<TX, TY, TZ, false>(cA, sm.red);
         const double hdt = 0.5 * dt_rep;
         const bool has_ra = a.tile_flag[tile] != 0 && nra > 0;
-        const PCells<TX, TY, TZ> pc(L, th0);
-        const PThread<TX, TY, TZ> &th = pc.c;
-        const bool in_a = pc.in_a, in_b = pc.in_b;
+        const bool in_xy = (L.c0x + th.lx < L.rd.nx) && (L.c0y + th.ly < L.rd.ny);
+        const bool in_a = in_xy && (L.c0z + th.lz < L.rd.nz);
+        const bool in_b = in_xy && (L.c0z + th.lz + G::HZ < L.rd.nz);
         const float4 A = cA[th.slot], B = cB[th.slot];
         PairSites ui;
         ui.ux = make_float2(A.x, A.y);
