@@ -704,8 +704,11 @@ int launch_forces(misa_sim *s, int kick, bool energy, bool step_marks = false)
     ra.ra_vx = s->ra_v[0]; ra.ra_vy = s->ra_v[1]; ra.ra_vz = s->ra_v[2];
     ra.energy = energy ? 1 : 0;
     ra.tx = kTiles[s->tile].tx; ra.ty = kTiles[s->tile].ty; ra.tz = kTiles[s->tile].tz;
-    // one warp per run-away: enough warps for a full list
-    const int rab = (s->cap + 7) / 8 < 16 ? 16 : ((s->cap + 7) / 8 > 512 ? 512 : (s->cap + 7) / 8);
+    // one warp per run-away (grid-stride): four CTAs of 8 warps per SM over
+    // all replicas, at least 16 per replica, never more than a full list
+    int rab = 4 * s->nsm / s->nrep;
+    if (rab < 16) rab = 16;
+    if (rab > (s->cap + 7) / 8) rab = (s->cap + 7) / 8 > 16 ? (s->cap + 7) / 8 : 16;
     if (step_marks) mark(s);  // end of the list phase
     launch_density<T>(s, gd, energy);
     if (step_marks) mark(s);
@@ -871,9 +874,9 @@ int create_impl(misa_sim *s)
     s->reps_fd = (RepDesc *)dalloc(s, sizeof(RepDesc) * s->nrep);
     s->tile_rep_f = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap);
     s->tile_flag_f = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap);
-    // a run-away is staged by at most 3 tiles per axis (7-cell window, tiles
-    // of at least 4 cells)
-    s->rt_cap = 27LL * s->cap * s->nrep;
+    // a run-away is staged by at most 4 tiles per axis (7-cell window, tiles
+    // of at least 4 cells, a partial last tile across the wrap)
+    s->rt_cap = 64LL * s->cap * s->nrep;
     if (s->rt_cap > 0x7FFFFFFFLL) s->rt_cap = 0x7FFFFFFFLL;
     // counts and cursors of both maps in one block each (one memset per step)
     int *cnt2 = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap * 2);
@@ -1356,6 +1359,12 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
     int nsh = 0;
     while (nsh < kLVec.nshell && kLVec.shell_n2[nsh] <= roff * roff) ++nsh;
     a.nvec = kLVec.shell_begin[nsh];
+    // the per-tile run-away index of the density map that the forward pass
+    // built (the list does not change during the evaluation): sites and
+    // run-aways scan only the run-aways within reach, in list order
+    a.tile_flag = s->tile_flag;
+    a.tx = kTiles[s->tile].tx; a.ty = kTiles[s->tile].ty; a.tz = kTiles[s->tile].tz;
+    a.ra_toff = s->rt_off[0]; a.ra_tcnt = s->rt_cnt[0]; a.ra_tlist = s->rt_list[0];
     k_adj_lambda<T><<<dim3(nb, s->nrep), 256, 0, s->st>>>(a, s->partial);
     k_sum_stage2<<<s->nrep, 1024, 0, s->st>>>(s->partial, nb, s->red_out + s->nrep);  // sum |F - Fref|^2
     k_adj_dl<T><<<site_grid(s), 256, 0, s->st>>>(a);
@@ -1954,11 +1963,11 @@ constexpr size_t kStaticAlign = 256;
 // upper bound of the carve below for either precision: per site <= 160 B,
 // per run-away slot <= 512 B, per knot <= 160 B, two flags and two map
 // entries per cell (density and force tile maps), the two maps' run-away
-// index (four ints per cell, 27 entries per run-away slot), two replica
+// index (four ints per cell, 64 entries per run-away slot), two replica
 // tables, the scalars, and the alignment padding
 constexpr size_t kStaticNeed = 160ull * MISA_STATIC_MAX_ATOMS + 512ull * MISA_STATIC_RUNAWAY_CAP +
                                160ull * MISA_STATIC_MAX_KNOTS + 16ull * (MISA_STATIC_MAX_ATOMS / 2) +
-                               2 * (16ull * (MISA_STATIC_MAX_ATOMS / 2) + 8 + 4 * 27ull * MISA_STATIC_RUNAWAY_CAP) +
+                               2 * (16ull * (MISA_STATIC_MAX_ATOMS / 2) + 8 + 4 * 64ull * MISA_STATIC_RUNAWAY_CAP) +
                                sizeof(DevScalars) + 2 * sizeof(RepDesc) + 128 * kStaticAlign;
 static_assert(kStaticNeed <= MISA_STATIC_SCRATCH_BYTES, "static scratch too small");
 
@@ -2031,7 +2040,7 @@ size_t carve_static(misa_sim *s, unsigned char *base, int nk)
     s->reps_fd = c.take<RepDesc>(1);
     s->tile_flag_f = c.take<int>(ns / 2);
     s->tile_rep_f = c.take<int>(ns / 2);
-    s->rt_cap = 27LL * (long long)cap;
+    s->rt_cap = 64LL * (long long)cap;
     int *cnt2 = c.take<int>(ns);  // ntile_cap = ns / 2 per map
     int *aux2 = c.take<int>(4);
     for (int k = 0; k < 2; ++k) {

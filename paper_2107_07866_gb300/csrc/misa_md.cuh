@@ -437,32 +437,62 @@ struct RaTileMap {
     int cap;     // list entries
 };
 
-// calls f(global tile) for every tile of rd whose staged set holds a
-// run-away with home site h
+// The distinct tiles along one axis that hold a cell within 3 of cell c
+// (periodic, the whole axis for boxes under 7 cells), kept in registers (no
+// local-memory arrays).  Tiles have 4 or more cells, so the 7-cell window
+// meets at most four: two across the wrap (a partial last tile and the one
+// before it) and two from cell 0 on.
+struct AxisTiles {
+    int t0, t1, t2, t3, n;
+};
+
+__device__ __forceinline__ AxisTiles axis_tiles(int c, int nn, int tt)
+{
+    AxisTiles r{-1, -1, -1, -1, 0};
+    const int w = nn < 7 ? nn : 7;
+    for (int o = 0; o < w; ++o) {
+        const int t = wrapi(c - 3 + o, nn) / tt;
+        if (t == r.t0 || t == r.t1 || t == r.t2 || t == r.t3) continue;
+        if (r.n == 0) r.t0 = t;
+        else if (r.n == 1) r.t1 = t;
+        else if (r.n == 2) r.t2 = t;
+        else r.t3 = t;
+        ++r.n;
+    }
+    return r;
+}
+
+__device__ __forceinline__ int axis_tile(const AxisTiles &a, int k)
+{
+    return k == 0 ? a.t0 : (k == 1 ? a.t1 : (k == 2 ? a.t2 : a.t3));
+}
+
+// calls f(global tile, tile coords) for every tile of rd within 3 cells of
+// the home cell of site h (a superset of the tiles that stage the run-away
+// for small boxes; exactly those when every axis has tile + 6 cells or more)
 template <typename F>
 __device__ __forceinline__ void for_ra_tiles(const RepDesc &rd, int h, int tx, int ty, int tz, F f)
 {
-    int x2 = h % (2 * rd.nx);
-    int q = h / (2 * rd.nx);
-    int c[3] = {x2 >> 1, q % rd.ny, q / rd.ny};
-    int nn[3] = {rd.nx, rd.ny, rd.nz};
-    int tt[3] = {tx, ty, tz};
-    int tl[3][8], nt[3];
-    for (int d = 0; d < 3; ++d) {
-        nt[d] = 0;
-        int w = nn[d] < 7 ? nn[d] : 7;
-        for (int o = 0; o < w; ++o) {
-            int cc = wrapi(c[d] - 3 + o, nn[d]);
-            int t = cc / tt[d];
-            bool seen = false;
-            for (int k = 0; k < nt[d]; ++k) seen |= (tl[d][k] == t);
-            if (!seen) tl[d][nt[d]++] = t;
+    const int x2 = h % (2 * rd.nx);
+    const int q = h / (2 * rd.nx);
+    const AxisTiles ax = axis_tiles(x2 >> 1, rd.nx, tx), ay = axis_tiles(q % rd.ny, rd.ny, ty),
+                    az = axis_tiles(q / rd.ny, rd.nz, tz);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        if (a >= az.n) break;
+        const int tiz = axis_tile(az, a);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            if (b >= ay.n) break;
+            const int tiy = axis_tile(ay, b);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (e >= ax.n) break;
+                const int tix = axis_tile(ax, e);
+                f(rd.tile_base + (tiz * rd.nty + tiy) * rd.ntx + tix, tix, tiy, tiz);
+            }
         }
     }
-    for (int a = 0; a < nt[2]; ++a)
-        for (int b = 0; b < nt[1]; ++b)
-            for (int e = 0; e < nt[0]; ++e) f(rd.tile_base + (tl[2][a] * rd.nty + tl[1][b]) * rd.ntx + tl[0][e], tl[0][e],
-                                              tl[1][b], tl[2][a]);
 }
 
 // the stage predicate of tile (tix, tiy, tiz) of a tx x ty x tz map (the

@@ -461,18 +461,20 @@ def test_newton3_density_variant_trajectory(misa, pot, oracle, opot):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_runaway_index_with_many_interstitials(misa, pot, oracle, opot, prec):
-    # 1,100 atoms on octahedral interstitial points of a 12^3-cell box: the
+@pytest.mark.parametrize("dims,nint", [((12, 12, 12), 1100), ((13, 9, 10), 300)])
+def test_runaway_index_with_many_interstitials(misa, pot, oracle, opot, prec, dims, nint):
+    # atoms on octahedral interstitial points.  12^3 cells, 1,100 of them: the
     # per-tile run-away index of a large tile overflows its sortable segment
-    # (the tile scans the whole list), small tiles are indexed; every tile
-    # shape gives bitwise the same result, and the oracle's
-    n, nint = 12, 1100
-    x = synth.interstitial_snapshot(n, n, n, 0.05, nint, 21)
-    L = synth.box(n, n, n)
+    # (the tile scans the whole list), small tiles are indexed.  13 x 9 x 10
+    # cells: 4-cell tiles leave partial last tiles of 1-2 cells, so a
+    # run-away's window across the periodic wrap meets four tiles along an
+    # axis.  Every tile shape gives bitwise the same result, and the oracle's
+    x = synth.interstitial_snapshot(*dims, 0.05, nint, 21)
+    L = synth.box(*dims)
     rho_o, _, e_o, f_o = oracle.eam(opot, x, L, mode=1)
     ref = None
     for t in misa.tile_indices(prec):
-        with misa.Sim(pot, n, precision=prec, tile=t) as s:
+        with misa.Sim(pot, *dims, precision=prec, tile=t) as s:
             s.set_state(x)
             f = s.forces()
             rho = s.density()
