@@ -805,7 +805,7 @@ def run_gpu(args):
             s.set_state_staged()
             if it + 1 < iters:
                 s.stage_state(x_host, v_host)    # H2D of the next state, beside this one's steps
-            s.step(inner)
+            s.step(inner, energies=True)         # the last step also evaluates E_i
             # D2H: per-atom energies E_i (and the totals) of the state reached
             pe, _, _ = s.energies(per_atom=True, out=e_host.numpy())
             pe_sum += pe
@@ -815,7 +815,8 @@ def run_gpu(args):
                "h2d_bytes_per_step": 48 * natoms, "d2h_bytes_per_step": 8 * natoms + 16,
                "iterations": iters,
                "note": f"one e2e step = state (x, v) from pinned host memory + {inner} MD steps + the per-atom "
-                       "energies E_i of the state reached back to pinned host memory (an energy evaluation); "
+                       "energies E_i of the state reached (evaluated inside the last step's passes) back to "
+                       "pinned host memory; "
                        "each state is staged on the library's copy stream while the previous one is simulated"}
         s.close()
         del s

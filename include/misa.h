@@ -193,6 +193,16 @@ int misa_insert_pka_replica(misa_sim *s, int32_t r, double energy_eV, const doub
  * only; never synchronises. */
 int misa_step(misa_sim *s, int n);
 
+/* misa_step(s, n) whose last step also evaluates the per-atom energies E_i
+ * (Eq. eam_base: F(rho_i) + half the pair terms) inside its own density and
+ * force passes -- the "calculate and output physical quantities" stage of
+ * Fig. 1's MD loop at the output cadence -- so that a following
+ * misa_get_energies / misa_replica_energies reads them without evaluating
+ * the potential again.  Results are bitwise those of misa_step followed by
+ * misa_get_energies.  The energies stay valid until the positions, the
+ * tables or the species change.  MISA_EINVAL for n < 1.  Launches only. */
+int misa_step_energies(misa_sim *s, int n);
+
 /* misa_step captures one step as a CUDA graph on an internal stream (joined
  * to the handle's stream by events) and replays it; enable = 0 launches the
  * kernels one by one instead.  Timing (misa_timing_enable) always launches

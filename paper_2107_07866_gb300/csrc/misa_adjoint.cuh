@@ -171,15 +171,15 @@ __device__ __forceinline__ void visit_site(const A &a, const RepDesc &rd, int nr
         if (adj_pair<T>(a, o.x, o.y, o.z, a.ux[t] - uix, a.uy[t] - uiy, a.uz[t] - uiz, false, t, P)) fn(P);
     }
     if (nra == 0) return;
-    // the run-aways of the site's tile index entry (list order), else the
-    // whole list
+    // the run-aways of the site's tile index entry (list order) when the
+    // list is longer than kRaScanMax, else the whole list
     const int *jl = nullptr;
     int nj = nra;
     if (a.tile_flag) {
         const int tl = rd.tile_base + ((cz / a.tz) * rd.nty + cy / a.ty) * rd.ntx + (x2 >> 1) / a.tx;
         const int f = a.tile_flag[tl];
         if (!f) return;
-        if (f == 1 && a.ra_tlist) {
+        if (f == 1 && a.ra_tlist && nra > kRaScanMax) {
             jl = a.ra_tlist + a.ra_toff[tl];
             nj = a.ra_tcnt[tl];
         }
@@ -237,9 +237,10 @@ __device__ __forceinline__ void visit_ra(const A &a, const RepDesc &rd, int nra,
     }
     const int Lx = 2 * rd.nx, Ly = 2 * rd.ny, Lz = 2 * rd.nz;
     // the other run-aways: the home tile's index entry (lane l takes the list
-    // indices k = l mod 32, ascending), else the whole list
+    // indices k = l mod 32, ascending) when the list is longer than
+    // kRaScanMax, else the whole list
     const int *kl = nullptr;
-    if (a.tile_flag && a.ra_tlist) {
+    if (a.tile_flag && a.ra_tlist && nra > kRaScanMax) {
         const int tl = rd.tile_base + ((hcz / a.tz) * rd.nty + hcy / a.ty) * rd.ntx + hcx / a.tx;
         if (a.tile_flag[tl] == 1) kl = a.ra_tlist + a.ra_toff[tl];
         if (kl) nra = a.ra_tcnt[tl];

@@ -219,6 +219,14 @@ struct misa_sim {
     bool use_graph = true;
     cudaGraphExec_t graph = nullptr;
     long long graph_launches = 0;  // kernels inside one replay
+    cudaGraphExec_t graph_e = nullptr;  // the same step with per-atom energies in its force passes
+    long long graph_e_launches = 0;
+    bool energy_valid = false;  // esite / ra_e hold the energies of the current positions
+    // the per-tile run-away index matches the current run-away list and tile
+    // maps (a force evaluation outside a step then skips its rebuild); a step
+    // being captured into a graph always rebuilds it
+    bool ra_index_valid = false;
+    bool capturing = false;
 };
 
 namespace {
@@ -235,6 +243,14 @@ int fail(misa_sim *s, int code, const std::string &msg)
         cudaError_t e_ = (call);                                                                   \
         if (e_ != cudaSuccess) return fail(s, MISA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
+
+// drops the captured step graphs (tile shapes, tables or species changed)
+void drop_graphs(misa_sim *s)
+{
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    if (s->graph_e) cudaGraphExecDestroy(s->graph_e);
+    s->graph = s->graph_e = nullptr;
+}
 
 void *dalloc(misa_sim *s, size_t bytes)
 {
@@ -518,6 +534,7 @@ int configure(misa_sim *s, int td, int tf)
         return fail(s, MISA_EINVAL, "tile shape not built for this precision");
     s->tile = td;
     s->tile_f = tf;
+    s->ra_index_valid = false;
     std::vector<int> map, map_f;
     std::vector<RepDesc> reps_f = s->reps;
     s->ntiles = build_tile_map(s, kTiles[td], s->reps, map);
@@ -552,10 +569,7 @@ int configure(misa_sim *s, int td, int tf)
     CK(tile_attrs<T>(tf, true, tile_launch(s)));
     CK(cudaFuncSetAttribute(k_ra_sort<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)(sizeof(unsigned long long) * kSortMax)));
-    if (s->graph) {
-        cudaGraphExecDestroy(s->graph);
-        s->graph = nullptr;
-    }
+    drop_graphs(s);
     return MISA_OK;
 }
 
@@ -564,6 +578,7 @@ int configure(misa_sim *s, int td, int tf)
 template <typename T>
 int mark_tiles(misa_sim *s)
 {
+    if (s->ra_index_valid && !s->capturing) return MISA_OK;
     MdArgs<T> m = md_args<T>(s);
     RaTileMaps Ms;
     int nt = 0;
@@ -589,6 +604,7 @@ int mark_tiles(misa_sim *s)
     k_ra_tfill<T><<<lg, 256, 0, s->st>>>(m, Ms);
     k_ra_tsort<<<dim3(s->nsm, 2), 32 * kRaSortWarps, 0, s->st>>>(Ms);
     s->launches += 4;
+    s->ra_index_valid = !s->capturing;
     return MISA_OK;
 }
 
@@ -725,9 +741,10 @@ int launch_forces(misa_sim *s, int kick, bool energy, bool step_marks = false)
 
 // the launches of one MD step on s->st
 template <typename T>
-int launch_step(misa_sim *s)
+int launch_step(misa_sim *s, bool energy = false)
 {
     MdArgs<T> m = md_args<T>(s);
+    s->ra_index_valid = false;  // the list phase below changes the run-away list
     mark(s);
     k_begin_step<T><<<rep_blocks(s), 128, 0, s->st>>>(m);
     k_ra_kick_drift<T><<<list_grid(s), 256, 0, s->st>>>(m);
@@ -737,7 +754,7 @@ int launch_step(misa_sim *s)
     k_reassign_promote<T><<<list_grid(s), 256, 0, s->st>>>(m, 0);
     k_ra_sort<T><<<s->nrep, 1024, sizeof(unsigned long long) * kSortMax, s->st>>>(m);
     s->launches += 6;
-    int rc = launch_forces<T>(s, 1, false, true);
+    int rc = launch_forces<T>(s, 1, energy, true);
     if (rc) return rc;
     k_end_step<T><<<rep_blocks(s), 128, 0, s->st>>>(m);
     mark(s);
@@ -746,37 +763,55 @@ int launch_step(misa_sim *s)
     return MISA_OK;
 }
 
-// One step captured as a CUDA graph on an internal stream, replayed n times;
-// the caller's stream is joined by events.
+// One step captured as a CUDA graph on an internal stream (a second graph
+// for the step whose force passes also evaluate per-atom energies), replayed
+// n times, the last one the energy step when asked; the caller's stream is
+// joined by events.
 template <typename T>
-int step_graph(misa_sim *s, int n)
+int capture_step(misa_sim *s, bool energy, cudaGraphExec_t *out, long long *launches)
 {
-    if (!s->graph) {
-        cudaStream_t user = s->st;
-        s->st = s->gst;
-        long long l0 = s->launches;
-        CK(cudaStreamBeginCapture(s->gst, cudaStreamCaptureModeThreadLocal));
-        int rc = launch_step<T>(s);
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(s->gst, &g);
-        s->st = user;
-        if (rc) {
-            if (g) cudaGraphDestroy(g);
-            return rc;
-        }
-        if (e != cudaSuccess) return fail(s, MISA_ECUDA, std::string("step capture: ") + cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&s->graph, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return fail(s, MISA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-        s->graph_launches = s->launches - l0;
-        s->launches = l0;
+    cudaStream_t user = s->st;
+    s->st = s->gst;
+    long long l0 = s->launches;
+    CK(cudaStreamBeginCapture(s->gst, cudaStreamCaptureModeThreadLocal));
+    s->capturing = true;
+    int rc = launch_step<T>(s, energy);
+    s->capturing = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->gst, &g);
+    s->st = user;
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(s, MISA_ECUDA, std::string("step capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(s, MISA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    *launches = s->launches - l0;
+    s->launches = l0;
+    return MISA_OK;
+}
+
+template <typename T>
+int step_graph(misa_sim *s, int n, bool energy_last = false)
+{
+    const int plain = energy_last ? n - 1 : n;
+    if (plain > 0 && !s->graph) {
+        int rc = capture_step<T>(s, false, &s->graph, &s->graph_launches);
+        if (rc) return rc;
+    }
+    if (energy_last && !s->graph_e) {
+        int rc = capture_step<T>(s, true, &s->graph_e, &s->graph_e_launches);
+        if (rc) return rc;
     }
     CK(cudaEventRecord(s->ev_in, s->st));
     CK(cudaStreamWaitEvent(s->gst, s->ev_in, 0));
-    for (int k = 0; k < n; ++k) CK(cudaGraphLaunch(s->graph, s->gst));
+    for (int k = 0; k < plain; ++k) CK(cudaGraphLaunch(s->graph, s->gst));
+    if (energy_last) CK(cudaGraphLaunch(s->graph_e, s->gst));
     CK(cudaEventRecord(s->ev_out, s->gst));
     CK(cudaStreamWaitEvent(s->st, s->ev_out, 0));
-    s->launches += s->graph_launches * n;
+    s->launches += s->graph_launches * plain + (energy_last ? s->graph_e_launches : 0);
     return MISA_OK;
 }
 
@@ -975,6 +1010,7 @@ int create_impl(misa_sim *s)
     if (rc) return rc;
     MdArgs<T> m = md_args<T>(s);
     k_init_crystal<T><<<site_grid(s), 256, 0, s->st>>>(m);
+    s->ra_index_valid = false;
     CK(cudaGetLastError());
     if (s->p.tile == 0) {
         rc = autotune<T>(s);
@@ -992,6 +1028,7 @@ int set_state_dev(misa_sim *s, const double *xd, const double *vd, cudaEvent_t d
 {
     const long long N = s->ns;
     MdArgs<T> m = md_args<T>(s);
+    s->ra_index_valid = false;
     k_reset_list<T><<<rep_blocks(s), 128, 0, s->st>>>(m);
     k_clear_sites<T><<<site_grid(s), 256, 0, s->st>>>(m);
     k_state_claim<T><<<site_grid(s), 256, 0, s->st>>>(m, xd, s->aux_int, s->out_buf);
@@ -1024,8 +1061,13 @@ int set_state_impl(misa_sim *s, const double *x, const double *v)
 template <typename T>
 int reduce_energy(misa_sim *s, double *pe, double *ke, double *per_atom)
 {
-    int rc = launch_forces<T>(s, 0, true);
-    if (rc) return rc;
+    // per-atom energies of the current positions: from the last step when
+    // it evaluated them (misa_step_energies), else one evaluation now
+    if (!s->energy_valid) {
+        int rc = launch_forces<T>(s, 0, true);
+        if (rc) return rc;
+        s->energy_valid = true;
+    }
     MdArgs<T> m = md_args<T>(s);
     const int nb = red_blocks(s);
     k_sum_stage1<T><<<dim3(nb, s->nrep), 256, 0, s->st>>>(m, 0, s->partial);
@@ -1174,10 +1216,7 @@ int set_tables_impl(misa_sim *s, const double *f, const double *phi, const doubl
                                                             (Vec4<T> *)s->tab_F, (Vec4<T> *)s->tab_d0,
                                                             (Vec2<T> *)s->tab_d1);
     CK(cudaGetLastError());
-    if (s->nsp != 1 && s->graph) {  // back to the single-type passes
-        cudaGraphExecDestroy(s->graph);
-        s->graph = nullptr;
-    }
+    if (s->nsp != 1) drop_graphs(s);  // back to the single-type passes
     s->nsp = 1;
     return refresh<T>(s, true);
 }
@@ -1194,10 +1233,7 @@ int set_species_impl(misa_sim *s, int nsp, const double *f, const double *F, con
         CK(cudaMemcpy(pF.data(), F, sizeof(double) * n, cudaMemcpyDefault));
         CK(cudaMemcpy(pp.data(), phi, sizeof(double) * n, cudaMemcpyDefault));
         s->nsp = 1;
-        if (s->graph) {
-            cudaGraphExecDestroy(s->graph);
-            s->graph = nullptr;
-        }
+        drop_graphs(s);
         return set_tables_impl<T>(s, pf.data(), pp.data(), pF.data());
     }
     std::vector<int8_t> ht((size_t)s->ns);
@@ -1269,10 +1305,7 @@ int set_species_impl(misa_sim *s, int nsp, const double *f, const double *F, con
         int rc = configure<T>(s, s->tile, s->tile_f);  // the alloy passes' kernel attributes
         if (rc) return rc;
     }
-    if (s->graph) {
-        cudaGraphExecDestroy(s->graph);
-        s->graph = nullptr;
-    }
+    drop_graphs(s);
     int rc = refresh<T>(s, true);
     if (rc) return rc;
     return check_status(s);
@@ -1465,7 +1498,7 @@ void misa_destroy(misa_sim *s)
     cudaStreamSynchronize(s->st);
     if (s->gst) cudaStreamSynchronize(s->gst);
     if (s->cst) cudaStreamSynchronize(s->cst);
-    if (s->graph) cudaGraphExecDestroy(s->graph);
+    drop_graphs(s);
     for (unsigned long long t : {s->tex_f, s->tex_d0, s->tex_d1, s->tex_afv, s->tex_afd, s->tex_apd})
         if (t) cudaDestroyTextureObject((cudaTextureObject_t)t);
     for (auto e : s->ev_pool) cudaEventDestroy(e);
@@ -1501,6 +1534,7 @@ int misa_replica_info(const misa_sim *s, int32_t r, int32_t dims[3], int64_t *at
 
 int misa_set_state(misa_sim *s, const double *x, const double *v, int64_t n)
 {
+    if (s) s->energy_valid = false;
     if (!s) return MISA_EINVAL;
     if (!x || n != s->ns) return fail(s, MISA_EINVAL, "set_state: x required, n must equal natoms");
     return s->prec == MISA_FP64 ? set_state_impl<double>(s, x, v) : set_state_impl<float>(s, x, v);
@@ -1538,6 +1572,7 @@ int misa_stage_state(misa_sim *s, const double *x, const double *v, int64_t n)
 
 int misa_set_state_staged(misa_sim *s)
 {
+    if (s) s->energy_valid = false;
     if (!s) return MISA_EINVAL;
     if (!s->stg_pending) return fail(s, MISA_EINVAL, "set_state_staged: no state staged");
     CK(cudaStreamWaitEvent(s->st, s->ev_stg, 0));
@@ -1590,23 +1625,40 @@ int misa_insert_pka_replica(misa_sim *s, int32_t r, double energy, const double 
     return misa_insert_pka(s, atom, energy, dir);
 }
 
-int misa_step(misa_sim *s, int n)
+static int step_impl(misa_sim *s, int n, bool energy_last)
 {
     if (!s) return MISA_EINVAL;
     if (n < 0) return fail(s, MISA_EINVAL, "step: n < 0");
     if (n == 0) return MISA_OK;
-    if (s->use_graph && !s->timing)
-        return s->prec == MISA_FP64 ? step_graph<double>(s, n) : step_graph<float>(s, n);
-    for (int k = 0; k < n; ++k) {
-        int rc = s->prec == MISA_FP64 ? launch_step<double>(s) : launch_step<float>(s);
+    s->energy_valid = false;
+    s->ra_index_valid = false;
+    if (s->use_graph && !s->timing) {
+        int rc = s->prec == MISA_FP64 ? step_graph<double>(s, n, energy_last) : step_graph<float>(s, n, energy_last);
         if (rc) return rc;
+    } else {
+        for (int k = 0; k < n; ++k) {
+            const bool e = energy_last && k == n - 1;
+            int rc = s->prec == MISA_FP64 ? launch_step<double>(s, e) : launch_step<float>(s, e);
+            if (rc) return rc;
+        }
     }
+    s->energy_valid = energy_last;
+    s->ra_index_valid = false;
     return MISA_OK;
+}
+
+int misa_step(misa_sim *s, int n) { return step_impl(s, n, false); }
+
+int misa_step_energies(misa_sim *s, int n)
+{
+    if (s && n < 1) return fail(s, MISA_EINVAL, "step_energies: n < 1");
+    return step_impl(s, n, true);
 }
 
 int misa_set_species(misa_sim *s, int n_species, const double *f_knots, const double *F_knots,
                      const double *phi_knots, const int8_t *types)
 {
+    if (s) s->energy_valid = false;
     if (!s || n_species < 1 || n_species > kMaxSpecies || !f_knots || !F_knots || !phi_knots ||
         (n_species > 1 && !types))
         return s ? fail(s, MISA_EINVAL, "misa_set_species arguments") : MISA_EINVAL;
@@ -1649,6 +1701,7 @@ int misa_retune(misa_sim *s)
 
 int misa_set_density_variant(misa_sim *s, int32_t variant)
 {
+    if (s) s->energy_valid = false;
     if (!s) return MISA_EINVAL;
     if (variant != 0 && variant != 1)
         return fail(s, MISA_EINVAL, "density variant: 0 (full neighbour) or 1 (Newton's third law inside tiles)");
@@ -1883,10 +1936,15 @@ int misa_save(misa_sim *s, const char *path)
     if (s && s->nsp > 1) return fail(s, MISA_EINVAL, "checkpoints hold one atom type");
     return ckpt_io(s, path, true);
 }
-int misa_load(misa_sim *s, const char *path) { return ckpt_io(s, path, false); }
+int misa_load(misa_sim *s, const char *path)
+{
+    if (s) s->energy_valid = s->ra_index_valid = false;
+    return ckpt_io(s, path, false);
+}
 
 int misa_set_tables(misa_sim *s, const double *f_knots, const double *phi_knots, const double *F_knots)
 {
+    if (s) s->energy_valid = false;
     if (!s) return MISA_EINVAL;
     if (!f_knots || !phi_knots || !F_knots) return fail(s, MISA_EINVAL, "set_tables: three knot arrays required");
     return s->prec == MISA_FP64 ? set_tables_impl<double>(s, f_knots, phi_knots, F_knots)

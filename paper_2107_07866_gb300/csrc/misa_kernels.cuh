@@ -25,6 +25,12 @@
 namespace misa {
 
 constexpr int kRaChunk = 128;  // run-away atoms staged per round in a tile CTA
+// A walker that visits a run-away's or a site's run-away neighbours scans
+// the whole list when the replica has at most this many run-aways (one
+// load per entry), else its tile's index segment (two dependent loads per
+// entry, but only the entries within reach).  Both visit the pairs inside
+// rc in list order, so the results do not depend on the choice.
+constexpr int kRaScanMax = 32;
 constexpr int kRedFloats = 112; // block-reduction scratch: 33 floats, then 32 doubles from byte 192
 constexpr double kRws = 1.1180339887498949;  // max distance to the nearest bcc site: sqrt(5)/2 (a0/2 units)
 

@@ -634,6 +634,8 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
+constexpr int kRaBatch = 4;  // window sites a lane loads at once
+
 // mode 0: density (+F, F'), mode 1: force (+kick); grid.y = replica
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_ra_gather(const __grid_constant__ RaGatherArgs<T> ra)
@@ -663,23 +665,53 @@ __global__ void __launch_bounds__(256) k_ra_gather(const __grid_constant__ RaGat
         double ephi = 0.0;
         const int wx = rd.nx < 7 ? rd.nx : 7, wy = rd.ny < 7 ? rd.ny : 7, wz = rd.nz < 7 ? rd.nz : 7;
         const int W = wx * wy * wz * 2;
-        for (int c = lane; c < W; c += 32) {
-            int q = c & 1;
-            int rr = c >> 1;
-            int ox = rr % wx, oy = (rr / wx) % wy, oz = rr / (wx * wy);
-            int cx = hcx - 3 + ox, cy = hcy - 3 + oy, cz = hcz - 3 + oz;
-            long long s = rd.site_base + (((long long)wrapi(cz, rd.nz) * rd.ny + wrapi(cy, rd.ny)) * rd.nx + wrapi(cx, rd.nx)) * 2 + q;
-            if (ra.sid[s] < 0) continue;
-            int nx_ = 2 * cx + q - X, ny_ = 2 * cy + q - Y, nz_ = 2 * cz + q - Z;
-            T dx = a.ux[s] - ujx, dy = a.uy[s] - ujy, dz = a.uz[s] - ujz;
-            T qq = (dx + (T)(2 * nx_)) * dx + (dy + (T)(2 * ny_)) * dy + (dz + (T)(2 * nz_)) * dz;
-            T r2 = (T)(nx_ * nx_ + ny_ * ny_ + nz_ * nz_) + qq;
-            if (r2 < a.rc2) {
-                int seg;
-                T t, rinv;
-                bool fh;
-                direct_arg<T>(r2, a.S, a.rfloor2, seg, t, rinv, fh);
-                seg = clamp_seg<T>(seg, a.nseg, t);
+        // lane l takes the window's sites c = l, l + 32, ... in ascending
+        // order; kRaBatch of them at a time, each dependent load (site id,
+        // displacement, table segment) issued for the whole batch before the
+        // next, so the chain of load latencies is W / (32 kRaBatch) batches
+        // long rather than W / 32 sites
+        for (int c0 = lane; c0 < W; c0 += 32 * kRaBatch) {
+            long long sb[kRaBatch];
+            bool ok[kRaBatch];
+            int nb[kRaBatch][3];
+#pragma unroll
+            for (int b = 0; b < kRaBatch; ++b) {
+                const int c = c0 + 32 * b;
+                const int q = c & 1;
+                const int rr = c >> 1;
+                const int ox = rr % wx, oy = (rr / wx) % wy, oz = rr / (wx * wy);
+                const int cx = hcx - 3 + ox, cy = hcy - 3 + oy, cz = hcz - 3 + oz;
+                sb[b] = rd.site_base +
+                        (((long long)wrapi(cz, rd.nz) * rd.ny + wrapi(cy, rd.ny)) * rd.nx + wrapi(cx, rd.nx)) * 2 + q;
+                nb[b][0] = 2 * cx + q - X; nb[b][1] = 2 * cy + q - Y; nb[b][2] = 2 * cz + q - Z;
+                ok[b] = c < W && ra.sid[c < W ? sb[b] : rd.site_base] >= 0;
+            }
+            T dxb[kRaBatch], dyb[kRaBatch], dzb[kRaBatch], fpb[kRaBatch];
+#pragma unroll
+            for (int b = 0; b < kRaBatch; ++b) {
+                const long long s = ok[b] ? sb[b] : rd.site_base;
+                dxb[b] = a.ux[s] - ujx; dyb[b] = a.uy[s] - ujy; dzb[b] = a.uz[s] - ujz;
+                fpb[b] = MODE == 1 ? a.fp[s] : (T)0;
+            }
+            int segb[kRaBatch];
+            T tb[kRaBatch], rinvb[kRaBatch];
+            bool inb[kRaBatch], fhb[kRaBatch];
+#pragma unroll
+            for (int b = 0; b < kRaBatch; ++b) {
+                const T dx = dxb[b], dy = dyb[b], dz = dzb[b];
+                const int nx_ = nb[b][0], ny_ = nb[b][1], nz_ = nb[b][2];
+                T qq = (dx + (T)(2 * nx_)) * dx + (dy + (T)(2 * ny_)) * dy + (dz + (T)(2 * nz_)) * dz;
+                T r2 = (T)(nx_ * nx_ + ny_ * ny_ + nz_ * nz_) + qq;
+                inb[b] = ok[b] && r2 < a.rc2;
+                direct_arg<T>(inb[b] ? r2 : a.rfloor2, a.S, a.rfloor2, segb[b], tb[b], rinvb[b], fhb[b]);
+                segb[b] = clamp_seg<T>(segb[b], a.nseg, tb[b]);
+            }
+#pragma unroll
+            for (int b = 0; b < kRaBatch; ++b) {
+                if (!inb[b]) continue;
+                const int seg = segb[b];
+                const T t = tb[b];
+                const bool fh = fhb[b];
                 if (fh) st |= kStRfloor;
                 if (MODE == 0) {
                     Vec4<T> cf = a.tab_f[seg];
@@ -689,11 +721,11 @@ __global__ void __launch_bounds__(256) k_ra_gather(const __grid_constant__ RaGat
                     Vec2<T> c1 = a.tab_d1[seg];
                     T dfr = (c0.x * t + c0.y) * t + c0.z;
                     T dph = (c0.w * t + c1.x) * t + c1.y;
-                    T coef = (fpj + a.fp[s]) * dfr + dph;
-                    T sc = fh ? (T)0 : coef * rinv;
-                    s0.add(sc * (dx + (T)nx_));
-                    s1.add(sc * (dy + (T)ny_));
-                    s2.add(sc * (dz + (T)nz_));
+                    T coef = (fpj + fpb[b]) * dfr + dph;
+                    T sc = fh ? (T)0 : coef * rinvb[b];
+                    s0.add(sc * (dxb[b] + (T)nb[b][0]));
+                    s1.add(sc * (dyb[b] + (T)nb[b][1]));
+                    s2.add(sc * (dzb[b] + (T)nb[b][2]));
                     if (ra.energy) {
                         Vec4<T> cp = a.tab_phi[seg];
                         ephi += 0.5 * (double)(((cp.x * t + cp.y) * t + cp.z) * t + cp.w);
@@ -702,12 +734,13 @@ __global__ void __launch_bounds__(256) k_ra_gather(const __grid_constant__ RaGat
             }
         }
         // the other run-aways: those of the home tile's index entry (every
-        // run-away within rc of this one is among them), else the whole
-        // list; either way lane l takes the list indices k = l mod 32 in
-        // ascending order, so the sums do not depend on the index
+        // run-away within rc of this one is among them) when the list is
+        // longer than kRaScanMax, else the whole list; either way lane l
+        // takes the list indices k = l mod 32 in ascending order, so the
+        // sums do not depend on the index
         const int tix = hcx / ra.tx, tiy = hcy / ra.ty, tiz = hcz / ra.tz;
         const int tl = rd.tile_base + (tiz * rd.nty + tiy) * rd.ntx + tix;
-        const bool indexed = a.tile_flag[tl] == 1;
+        const bool indexed = n > kRaScanMax && a.tile_flag[tl] == 1;
         const int nk = indexed ? a.ra_tcnt[tl] : (n + 31 - lane) / 32;
         const int *klist = indexed ? a.ra_tlist + a.ra_toff[tl] : nullptr;
         for (int kq = 0; kq < nk; ++kq) {

@@ -97,6 +97,7 @@ def lib():
         L.misa_set_state_staged.argtypes = [C.c_void_p]
         L.misa_insert_pka.argtypes = [C.c_void_p, C.c_int64, C.c_double, _D]
         L.misa_step.argtypes = [C.c_void_p, C.c_int]
+        L.misa_step_energies.argtypes = [C.c_void_p, C.c_int]
         L.misa_get_energies.argtypes = [C.c_void_p, _D, _D, C.c_void_p]
         for name in ("misa_get_positions", "misa_get_velocities", "misa_get_forces", "misa_get_density"):
             getattr(L, name).argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
@@ -287,8 +288,11 @@ class Sim:
         d = (C.c_double * 3)(*[float(t) for t in direction])
         self._check(lib().misa_insert_pka(self.h, int(atom), float(energy), d))
 
-    def step(self, n=1):
-        self._check(lib().misa_step(self.h, int(n)))
+    def step(self, n=1, energies=False):
+        """n MD steps; with energies the last one also evaluates the per-atom
+        energies, which energies() then reads without another evaluation."""
+        fn = lib().misa_step_energies if energies else lib().misa_step
+        self._check(fn(self.h, int(n)))
 
     # -- read-out -----------------------------------------------------------
     def energies(self, per_atom=False, out=None):

@@ -488,3 +488,78 @@ def test_runaway_index_with_many_interstitials(misa, pot, oracle, opot, prec, di
         else:
             for a_, b_ in zip(ref, (f, rho, e)):
                 np.testing.assert_array_equal(a_, b_)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_energy_step_equals_separate_evaluation(misa, pot, prec):
+    # energies evaluated inside the last step's passes (misa_step_energies)
+    # are bitwise those of a separate evaluation after plain steps, for the
+    # direct and the graph-replayed step; a later plain step invalidates them
+    n = 8
+    x0 = synth.cascade_snapshot(n, n, n, 0.1, 6, 2, 11)
+    v0 = synth.maxwell_velocities(len(x0), 600.0, M, 4)
+    out = []
+    for energies, graphs in ((False, True), (True, True), (True, False)):
+        with misa.Sim(pot, n, precision=prec, dx_max=0.02, reassign_period=3) as s:
+            s.set_graphs(graphs)
+            s.set_state(x0, v0)
+            s.insert_pka(-1, 300.0, synth.random_direction(9))
+            s.step(7, energies=energies)
+            l0 = s.stats()["launches"]
+            pe, ke, e = s.energies(per_atom=True)
+            evaluated = s.stats()["launches"] - l0
+            out.append((s.positions(), s.velocities(), pe, ke, e, evaluated))
+            s.step(2, energies=energies)
+            s.step(1)
+            pe2, _, e2 = s.energies(per_atom=True)
+            out[-1] = out[-1] + (pe2, e2)
+    ref = out[0]
+    for got in out[1:]:
+        for k in (0, 1, 4, 7):
+            np.testing.assert_array_equal(got[k], ref[k])
+        assert got[2] == ref[2] and got[3] == ref[3] and got[6] == ref[6]
+    # the energy step saved the evaluation's launches
+    assert out[1][5] < ref[5] and out[2][5] < ref[5]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("nint", [12, 300])
+def test_runaway_index_follows_state_changes(misa, pot, prec, nint, tmp_path):
+    # A force evaluation outside a step reuses the per-tile run-away index
+    # while the run-away list is unchanged; set_state, steps and a checkpoint
+    # load must rebuild it.  Each result is compared bitwise with a fresh
+    # handle's.  12 run-aways: the walkers scan the whole list; 300: they
+    # use the index.
+    n = 10
+    xa = synth.interstitial_snapshot(n, n, n, 0.05, nint, 31)
+    xb = synth.interstitial_snapshot(n, n, n, 0.05, nint + 7, 32)
+    vb = synth.maxwell_velocities(len(xb), 600.0, M, 5)
+
+    def fields(s):
+        _, _, e = s.energies(per_atom=True)
+        return s.forces(), s.density(), e
+
+    with misa.Sim(pot, n, precision=prec, dx_max=0.02, reassign_period=2) as s:
+        s.set_state(xa)
+        first = fields(s)
+        np.testing.assert_array_equal(fields(s)[0], first[0])  # evaluation with the cached index
+        s.set_state(xb, vb)
+        got_b = fields(s)
+        s.step(5)
+        got_c = fields(s)
+        ck = str(tmp_path / "state.ckpt")
+        s.save(ck)
+        st = s.stats()
+    assert st["n_runaway"] >= nint and st["status"] & 0x3 == 0
+    with misa.Sim(pot, n, precision=prec, dx_max=0.02, reassign_period=2) as t:
+        t.set_state(xb, vb)
+        ref_b = fields(t)
+    for a_, b_ in zip(got_b, ref_b):
+        np.testing.assert_array_equal(a_, b_)
+    with misa.Sim(pot, n, precision=prec, dx_max=0.02, reassign_period=2) as t:
+        t.set_state(xa)
+        fields(t)
+        t.load(ck)
+        ref_c = fields(t)
+    for a_, b_ in zip(got_c, ref_c):
+        np.testing.assert_array_equal(a_, b_)
