@@ -31,6 +31,45 @@ namespace misa {
 // the bcc lattice vectors for runtime-indexed device loops
 static __constant__ LVecTable c_lvec = kLVec;
 
+// The upper half of every shell of kLVec: within a shell the vectors are
+// sorted by (z, y, x), an order that negation reverses, so the second half
+// holds exactly the vectors whose (z, y, x) is lexicographically positive.
+// Walking it from every array site meets each unordered pair of array sites
+// once.  Its prefix of n / 2 vectors covers the shells of kLVec's prefix of n.
+constexpr LVecTable make_lvec_half()
+{
+    LVecTable t{};
+    int c = 0;
+    t.nshell = kLVec.nshell;
+    for (int sh = 0; sh < kLVec.nshell; ++sh) {
+        const int b = kLVec.shell_begin[sh], e = kLVec.shell_begin[sh + 1];
+        t.shell_n2[sh] = kLVec.shell_n2[sh];
+        t.shell_begin[sh] = c;
+        for (int k = b + (e - b) / 2; k < e; ++k) t.v[c++] = kLVec.v[k];
+    }
+    t.shell_begin[t.nshell] = c;
+    return t;
+}
+
+constexpr bool lvec_half_ok()
+{
+    for (int sh = 0; sh < kLVec.nshell; ++sh) {
+        if ((kLVec.shell_begin[sh + 1] - kLVec.shell_begin[sh]) % 2) return false;
+        for (int k = kLVec.shell_begin[sh]; k < kLVec.shell_begin[sh + 1]; ++k) {
+            const LVec &o = kLVec.v[k];
+            const bool pos = o.z > 0 || (o.z == 0 && (o.y > 0 || (o.y == 0 && o.x > 0)));
+            const bool upper = k >= kLVec.shell_begin[sh] + (kLVec.shell_begin[sh + 1] - kLVec.shell_begin[sh]) / 2;
+            if (pos != upper) return false;
+        }
+    }
+    return true;
+}
+
+constexpr LVecTable kLVecHalf = make_lvec_half();
+static_assert(lvec_half_ok() && kLVecHalf.shell_begin[kLVecHalf.nshell] == kNVec / 2,
+              "each shell splits into a negative and a positive half");
+static __constant__ LVecTable c_lvec_half = kLVecHalf;
+
 // |n| S = xint + xfrac for every |n|^2 <= kMaxN2 (S: knot index per lattice
 // unit), split on the host in FP64 so that the FP32 pair geometry needs no
 // FP64 arithmetic
@@ -64,6 +103,7 @@ struct AdjArgs {
     T *lam_x, *lam_y, *lam_z;        // per site (pooled)
     T *ra_lx, *ra_ly, *ra_lz;        // per run-away slot
     T *dl, *ra_dl;                   // D_lambda rho per site / run-away slot
+    T *cw;  // per site: ce F'_i - F''_i D_lambda rho_i, the weight of the knot values in the f scatter
     int nvec;                        // offsets within rc + 2 skin (prefix of kLVec)
     const int *tile_flag;            // null: every site scans the run-away list
     int tx, ty, tz;
@@ -146,22 +186,20 @@ __device__ __forceinline__ bool adj_pair(const A &a, int nx, int ny, int nz, T d
     return true;
 }
 
-// Visits every neighbour j of array atom i (pooled site s, replica-local
-// site ls) inside rc: array atoms through the offset vectors, then the
-// replica's run-away list (only from tiles flagged as within reach of a
-// run-away when a.tile_flag is set; rd's tile counts are those tiles').
-template <typename T, typename A, typename Fn>
-__device__ __forceinline__ void visit_site(const A &a, const RepDesc &rd, int nra, long long ls, Fn &fn)
+// Visits the array-site neighbours j of array atom i (replica-local site
+// ls, displacement ui, half-lattice x index x2 and cell row cy, cz) inside
+// rc through the offset vectors: all of them, or with HALF only those along
+// the positive half of each shell (every unordered pair of array sites once
+// over all i).
+template <typename T, bool HALF, typename A, typename Fn>
+__device__ __forceinline__ void visit_site_array(const A &a, const RepDesc &rd, T uix, T uiy, T uiz, int x2, int cy,
+                                                 int cz, Fn &fn)
 {
-    const long long s = rd.site_base + ls;
-    const T uix = a.ux[s], uiy = a.uy[s], uiz = a.uz[s];
-    const int x2 = (int)(ls % (2 * rd.nx));
-    const long long q = ls / (2 * rd.nx);
-    const int cy = (int)(q % rd.ny), cz = (int)(q / rd.ny);
     const int p = x2 & 1;
+    const int nv = HALF ? a.nvec / 2 : a.nvec;
 #pragma unroll 4
-    for (int k = 0; k < a.nvec; ++k) {
-        const LVec o = c_lvec.v[k];
+    for (int k = 0; k < nv; ++k) {
+        const LVec o = HALF ? c_lvec_half.v[k] : c_lvec.v[k];
         const int tx = wrapi(x2 + o.x, 2 * rd.nx);
         const int ty = wrapi(cy + cell_shift(p, o.y), rd.ny);
         const int tz = wrapi(cz + cell_shift(p, o.z), rd.nz);
@@ -170,9 +208,17 @@ __device__ __forceinline__ void visit_site(const A &a, const RepDesc &rd, int nr
         AdjPair<T> P;
         if (adj_pair<T>(a, o.x, o.y, o.z, a.ux[t] - uix, a.uy[t] - uiy, a.uz[t] - uiz, false, t, P)) fn(P);
     }
+}
+
+// Visits the run-aways j within rc of array atom i: those of the site's
+// tile index entry (list order) when the list is longer than kRaScanMax,
+// else the whole list (only from tiles flagged as within reach of a
+// run-away when a.tile_flag is set; rd's tile counts are those tiles').
+template <typename T, typename A, typename Fn>
+__device__ __forceinline__ void visit_site_ra(const A &a, const RepDesc &rd, int nra, long long ls, T uix, T uiy,
+                                              T uiz, int x2, int cy, int cz, Fn &fn)
+{
     if (nra == 0) return;
-    // the run-aways of the site's tile index entry (list order) when the
-    // list is longer than kRaScanMax, else the whole list
     const int *jl = nullptr;
     int nj = nra;
     if (a.tile_flag) {
@@ -202,6 +248,31 @@ __device__ __forceinline__ void visit_site(const A &a, const RepDesc &rd, int nr
         AdjPair<T> P;
         if (adj_pair<T>(a, nx_, ny_, nz_, a.ra_ux[g] - uix, a.ra_uy[g] - uiy, a.ra_uz[g] - uiz, true, g, P)) fn(P);
     }
+}
+
+// where array site ls sits: its displacement and lattice row
+template <typename T, typename A>
+__device__ __forceinline__ void site_here(const A &a, const RepDesc &rd, long long ls, T &uix, T &uiy, T &uiz,
+                                          int &x2, int &cy, int &cz)
+{
+    const long long s = rd.site_base + ls;
+    uix = a.ux[s]; uiy = a.uy[s]; uiz = a.uz[s];
+    x2 = (int)(ls % (2 * rd.nx));
+    const long long q = ls / (2 * rd.nx);
+    cy = (int)(q % rd.ny);
+    cz = (int)(q / rd.ny);
+}
+
+// Visits every neighbour j of array atom i (replica-local site ls) inside
+// rc: array atoms through the offset vectors, then the run-aways.
+template <typename T, typename A, typename Fn>
+__device__ __forceinline__ void visit_site(const A &a, const RepDesc &rd, int nra, long long ls, Fn &fn)
+{
+    T uix, uiy, uiz;
+    int x2, cy, cz;
+    site_here<T>(a, rd, ls, uix, uiy, uiz, x2, cy, cz);
+    visit_site_array<T, false>(a, rd, uix, uiy, uiz, x2, cy, cz, fn);
+    visit_site_ra<T>(a, rd, nra, ls, uix, uiy, uiz, x2, cy, cz, fn);
 }
 
 // One warp per run-away: j runs over the warps of the grid (warp-uniform).
@@ -414,17 +485,30 @@ struct DlFn {
 };
 
 template <typename T>
+__device__ __forceinline__ T energy_weight(const AdjArgs<T> &a, int r, const RepDesc &rd)
+{
+    const double Nr = (double)rd.ns;
+    return (T)(2.0 * (a.Etot[r] - a.Eref[r]) / (Nr * Nr));
+}
+
+template <typename T>
+__device__ __forceinline__ T embed_dd(const AdjArgs<T> &a, T rho);
+
+template <typename T>
 __global__ void k_adj_dl(AdjArgs<T> a)
 {
     const int r = blockIdx.y;
     const RepDesc rd = a.reps[r];
     const int nra = a.sc[r].n_ra;
+    const T ce = energy_weight<T>(a, r, rd);
     MISA_SITE_LOOP(rd, ls) {
         const long long s = rd.site_base + ls;
         if (a.sid[s] < 0) continue;
         DlFn<T> fn{a, a.lam_x[s], a.lam_y[s], a.lam_z[s], Acc<T>()};
         visit_site<T>(a, rd, nra, ls, fn);
-        a.dl[s] = fn.acc.value();
+        const T dl = fn.acc.value();
+        a.dl[s] = dl;
+        a.cw[s] = ce * a.fp[s] - embed_dd<T>(a, a.rho[s]) * dl;
     }
     MISA_RA_WARP_LOOP(nra, j) {
         const int g = rd.ra_base + j;
@@ -469,6 +553,40 @@ struct GradFn {
         atomicAdd(&Yp[sg + 1], hce * c2 - hD * d2);
         atomicAdd(&Mp[sg], hce * c1 - hD * d1);
         atomicAdd(&Mp[sg + 1], hce * c3 - hD * d3);
+    }
+};
+
+// The same scatter for an unordered pair of array sites, visited once (the
+// half walk): both directions share r, its segment and t, and D (e and
+// lambda_j - lambda_i both change sign), so their terms add up to one
+// scatter with the weights summed: cw_i + cw_j and (F'_i + F'_j) D for f,
+// ce and D for phi.
+template <typename T>
+struct GradPairFn {
+    const AdjArgs<T> &a;
+    T *bins;
+    T lix, liy, liz;
+    T cwi, Fpi, ce;
+    __device__ __forceinline__ void operator()(const AdjPair<T> &P)
+    {
+        const T ljx = a.lam_x[P.j], ljy = a.lam_y[P.j], ljz = a.lam_z[P.j];
+        const T cw = cwi + a.cw[P.j];
+        const T D = P.ex * (ljx - lix) + P.ey * (ljy - liy) + P.ez * (ljz - liz);
+        const T fD = (Fpi + a.fp[P.j]) * D;
+        const T t = P.t, t2 = t * t, t3 = t2 * t, ih = a.inv_hr;
+        const T c0 = 2 * t3 - 3 * t2 + 1, c1 = t3 - 2 * t2 + t, c2 = -2 * t3 + 3 * t2, c3 = t3 - t2;
+        const T d0 = (6 * t2 - 6 * t) * ih, d1 = (3 * t2 - 4 * t + 1) * ih, d2 = (-6 * t2 + 6 * t) * ih,
+                d3 = (3 * t2 - 2 * t) * ih;
+        const int sg = P.seg;
+        T *Yf = bins, *Yp = bins + a.n, *Mf = bins + 3 * a.n, *Mp = bins + 4 * a.n;
+        atomicAdd(&Yf[sg], cw * c0 - fD * d0);
+        atomicAdd(&Yf[sg + 1], cw * c2 - fD * d2);
+        atomicAdd(&Mf[sg], cw * c1 - fD * d1);
+        atomicAdd(&Mf[sg + 1], cw * c3 - fD * d3);
+        atomicAdd(&Yp[sg], ce * c0 - D * d0);
+        atomicAdd(&Yp[sg + 1], ce * c2 - D * d2);
+        atomicAdd(&Mp[sg], ce * c1 - D * d1);
+        atomicAdd(&Mp[sg + 1], ce * c3 - D * d3);
     }
 };
 
@@ -528,17 +646,22 @@ __global__ void __launch_bounds__(kGradThreads<T>) k_adj_grad(AdjArgs<T> a, doub
     for (int k = threadIdx.x; k < copies * nb; k += blockDim.x) reinterpret_cast<T *>(bin_smem)[k] = (T)0;
     T *bins = reinterpret_cast<T *>(bin_smem) + (copies == 2 && (threadIdx.x & 16) ? nb : 0);
     __syncthreads();
-    const double Nr = (double)rd.ns;
-    const T ce = (T)(2.0 * (a.Etot[r] - a.Eref[r]) / (Nr * Nr));
+    const T ce = energy_weight<T>(a, r, rd);
     MISA_SITE_LOOP(rd, ls) {
         const long long s = rd.site_base + ls;
         if (a.sid[s] < 0) continue;
-        const T rho = a.rho[s];
-        const T Fpi = a.fp[s];
-        GradFn<T> fn{a, bins, a.lam_x[s], a.lam_y[s], a.lam_z[s], ce * Fpi - embed_dd<T>(a, rho) * a.dl[s], Fpi,
-                     (T)0.5 * ce};
-        visit_site<T>(a, rd, nra, ls, fn);
-        embed_bins<T>(a, bins, rho, ce, a.dl[s]);
+        const T Fpi = a.fp[s], cwi = a.cw[s];
+        T uix, uiy, uiz;
+        int x2, cy, cz;
+        site_here<T>(a, rd, ls, uix, uiy, uiz, x2, cy, cz);
+        // array-site pairs once (half walk, both directions' terms), the
+        // site's run-away pairs from this side (the run-away's walk below
+        // adds the other direction)
+        GradPairFn<T> fp2{a, bins, a.lam_x[s], a.lam_y[s], a.lam_z[s], cwi, Fpi, ce};
+        visit_site_array<T, true>(a, rd, uix, uiy, uiz, x2, cy, cz, fp2);
+        GradFn<T> fn{a, bins, a.lam_x[s], a.lam_y[s], a.lam_z[s], cwi, Fpi, (T)0.5 * ce};
+        visit_site_ra<T>(a, rd, nra, ls, uix, uiy, uiz, x2, cy, cz, fn);
+        embed_bins<T>(a, bins, a.rho[s], ce, a.dl[s]);
     }
     MISA_RA_WARP_LOOP(nra, j) {
         const int g = rd.ra_base + j;

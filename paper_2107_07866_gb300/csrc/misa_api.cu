@@ -204,7 +204,7 @@ struct misa_sim {
     size_t ev_used = 0;
     // adjoint work arrays (allocated on first use)
     void *lam[3] = {}, *ra_lam[3] = {};
-    void *dl = nullptr, *ra_dl = nullptr;
+    void *dl = nullptr, *ra_dl = nullptr, *cw = nullptr;
     double *adj_partial = nullptr, *adj_sum = nullptr, *adj_grad = nullptr, *adj_eref = nullptr, *adj_fref = nullptr;
     int adj_cta = 0;
     // alloys (misa_set_species): species per atom id, coefficient tables
@@ -1330,6 +1330,7 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
             if (!s->lam[d] || !s->ra_lam[d]) return fail(s, MISA_EOOM, "adjoint work arrays");
         }
         s->dl = dalloc(s, sizeof(T) * s->ns);
+        s->cw = dalloc(s, sizeof(T) * s->ns);
         s->ra_dl = dalloc(s, sizeof(T) * capt);
         // FP32: one 1024-thread CTA per SM (two bin copies); FP64: two 256-thread CTAs
         int gx = ((sizeof(T) == 4 ? s->nsm : s->nsm * 2) + s->nrep - 1) / s->nrep;
@@ -1339,7 +1340,8 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
         s->adj_grad = (double *)dalloc(s, sizeof(double) * 3 * n);
         s->adj_eref = (double *)dalloc(s, sizeof(double) * s->nrep * 2);
         s->adj_fref = (double *)dalloc(s, sizeof(double) * 3 * s->ns);
-        if (!s->dl || !s->ra_dl || !s->adj_partial || !s->adj_sum || !s->adj_grad || !s->adj_eref || !s->adj_fref)
+        if (!s->dl || !s->cw || !s->ra_dl || !s->adj_partial || !s->adj_sum || !s->adj_grad || !s->adj_eref ||
+            !s->adj_fref)
             return fail(s, MISA_EOOM, "adjoint work arrays");
         CK(cudaFuncSetAttribute(k_adj_grad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bin_bytes * copies)));
     }
@@ -1387,7 +1389,7 @@ int loss_grad_impl(misa_sim *s, const double *Fref, const double *Eref, double *
     a.Etot = s->red_out;
     a.lam_x = (T *)s->lam[0]; a.lam_y = (T *)s->lam[1]; a.lam_z = (T *)s->lam[2];
     a.ra_lx = (T *)s->ra_lam[0]; a.ra_ly = (T *)s->ra_lam[1]; a.ra_lz = (T *)s->ra_lam[2];
-    a.dl = (T *)s->dl; a.ra_dl = (T *)s->ra_dl;
+    a.dl = (T *)s->dl; a.ra_dl = (T *)s->ra_dl; a.cw = (T *)s->cw;
     const double roff = (s->p.rc + 2.0 * s->p.skin) / half;
     int nsh = 0;
     while (nsh < kLVec.nshell && kLVec.shell_n2[nsh] <= roff * roff) ++nsh;

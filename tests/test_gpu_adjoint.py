@@ -155,6 +155,40 @@ def test_gradient_matches_central_differences(misa, pot, case):
         s.set_tables(*tabs)
 
 
+def test_fp32_gradient_matches_central_differences(misa, pot, case):
+    # the FP32 gradient against central differences (h = 1e-6) on 32 seeded
+    # coefficients.  The differences are taken of the FP64 handle's loss: a
+    # 1e-6 knot step moves the loss by less than the FP32 loss's own
+    # rounding.  Bound: FP32_TOL of the largest gradient entry (the FP32
+    # error budget above).
+    n, snaps, target = case
+    F32, E32 = gpu_targets(misa, target, n, snaps, "fp32")
+    _, g32 = gpu_loss_grad(misa, pot, n, snaps, F32, E32, "fp32")
+    Fref, Eref = gpu_targets(misa, target, n, snaps, "fp64")
+    scale = np.abs(g32).max()
+    with misa.Sim(pot, replicas=[(n, n, n)] * len(snaps), precision="fp64") as s:
+        s.set_state(np.concatenate(snaps))
+        rng = np.random.default_rng(13)
+        hot = np.flatnonzero(np.abs(g32) > 1e-3 * scale)
+        idx = rng.choice(hot, 32, replace=False)
+        tabs = [pot.f.copy(), pot.phi.copy(), pot.F.copy()]
+        worst = 0.0
+        for k in idx:
+            t, j = divmod(int(k), pot.n)
+            h = 1e-6 * max(1.0, abs(tabs[t][j]))
+            y0 = tabs[t][j]
+            tabs[t][j] = y0 + h
+            s.set_tables(*tabs)
+            lp, _ = s.loss_grad(Fref, Eref, grad=np.empty(3 * pot.n))
+            tabs[t][j] = y0 - h
+            s.set_tables(*tabs)
+            lm, _ = s.loss_grad(Fref, Eref, grad=np.empty(3 * pot.n))
+            tabs[t][j] = y0
+            worst = max(worst, abs(g32[k] - (lp - lm) / (2 * h)) / scale)
+        s.set_tables(*tabs)
+    assert worst < FP32_TOL, worst
+
+
 def test_autograd_function(misa, pot, case):
     import torch
     from paper_2107_07866_gb300.autograd import eam_loss
