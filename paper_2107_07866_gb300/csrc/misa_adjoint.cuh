@@ -494,8 +494,10 @@ __device__ __forceinline__ T energy_weight(const AdjArgs<T> &a, int r, const Rep
 template <typename T>
 __device__ __forceinline__ T embed_dd(const AdjArgs<T> &a, T rho);
 
+// three 256-thread CTAs per SM for FP32 (79 registers, no spills): the walk
+// is bound by load latency and gains from the extra warps
 template <typename T>
-__global__ void k_adj_dl(AdjArgs<T> a)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_adj_dl(AdjArgs<T> a)
 {
     const int r = blockIdx.y;
     const RepDesc rd = a.reps[r];

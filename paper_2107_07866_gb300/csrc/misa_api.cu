@@ -227,6 +227,10 @@ struct misa_sim {
     // being captured into a graph always rebuilds it
     bool ra_index_valid = false;
     bool capturing = false;
+    // kick/drift block map (replica, first site) and its host copy
+    int2 *kd_map = nullptr;
+    int kd_blocks = 0;
+    std::vector<int2> kd_host;
 };
 
 namespace {
@@ -305,6 +309,7 @@ MdArgs<T> md_args(misa_sim *s)
     MdArgs<T> m{};
     m.reps = s->reps_d;
     m.nrep = s->nrep;
+    m.kd_map = s->kd_map;
     m.sid = s->sid;
     m.ux = s->u[0]; m.uy = s->u[1]; m.uz = s->u[2];
     m.sx = (T *)s->s[0]; m.sy = (T *)s->s[1]; m.sz = (T *)s->s[2];
@@ -748,7 +753,7 @@ int launch_step(misa_sim *s, bool energy = false)
     mark(s);
     k_begin_step<T><<<rep_blocks(s), 128, 0, s->st>>>(m);
     k_ra_kick_drift<T><<<list_grid(s), 256, 0, s->st>>>(m);
-    k_kick_drift<T><<<site_grid(s), 256, 0, s->st>>>(m);
+    k_kick_drift<T><<<s->kd_blocks, 256, 0, s->st>>>(m);
     mark(s);
     k_reassign_claim<T><<<list_grid(s), 256, 0, s->st>>>(m, 0);
     k_reassign_promote<T><<<list_grid(s), 256, 0, s->st>>>(m, 0);
@@ -904,6 +909,16 @@ int create_impl(misa_sim *s)
     size_t Tb = sizeof(T);
     s->reps_d = (RepDesc *)dalloc(s, sizeof(RepDesc) * s->nrep);
     s->sc = (DevScalars *)dalloc(s, sizeof(DevScalars) * s->nrep);
+    // kick/drift: one block per kKdChunk sites of each replica, so that the
+    // sweep's blocks carry equal work whatever the replicas' sizes
+    s->kd_host.clear();
+    for (int r = 0; r < s->nrep; ++r)
+        for (long long b = 0; b < s->reps[r].ns; b += kKdChunk) s->kd_host.push_back(make_int2(r, (int)b));
+    s->kd_blocks = (int)s->kd_host.size();
+    s->kd_map = (int2 *)dalloc(s, sizeof(int2) * s->kd_host.size());
+    if (!s->kd_map) return fail(s, MISA_EOOM, "device allocation failed (kick/drift map)");
+    CK(cudaMemcpyAsync(s->kd_map, s->kd_host.data(), sizeof(int2) * s->kd_host.size(), cudaMemcpyHostToDevice,
+                       s->st));
     s->tile_rep = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap);
     s->tile_flag = (int *)dalloc(s, sizeof(int) * (size_t)s->ntile_cap);
     s->reps_fd = (RepDesc *)dalloc(s, sizeof(RepDesc) * s->nrep);

@@ -53,7 +53,12 @@ struct MdArgs {
     int reassign_period;
     double acc_conv;  // eV/A -> A/fs^2
     double mass;
+    // kick/drift blocks: block b sweeps sites [y, y + kKdChunk) of replica x
+    // (block counts proportional to the replicas' sizes)
+    const int2 *kd_map;
 };
+
+constexpr int kKdChunk = 4096;  // sites per kick/drift block (16 per thread)
 
 // local site id <-> lattice coordinates (lattice units: (2cx + p, 2cy + p, 2cz + p))
 __device__ __forceinline__ void site_lat(long long s, int nx, int ny, int &X, int &Y, int &Z)
@@ -208,13 +213,15 @@ __device__ __forceinline__ double f2d(double x) { return x; }
 template <typename T>
 __global__ void __launch_bounds__(256, 4) k_kick_drift(MdArgs<T> m)
 {
-    const int r = blockIdx.y;
+    const int2 bm = m.kd_map[blockIdx.x];
+    const int r = bm.x;
     const RepDesc rd = m.reps[r];
     DevScalars *sc = m.sc + r;
     const double dt = sc->dt, hdt = 0.5 * dt, dtl = dt * m.inv_half;
     const int base = sc->n_ra_old;
     const float skin2f = (float)m.skin2;
-    MISA_SITE_LOOP(rd, ls) {
+    const long long lend = min(rd.ns, (long long)bm.y + kKdChunk);
+    for (long long ls = bm.y + threadIdx.x; ls < lend; ls += blockDim.x) {
         const long long s = rd.site_base + ls;
         int id = m.sid[s];
         if (id < 0) continue;

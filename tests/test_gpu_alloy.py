@@ -178,3 +178,24 @@ def test_alloy_parity_at_benchmark_size(misa, oracle):
     assert nerr(f, f_o) < TOL["fp32"], nerr(f, f_o)
     assert nerr(rho, rho_o) < TOL["fp32"], nerr(rho, rho_o)
     assert nerr(e, e_o) < TOL["fp32"], nerr(e, e_o)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_alloy_energy_step_equals_separate_evaluation(misa, prec):
+    # the alloy passes of the energy step (misa_step_energies) write the
+    # same per-atom energies as a separate evaluation after plain steps
+    nsp, dims, mk, frac = CASES["cascade_3sp_10x9x12"]
+    al = synth.alloy_potential(nsp)
+    x = mk()
+    t = synth.random_types(len(x), frac, 33)
+    v = synth.maxwell_velocities(len(x), 600.0, synth.MASS_FE, 6)
+    out = []
+    for energies in (False, True):
+        with misa.Sim(al.species(0), *dims, precision=prec, dx_max=0.02, reassign_period=3) as s:
+            s.set_species(al, t)
+            s.set_state(x, v)
+            s.step(6, energies=energies)
+            pe, ke, e = s.energies(per_atom=True)
+            out.append((s.positions(), pe, ke, e))
+    for a_, b_ in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a_, b_)
