@@ -203,7 +203,8 @@ __device__ __forceinline__ void visit_site_array(const A &a, const RepDesc &rd, 
         const int tx = wrapi(x2 + o.x, 2 * rd.nx);
         const int ty = wrapi(cy + cell_shift(p, o.y), rd.ny);
         const int tz = wrapi(cz + cell_shift(p, o.z), rd.nz);
-        const long long t = rd.site_base + (((long long)tz * rd.ny + ty) * rd.nx) * 2 + tx;
+        // 32-bit index arithmetic: a handle holds fewer than 2^31 sites
+        const int t = (int)rd.site_base + ((tz * rd.ny + ty) * rd.nx) * 2 + tx;
         if (a.sid[t] < 0) continue;
         AdjPair<T> P;
         if (adj_pair<T>(a, o.x, o.y, o.z, a.ux[t] - uix, a.uy[t] - uiy, a.uz[t] - uiz, false, t, P)) fn(P);
@@ -299,7 +300,7 @@ __device__ __forceinline__ void visit_ra(const A &a, const RepDesc &rd, int nra,
         const int qq = c & 1, rr = c >> 1;
         const int ox = rr % wx, oy = (rr / wx) % wy, oz = rr / (wx * wy);
         const int cx = hcx - 3 + ox, cy = hcy - 3 + oy, cz = hcz - 3 + oz;
-        const long long t = rd.site_base + (((long long)wrapi(cz, rd.nz) * rd.ny + wrapi(cy, rd.ny)) * rd.nx + wrapi(cx, rd.nx)) * 2 + qq;
+        const int t = (int)rd.site_base + ((wrapi(cz, rd.nz) * rd.ny + wrapi(cy, rd.ny)) * rd.nx + wrapi(cx, rd.nx)) * 2 + qq;
         if (a.sid[t] < 0) continue;
         AdjPair<T> P;
         if (adj_pair<T>(a, 2 * cx + qq - X, 2 * cy + qq - Y, 2 * cz + qq - Z, a.ux[t] - ujx, a.uy[t] - ujy,
