@@ -258,10 +258,11 @@ __device__ __forceinline__ void site_here(const A &a, const RepDesc &rd, long lo
 {
     const long long s = rd.site_base + ls;
     uix = a.ux[s]; uiy = a.uy[s]; uiz = a.uz[s];
-    x2 = (int)(ls % (2 * rd.nx));
-    const long long q = ls / (2 * rd.nx);
-    cy = (int)(q % rd.ny);
-    cz = (int)(q / rd.ny);
+    const int li = (int)ls;  // fewer than 2^31 sites: 32-bit division
+    x2 = li % (2 * rd.nx);
+    const int q = li / (2 * rd.nx);
+    cy = q % rd.ny;
+    cz = q / rd.ny;
 }
 
 // Visits every neighbour j of array atom i (replica-local site ls) inside

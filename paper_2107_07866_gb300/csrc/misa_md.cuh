@@ -61,11 +61,13 @@ struct MdArgs {
 constexpr int kKdChunk = 4096;  // sites per kick/drift block (16 per thread)
 
 // local site id <-> lattice coordinates (lattice units: (2cx + p, 2cy + p, 2cz + p))
+// (32-bit division: a replica holds fewer than 2^31 sites)
 __device__ __forceinline__ void site_lat(long long s, int nx, int ny, int &X, int &Y, int &Z)
 {
-    int x2 = (int)(s % (2 * nx));
-    long long r = s / (2 * nx);
-    int cy = (int)(r % ny), cz = (int)(r / ny);
+    const int si = (int)s;
+    int x2 = si % (2 * nx);
+    int r = si / (2 * nx);
+    int cy = r % ny, cz = r / ny;
     int p = x2 & 1;
     X = x2;
     Y = 2 * cy + p;
@@ -74,7 +76,13 @@ __device__ __forceinline__ void site_lat(long long s, int nx, int ny, int &X, in
 
 __device__ __forceinline__ int wrapi(int a, int n)
 {
-    int r = a % n;
+    // a neighbour walk stays within one period of [0, n) (offsets are
+    // shorter than the box): one add or subtract; other values take the
+    // remainder (an integer division, tens of instructions)
+    if (a >= 0 && a < n) return a;
+    if (a < 0 && a >= -n) return a + n;
+    if (a >= n && a < 2 * n) return a - n;
+    const int r = a % n;
     return r < 0 ? r + n : r;
 }
 
