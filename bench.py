@@ -56,13 +56,13 @@ BYTES_FORCE_SITE = 84
 # DRAM traffic of the force pass (k_force_p) per launch at the 54M-atom
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by the kernel sources it was measured on.
-NCU_FORCE_TRAFFIC = {"source_sha": "45f3aafa8bb3af05", "bytes_per_launch": 4.8484e9,
-                     "note": "k_force_p<8,8,12> at 300^3 cells: 2.955e9 B read + 1.893e9 B written per launch "
+NCU_FORCE_TRAFFIC = {"source_sha": "3e852c4383202e23", "bytes_per_launch": 4.8517e9,
+                     "note": "k_force_p<8,8,12> at 300^3 cells: 2.959e9 B read + 1.893e9 B written per launch "
                              "(mean of 3 launches), 89.8 B/site vs 84 algorithmic"}
 # Shared-memory (LSU) and texture wavefronts per site of the two gathers from
 # one ncu capture of the 2M-atom case (equilibrated crystal), same keying;
 # the L1 data pipe serves one wavefront per SM per clock.
-NCU_WAVEFRONTS = {"source_sha": "45f3aafa8bb3af05", "density": (27.4, 16.4), "force": (37.5, 23.6)}
+NCU_WAVEFRONTS = {"source_sha": "3e852c4383202e23", "density": (27.4, 16.4), "force": (37.5, 23.6)}
 
 
 def kernel_source_sha():
@@ -798,26 +798,28 @@ def run_gpu(args):
         spd = math.sqrt(2.0 * w["pka_eV"] / synth.MASS_FE / synth.EV_PER_AMU_A2_FS2)
         v0[pka] = spd * d
         v_host = torch.from_numpy(v0).pin_memory()
-        e_host = torch.empty(natoms, dtype=torch.float64).pin_memory()
+        e_host = [torch.empty(natoms, dtype=torch.float64).pin_memory() for _ in range(2)]
         inner = max(10, w["reassign"])
         iters = max(10, args.e2e_iters)
         s.stage_state(x_host, v_host)
         s.set_state_staged()
         s.step(inner)
         s.energies(per_atom=True)
+        s.energies_async(e_host[0])
+        s.wait_outputs()
         torch.cuda.synchronize()
         barrier(ws)
         t0 = time.perf_counter()
         s.stage_state(x_host, v_host)            # H2D of the first state
-        pe_sum = 0.0
         for it in range(iters):
             s.set_state_staged()
             if it + 1 < iters:
                 s.stage_state(x_host, v_host)    # H2D of the next state, beside this one's steps
             s.step(inner, energies=True)         # the last step also evaluates E_i
-            # D2H: per-atom energies E_i (and the totals) of the state reached
-            pe, _, _ = s.energies(per_atom=True, out=e_host.numpy())
-            pe_sum += pe
+            # D2H of the state's per-atom energies E_i, beside the next state's
+            # steps (two pinned buffers in turn)
+            s.energies_async(e_host[it % 2])
+        s.wait_outputs()
         torch.cuda.synchronize()
         el = barrier_max(ws, time.perf_counter() - t0)
         e2e = {"value": natoms * ws * inner * iters / el, "unit": UNIT,
@@ -825,7 +827,7 @@ def run_gpu(args):
                "iterations": iters,
                "note": f"one e2e step = state (x, v) from pinned host memory + {inner} MD steps + the per-atom "
                        "energies E_i of the state reached (evaluated inside the last step's passes) back to "
-                       "pinned host memory; "
+                       "pinned host memory (two buffers in turn, copied beside the next state's steps); "
                        "each state is staged on the library's copy stream while the previous one is simulated"}
         s.close()
         del s

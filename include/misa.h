@@ -217,6 +217,23 @@ int misa_get_energies(misa_sim *s, double *pe, double *ke, double *per_atom);
 /* Potential and kinetic energy of every replica (arrays of nrep). */
 int misa_replica_energies(misa_sim *s, double *pe, double *ke);
 
+/* E_i of every atom (Eq. eam_base) of the current state into per_atom
+ * (n >= natoms doubles, indexed by atom id, host or device memory) without
+ * waiting: the handle's stream writes them into a buffer of the handle (from
+ * the last misa_step_energies, else after one evaluation of the potential)
+ * and an output stream of the handle copies them to per_atom, so that the
+ * caller's next calls (a new state, more steps) run beside the copy.  From
+ * pinned host memory the copy is asynchronous; from pageable memory it may
+ * complete before the call returns.  per_atom must stay valid, and its
+ * contents are undefined, until misa_wait_outputs returns.  A later call
+ * waits on the device for the previous copy before it overwrites the
+ * buffer.  MISA_EOOM if the buffer (8 bytes per atom) cannot be allocated. */
+int misa_get_energies_async(misa_sim *s, double *per_atom, int64_t n);
+
+/* Waits for the copies started by misa_get_energies_async; status as for
+ * the synchronous calls.  Synchronises. */
+int misa_wait_outputs(misa_sim *s);
+
 /* Per-atom host outputs (3 natoms doubles, or natoms for the density),
  * indexed by atom id; n must be >= natoms.  Positions are wrapped into the
  * box.  Forces are those of the current positions (eV/A).  Synchronise. */

@@ -200,9 +200,9 @@ __device__ __forceinline__ void visit_site_array(const A &a, const RepDesc &rd, 
 #pragma unroll 4
     for (int k = 0; k < nv; ++k) {
         const LVec o = HALF ? c_lvec_half.v[k] : c_lvec.v[k];
-        const int tx = wrapi(x2 + o.x, 2 * rd.nx);
-        const int ty = wrapi(cy + cell_shift(p, o.y), rd.ny);
-        const int tz = wrapi(cz + cell_shift(p, o.z), rd.nz);
+        const int tx = wrap_near(x2 + o.x, 2 * rd.nx);
+        const int ty = wrap_near(cy + cell_shift(p, o.y), rd.ny);
+        const int tz = wrap_near(cz + cell_shift(p, o.z), rd.nz);
         // 32-bit index arithmetic: a handle holds fewer than 2^31 sites
         const int t = (int)rd.site_base + ((tz * rd.ny + ty) * rd.nx) * 2 + tx;
         if (a.sid[t] < 0) continue;
@@ -232,13 +232,13 @@ __device__ __forceinline__ void visit_site_ra(const A &a, const RepDesc &rd, int
         }
     }
     int X, Y, Z;
-    site_lat(ls, rd.nx, rd.ny, X, Y, Z);
+    site_lat32((int)ls, rd.nx, rd.ny, X, Y, Z);
     const int Lx = 2 * rd.nx, Ly = 2 * rd.ny, Lz = 2 * rd.nz;
     for (int jq = 0; jq < nj; ++jq) {
         const int j = jl ? jl[jq] : jq;
         const int g = rd.ra_base + j;
         int Xj, Yj, Zj;
-        site_lat(a.ra_home[g], rd.nx, rd.ny, Xj, Yj, Zj);
+        site_lat32(a.ra_home[g], rd.nx, rd.ny, Xj, Yj, Zj);
         int nx_ = Xj - X, ny_ = Yj - Y, nz_ = Zj - Z;
         nx_ -= (nx_ > rd.nx) ? Lx : 0;
         nx_ += (nx_ < -rd.nx) ? Lx : 0;
@@ -292,7 +292,7 @@ __device__ __forceinline__ void visit_ra(const A &a, const RepDesc &rd, int nra,
     const int lane = threadIdx.x & 31;
     const int g = rd.ra_base + jl;
     int X, Y, Z;
-    site_lat(a.ra_home[g], rd.nx, rd.ny, X, Y, Z);
+    site_lat32(a.ra_home[g], rd.nx, rd.ny, X, Y, Z);
     const int hp = X & 1;
     const int hcx = X >> 1, hcy = (Y - hp) >> 1, hcz = (Z - hp) >> 1;
     const T ujx = a.ra_ux[g], ujy = a.ra_uy[g], ujz = a.ra_uz[g];
@@ -301,7 +301,7 @@ __device__ __forceinline__ void visit_ra(const A &a, const RepDesc &rd, int nra,
         const int qq = c & 1, rr = c >> 1;
         const int ox = rr % wx, oy = (rr / wx) % wy, oz = rr / (wx * wy);
         const int cx = hcx - 3 + ox, cy = hcy - 3 + oy, cz = hcz - 3 + oz;
-        const int t = (int)rd.site_base + ((wrapi(cz, rd.nz) * rd.ny + wrapi(cy, rd.ny)) * rd.nx + wrapi(cx, rd.nx)) * 2 + qq;
+        const int t = (int)rd.site_base + ((wrap_near(cz, rd.nz) * rd.ny + wrap_near(cy, rd.ny)) * rd.nx + wrap_near(cx, rd.nx)) * 2 + qq;
         if (a.sid[t] < 0) continue;
         AdjPair<T> P;
         if (adj_pair<T>(a, 2 * cx + qq - X, 2 * cy + qq - Y, 2 * cz + qq - Z, a.ux[t] - ujx, a.uy[t] - ujy,
@@ -324,7 +324,7 @@ __device__ __forceinline__ void visit_ra(const A &a, const RepDesc &rd, int nra,
         if (k == jl) continue;
         const int gk = rd.ra_base + k;
         int Xk, Yk, Zk;
-        site_lat(a.ra_home[gk], rd.nx, rd.ny, Xk, Yk, Zk);
+        site_lat32(a.ra_home[gk], rd.nx, rd.ny, Xk, Yk, Zk);
         int nx_ = Xk - X, ny_ = Yk - Y, nz_ = Zk - Z;
         nx_ -= (nx_ > rd.nx) ? Lx : 0;
         nx_ += (nx_ < -rd.nx) ? Lx : 0;

@@ -191,6 +191,12 @@ struct misa_sim {
     cudaEvent_t ev_stg_free = nullptr;  // the last staged state has been read
     double *stg_x = nullptr, *stg_v = nullptr;
     bool stg_pending = false, stg_has_v = false;
+    // asynchronous per-atom energies (misa_get_energies_async): written into
+    // e_buf on the handle's stream, copied out on an output stream of their own
+    cudaStream_t ost = nullptr;
+    cudaEvent_t ev_e_ready = nullptr;  // e_buf holds the energies to copy
+    cudaEvent_t ev_e_done = nullptr;   // the last copy out of e_buf is complete
+    double *e_buf = nullptr;
     long long ntile_cap = 0;    // tile_flag / tile_rep capacity (smallest tile shape)
     int ntiles = 0;
     size_t smem_density = 0, smem_force = 0;
@@ -1119,6 +1125,38 @@ int scatter_out(misa_sim *s, int kind, double *out)
     return MISA_OK;
 }
 
+// E_i of the current positions into e_buf (handle's stream), then copied to
+// out on the output stream; nothing waits on the host
+template <typename T>
+int energies_async(misa_sim *s, double *out)
+{
+    if (!s->ost) {
+        CK(cudaStreamCreateWithFlags(&s->ost, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&s->ev_e_ready, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&s->ev_e_done, cudaEventDisableTiming));
+    }
+    if (!s->e_buf) {
+        s->e_buf = (double *)dalloc(s, sizeof(double) * (size_t)s->ns);
+        if (!s->e_buf) return fail(s, MISA_EOOM, "get_energies_async: output buffer");
+    }
+    if (!s->energy_valid) {
+        int rc = launch_forces<T>(s, 0, true);
+        if (rc) return rc;
+        s->energy_valid = true;
+    }
+    // the previous copy out of e_buf is complete before it is overwritten
+    CK(cudaStreamWaitEvent(s->st, s->ev_e_done, 0));
+    MdArgs<T> m = md_args<T>(s);
+    k_scatter<T><<<site_grid(s), 256, 0, s->st>>>(m, 4, s->e_buf);
+    CK(cudaGetLastError());
+    s->launches += 1;
+    CK(cudaEventRecord(s->ev_e_ready, s->st));
+    CK(cudaStreamWaitEvent(s->ost, s->ev_e_ready, 0));
+    CK(cudaMemcpyAsync(out, s->e_buf, sizeof(double) * (size_t)s->ns, cudaMemcpyDefault, s->ost));
+    CK(cudaEventRecord(s->ev_e_done, s->ost));
+    return MISA_OK;
+}
+
 int check_status(misa_sim *s)
 {
     unsigned st = 0;
@@ -1525,6 +1563,10 @@ void misa_destroy(misa_sim *s)
     if (s->ev_stg) cudaEventDestroy(s->ev_stg);
     if (s->ev_stg_free) cudaEventDestroy(s->ev_stg_free);
     if (s->cst) cudaStreamDestroy(s->cst);
+    if (s->ost) cudaStreamSynchronize(s->ost);
+    if (s->ev_e_ready) cudaEventDestroy(s->ev_e_ready);
+    if (s->ev_e_done) cudaEventDestroy(s->ev_e_done);
+    if (s->ost) cudaStreamDestroy(s->ost);
     for (auto &a : s->allocs) {
         if (s->p.free) s->p.free(a.first, a.second, s->p.alloc_ctx);
         else cudaFree(a.first);
@@ -1752,6 +1794,20 @@ int misa_set_graphs(misa_sim *s, int enable)
     if (!s) return MISA_EINVAL;
     s->use_graph = enable != 0;
     return MISA_OK;
+}
+
+int misa_get_energies_async(misa_sim *s, double *per_atom, int64_t n)
+{
+    if (!s) return MISA_EINVAL;
+    if (!per_atom || n < s->ns) return fail(s, MISA_EINVAL, "get_energies_async: per_atom of natoms required");
+    return s->prec == MISA_FP64 ? energies_async<double>(s, per_atom) : energies_async<float>(s, per_atom);
+}
+
+int misa_wait_outputs(misa_sim *s)
+{
+    if (!s) return MISA_EINVAL;
+    if (s->ost) CK(cudaStreamSynchronize(s->ost));
+    return check_status(s);
 }
 
 int misa_get_energies(misa_sim *s, double *pe, double *ke, double *per_atom)

@@ -61,29 +61,44 @@ struct MdArgs {
 constexpr int kKdChunk = 4096;  // sites per kick/drift block (16 per thread)
 
 // local site id <-> lattice coordinates (lattice units: (2cx + p, 2cy + p, 2cz + p))
-// (32-bit division: a replica holds fewer than 2^31 sites)
 __device__ __forceinline__ void site_lat(long long s, int nx, int ny, int &X, int &Y, int &Z)
 {
-    const int si = (int)s;
-    int x2 = si % (2 * nx);
-    int r = si / (2 * nx);
-    int cy = r % ny, cz = r / ny;
+    int x2 = (int)(s % (2 * nx));
+    long long r = s / (2 * nx);
+    int cy = (int)(r % ny), cz = (int)(r / ny);
     int p = x2 & 1;
     X = x2;
     Y = 2 * cy + p;
     Z = 2 * cz + p;
 }
 
+// the same with 32-bit divisions (a replica holds fewer than 2^31 sites),
+// for the run-away pair loops; the rare paths keep the 64-bit form, whose
+// division is a called routine with fewer live registers
+__device__ __forceinline__ void site_lat32(int s, int nx, int ny, int &X, int &Y, int &Z)
+{
+    const int x2 = s % (2 * nx);
+    const int r = s / (2 * nx);
+    const int p = x2 & 1;
+    X = x2;
+    Y = 2 * (r % ny) + p;
+    Z = 2 * (r / ny) + p;
+}
+
 __device__ __forceinline__ int wrapi(int a, int n)
 {
-    // a neighbour walk stays within one period of [0, n) (offsets are
-    // shorter than the box): one add or subtract; other values take the
-    // remainder (an integer division, tens of instructions)
-    if (a >= 0 && a < n) return a;
-    if (a < 0 && a >= -n) return a + n;
-    if (a >= n && a < 2 * n) return a - n;
-    const int r = a % n;
+    int r = a % n;
     return r < 0 ? r + n : r;
+}
+
+// The same for a in [-n, 2n) -- a neighbour walk's cell index, whose offset
+// is shorter than the box (boxes have at least 6 cells, offsets reach 4
+// half-cells or 3 cells) -- by one add or subtract instead of an integer
+// remainder
+__device__ __forceinline__ int wrap_near(int a, int n)
+{
+    a += a < 0 ? n : 0;
+    return a >= n ? a - n : a;
 }
 
 // The hash function of Sec. 3 in lattice units: nearest site of the point
@@ -466,7 +481,7 @@ __device__ __forceinline__ AxisTiles axis_tiles(int c, int nn, int tt)
     AxisTiles r{-1, -1, -1, -1, 0};
     const int w = nn < 7 ? nn : 7;
     for (int o = 0; o < w; ++o) {
-        const int t = wrapi(c - 3 + o, nn) / tt;
+        const int t = wrap_near(c - 3 + o, nn) / tt;
         if (t == r.t0 || t == r.t1 || t == r.t2 || t == r.t3) continue;
         if (r.n == 0) r.t0 = t;
         else if (r.n == 1) r.t1 = t;
@@ -671,7 +686,7 @@ __global__ void __launch_bounds__(256) k_ra_gather(const __grid_constant__ RaGat
     for (int j = warp; j < n; j += nwarps) {
         int h = a.ra_home[B + j];
         int X, Y, Z;
-        site_lat(h, rd.nx, rd.ny, X, Y, Z);
+        site_lat32(h, rd.nx, rd.ny, X, Y, Z);
         const int hp = X & 1;
         const int hcx = X >> 1, hcy = (Y - hp) >> 1, hcz = (Z - hp) >> 1;
         T ujx = ra.ra_sx[B + j], ujy = ra.ra_sy[B + j], ujz = ra.ra_sz[B + j];
@@ -697,7 +712,7 @@ __global__ void __launch_bounds__(256) k_ra_gather(const __grid_constant__ RaGat
                 const int ox = rr % wx, oy = (rr / wx) % wy, oz = rr / (wx * wy);
                 const int cx = hcx - 3 + ox, cy = hcy - 3 + oy, cz = hcz - 3 + oz;
                 sb[b] = rd.site_base +
-                        (((long long)wrapi(cz, rd.nz) * rd.ny + wrapi(cy, rd.ny)) * rd.nx + wrapi(cx, rd.nx)) * 2 + q;
+                        (((long long)wrap_near(cz, rd.nz) * rd.ny + wrap_near(cy, rd.ny)) * rd.nx + wrap_near(cx, rd.nx)) * 2 + q;
                 nb[b][0] = 2 * cx + q - X; nb[b][1] = 2 * cy + q - Y; nb[b][2] = 2 * cz + q - Z;
                 ok[b] = c < W && ra.sid[c < W ? sb[b] : rd.site_base] >= 0;
             }
@@ -763,7 +778,7 @@ __global__ void __launch_bounds__(256) k_ra_gather(const __grid_constant__ RaGat
             if (indexed && (k & 31) != lane) continue;
             if (k == j) continue;
             int Xk, Yk, Zk;
-            site_lat(a.ra_home[B + k], rd.nx, rd.ny, Xk, Yk, Zk);
+            site_lat32(a.ra_home[B + k], rd.nx, rd.ny, Xk, Yk, Zk);
             int nx_ = Xk - X, ny_ = Yk - Y, nz_ = Zk - Z;
             nx_ -= (nx_ > rd.nx) ? Lx : 0;
             nx_ += (nx_ < -rd.nx) ? Lx : 0;

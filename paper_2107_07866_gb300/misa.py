@@ -99,6 +99,8 @@ def lib():
         L.misa_step.argtypes = [C.c_void_p, C.c_int]
         L.misa_step_energies.argtypes = [C.c_void_p, C.c_int]
         L.misa_get_energies.argtypes = [C.c_void_p, _D, _D, C.c_void_p]
+        L.misa_get_energies_async.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+        L.misa_wait_outputs.argtypes = [C.c_void_p]
         for name in ("misa_get_positions", "misa_get_velocities", "misa_get_forces", "misa_get_density"):
             getattr(L, name).argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
         L.misa_get_site_map.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, _I64]
@@ -302,6 +304,19 @@ class Sim:
         e = (np.empty(self.natoms) if out is None else out) if per_atom else None
         self._check(lib().misa_get_energies(self.h, C.byref(pe), C.byref(ke), _ptr(e)))
         return (pe.value, ke.value, e) if per_atom else (pe.value, ke.value)
+
+    def energies_async(self, out):
+        """E_i of every atom into out (float64, natoms; pinned host memory
+        for a copy that runs beside the following calls) without waiting;
+        out holds them once wait_outputs() has returned."""
+        if len(out) < self.natoms:
+            raise ValueError("out must hold natoms values")
+        self._check(lib().misa_get_energies_async(self.h, _ptr(out), len(out)))
+        return out
+
+    def wait_outputs(self):
+        """Waits for the copies started by energies_async."""
+        self._check(lib().misa_wait_outputs(self.h))
 
     def _get(self, fn, width, out=None):
         if out is None:

@@ -563,3 +563,39 @@ def test_runaway_index_follows_state_changes(misa, pot, prec, nint, tmp_path):
         ref_c = fields(t)
     for a_, b_ in zip(got_c, ref_c):
         np.testing.assert_array_equal(a_, b_)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_energies_async_equal_synchronous_read(misa, pot, prec):
+    # misa_get_energies_async hands back, once misa_wait_outputs has
+    # returned, bitwise the E_i that misa_get_energies reads; steps issued
+    # after it run beside the copy and do not disturb it; a second call
+    # waits for the first copy before it overwrites the handle's buffer
+    import torch
+    n = 8
+    x0 = synth.cascade_snapshot(n, n, n, 0.1, 6, 2, 13)
+    v0 = synth.maxwell_velocities(len(x0), 600.0, M, 7)
+    ref = []
+    with misa.Sim(pot, n, precision=prec, dx_max=0.02, reassign_period=3) as s:
+        s.set_state(x0, v0)
+        for _ in range(2):
+            s.step(4, energies=True)
+            ref.append(s.energies(per_atom=True)[2].copy())
+    bufs = [torch.zeros(len(x0), dtype=torch.float64).pin_memory() for _ in range(2)]
+    with misa.Sim(pot, n, precision=prec, dx_max=0.02, reassign_period=3) as s:
+        s.set_state(x0, v0)
+        for k in range(2):
+            s.step(4, energies=True)
+            s.energies_async(bufs[k])
+        s.step(3)  # runs beside the second copy
+        s.wait_outputs()
+        for k in range(2):
+            np.testing.assert_array_equal(bufs[k].numpy(), ref[k])
+        # without a preceding energy step the call evaluates the potential
+        pe, _, e = s.energies(per_atom=True)
+        out = np.zeros(len(x0))
+        s.step(1)
+        s.energies_async(out)
+        s.wait_outputs()
+        _, _, e1 = s.energies(per_atom=True)
+        np.testing.assert_array_equal(out, e1)
