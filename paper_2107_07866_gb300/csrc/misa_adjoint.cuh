@@ -28,9 +28,6 @@
 
 namespace misa {
 
-// the bcc lattice vectors for runtime-indexed device loops
-static __constant__ LVecTable c_lvec = kLVec;
-
 // The upper half of every shell of kLVec: within a shell the vectors are
 // sorted by (z, y, x), an order that negation reverses, so the second half
 // holds exactly the vectors whose (z, y, x) is lexicographically positive.
@@ -68,7 +65,34 @@ constexpr bool lvec_half_ok()
 constexpr LVecTable kLVecHalf = make_lvec_half();
 static_assert(lvec_half_ok() && kLVecHalf.shell_begin[kLVecHalf.nshell] == kNVec / 2,
               "each shell splits into a negative and a positive half");
-static __constant__ LVecTable c_lvec_half = kLVecHalf;
+
+// One offset of the per-site walks with what every candidate derives from
+// it: the cell shifts along y and z from a site of parity 0 and 1, |n|^2,
+// and n and |n|^2 as (exact) floating-point values, so that the walk
+// computes no shift and converts no integer per candidate
+struct WalkVec {
+    int x, n2;
+    int sy[2], sz[2];
+    float fx, fy, fz, fn2;
+};
+struct WalkTable {
+    WalkVec v[kNVec];
+};
+
+constexpr WalkTable make_walk(const LVecTable &t, int count)
+{
+    WalkTable w{};
+    for (int k = 0; k < count; ++k) {
+        const LVec &o = t.v[k];
+        w.v[k] = WalkVec{o.x, o.n2, {cell_shift(0, o.y), cell_shift(1, o.y)}, {cell_shift(0, o.z), cell_shift(1, o.z)},
+                         (float)o.x, (float)o.y, (float)o.z, (float)o.n2};
+    }
+    return w;
+}
+// the bcc lattice vectors (all, and the upper half of every shell) for the
+// runtime-indexed walks
+static __constant__ WalkTable c_walk = make_walk(kLVec, kNVec);
+static __constant__ WalkTable c_walk_half = make_walk(kLVecHalf, kNVec / 2);
 
 // |n| S = xint + xfrac for every |n|^2 <= kMaxN2 (S: knot index per lattice
 // unit), split on the host in FP64 so that the FP32 pair geometry needs no
@@ -129,15 +153,16 @@ struct AdjPair {
 // split into integer and fraction) plus (r - |n|) S with
 // r - |n| = q / (r + |n|), q = (2n + d).d: full precision in t also in FP32
 // (x is near 2000, where a plain FP32 r S keeps only ~1e-4 of t).
+// (n given as exact floating-point values nxf, nyf, nzf and |n|^2 as n2
+// and n2f, so that a walk over a fixed offset table converts nothing)
 template <typename T, typename A>
-__device__ __forceinline__ bool adj_pair(const A &a, int nx, int ny, int nz, T dx, T dy, T dz, bool ra, long long j,
-                                         AdjPair<T> &P)
+__device__ __forceinline__ bool adj_pair_n(const A &a, T nxf, T nyf, T nzf, int n2, T n2f, T dx, T dy, T dz, bool ra,
+                                           long long j, AdjPair<T> &P)
 {
-    const T q = ((T)(2 * nx) + dx) * dx + ((T)(2 * ny) + dy) * dy + ((T)(2 * nz) + dz) * dz;
-    const int n2 = nx * nx + ny * ny + nz * nz;
-    const T r2 = (T)n2 + q;
+    const T q = ((T)2 * nxf + dx) * dx + ((T)2 * nyf + dy) * dy + ((T)2 * nzf + dz) * dz;
+    const T r2 = n2f + q;
     if (!(r2 < a.rc2)) return false;
-    const T rx = (T)nx + dx, ry = (T)ny + dy, rz = (T)nz + dz;
+    const T rx = nxf + dx, ry = nyf + dy, rz = nzf + dz;
     P.ra = ra;
     P.j = j;
     P.floor_hit = r2 < a.rfloor2;
@@ -186,6 +211,14 @@ __device__ __forceinline__ bool adj_pair(const A &a, int nx, int ny, int nz, T d
     return true;
 }
 
+template <typename T, typename A>
+__device__ __forceinline__ bool adj_pair(const A &a, int nx, int ny, int nz, T dx, T dy, T dz, bool ra, long long j,
+                                         AdjPair<T> &P)
+{
+    const int n2 = nx * nx + ny * ny + nz * nz;
+    return adj_pair_n<T>(a, (T)nx, (T)ny, (T)nz, n2, (T)n2, dx, dy, dz, ra, j, P);
+}
+
 // Visits the array-site neighbours j of array atom i (replica-local site
 // ls, displacement ui, half-lattice x index x2 and cell row cy, cz) inside
 // rc through the offset vectors: all of them, or with HALF only those along
@@ -199,15 +232,17 @@ __device__ __forceinline__ void visit_site_array(const A &a, const RepDesc &rd, 
     const int nv = HALF ? a.nvec / 2 : a.nvec;
 #pragma unroll 4
     for (int k = 0; k < nv; ++k) {
-        const LVec o = HALF ? c_lvec_half.v[k] : c_lvec.v[k];
+        const WalkVec &o = HALF ? c_walk_half.v[k] : c_walk.v[k];
         const int tx = wrap_near(x2 + o.x, 2 * rd.nx);
-        const int ty = wrap_near(cy + cell_shift(p, o.y), rd.ny);
-        const int tz = wrap_near(cz + cell_shift(p, o.z), rd.nz);
+        const int ty = wrap_near(cy + o.sy[p], rd.ny);
+        const int tz = wrap_near(cz + o.sz[p], rd.nz);
         // 32-bit index arithmetic: a handle holds fewer than 2^31 sites
         const int t = (int)rd.site_base + ((tz * rd.ny + ty) * rd.nx) * 2 + tx;
         if (a.sid[t] < 0) continue;
         AdjPair<T> P;
-        if (adj_pair<T>(a, o.x, o.y, o.z, a.ux[t] - uix, a.uy[t] - uiy, a.uz[t] - uiz, false, t, P)) fn(P);
+        if (adj_pair_n<T>(a, (T)o.fx, (T)o.fy, (T)o.fz, o.n2, (T)o.fn2, a.ux[t] - uix, a.uy[t] - uiy, a.uz[t] - uiz,
+                          false, t, P))
+            fn(P);
     }
 }
 
