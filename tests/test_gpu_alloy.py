@@ -195,7 +195,13 @@ def test_alloy_energy_step_equals_separate_evaluation(misa, prec):
             s.set_species(al, t)
             s.set_state(x, v)
             s.step(6, energies=energies)
+            if energies:
+                # the asynchronous read-out of the same energies
+                e_async = np.zeros(len(x))
+                s.energies_async(e_async)
+                s.wait_outputs()
             pe, ke, e = s.energies(per_atom=True)
             out.append((s.positions(), pe, ke, e))
     for a_, b_ in zip(out[0], out[1]):
         np.testing.assert_array_equal(a_, b_)
+    np.testing.assert_array_equal(e_async, out[1][3])

@@ -599,3 +599,17 @@ def test_energies_async_equal_synchronous_read(misa, pot, prec):
         s.wait_outputs()
         _, _, e1 = s.energies(per_atom=True)
         np.testing.assert_array_equal(out, e1)
+
+
+def test_destroy_waits_for_async_energies(misa, pot):
+    # closing the handle right after misa_get_energies_async waits for the
+    # copy: the host buffer holds the energies afterwards
+    import torch
+    n = 8
+    x0 = synth.thermal_snapshot(n, n, n, 0.1, 17)
+    buf = torch.zeros(len(x0), dtype=torch.float64).pin_memory()
+    with misa.Sim(pot, n, precision="fp32") as s:
+        s.set_state(x0)
+        ref = s.energies(per_atom=True)[2].copy()
+        s.energies_async(buf)
+    np.testing.assert_array_equal(buf.numpy(), ref)
