@@ -187,8 +187,11 @@ __device__ __forceinline__ void force_pair_pa(const PShell &sh, const PGeom &g, 
     arg_p(sh, g.q, S2, nwin, t, rs, ia, ib);
     const int ja = (int)(ty & 0xffu), jb = (int)(ty >> 8);
     const int pa = alloy_pair(si.ta, ja, tx.nsp) * tx.n + ia, pb = alloy_pair(si.tb, jb, tx.nsp) * tx.n + ib;
-    const float4 dja = tex4(tx.fd, ja * tx.n + ia), djb = tex4(tx.fd, jb * tx.n + ib);
+    // rho' of the neighbour's species: the site's own fetch when the two
+    // species agree (the pass is bound by texture fetches)
     const float4 dia = tex4(tx.fd, si.oa + ia), dib = tex4(tx.fd, si.ob + ib);
+    const float4 dja = ja == si.ta ? dia : tex4(tx.fd, ja * tx.n + ia);
+    const float4 djb = jb == si.tb ? dib : tex4(tx.fd, jb * tx.n + ib);
     const float4 dpa = tex4(tx.pd, pa), dpb = tex4(tx.pd, pb);
     const float2 dfj = make_float2(quad(dja, t.x), quad(djb, t.y));
     const float2 dfi = make_float2(quad(dia, t.x), quad(dib, t.y));
