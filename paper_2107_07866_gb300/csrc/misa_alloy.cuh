@@ -103,8 +103,9 @@ struct AlloyForceFn {
         const T Fpj = P.ra ? a.ra_fp[P.j] : a.fp[P.j];
         const size_t sg = (size_t)P.seg;
         const int pr = alloy_pair(ti, tj, a.nsp);
-        const T dfj = quad_at<T>(a.tfd[(size_t)tj * a.n + sg], P.t);
         const T dfi = quad_at<T>(a.tfd[(size_t)ti * a.n + sg], P.t);
+        // the same function when the species agree: no second read or evaluation
+        const T dfj = tj == ti ? dfi : quad_at<T>(a.tfd[(size_t)tj * a.n + sg], P.t);
         const T dph = quad_at<T>(a.tpd[(size_t)pr * a.n + sg], P.t);
         // Eq. eam_force_ij; the unit vector is zero below r_floor
         const T s = Fpi * dfj + Fpj * dfi + dph;

@@ -235,7 +235,7 @@ struct misa_sim {
     bool capturing = false;
     // kick/drift block map (replica, first site) and its host copy
     int2 *kd_map = nullptr;
-    int kd_blocks = 0;
+    int kd_blocks = 0, kd_chunk = 0;
     std::vector<int2> kd_host;
 };
 
@@ -316,6 +316,7 @@ MdArgs<T> md_args(misa_sim *s)
     m.reps = s->reps_d;
     m.nrep = s->nrep;
     m.kd_map = s->kd_map;
+    m.kd_chunk = s->kd_chunk;
     m.sid = s->sid;
     m.ux = s->u[0]; m.uy = s->u[1]; m.uz = s->u[2];
     m.sx = (T *)s->s[0]; m.sy = (T *)s->s[1]; m.sz = (T *)s->s[2];
@@ -915,11 +916,13 @@ int create_impl(misa_sim *s)
     size_t Tb = sizeof(T);
     s->reps_d = (RepDesc *)dalloc(s, sizeof(RepDesc) * s->nrep);
     s->sc = (DevScalars *)dalloc(s, sizeof(DevScalars) * s->nrep);
-    // kick/drift: one block per kKdChunk sites of each replica, so that the
+    // kick/drift: one block per kd_chunk sites of each replica, so that the
     // sweep's blocks carry equal work whatever the replicas' sizes
+    s->kd_chunk = kKdChunkMax;
+    while (s->kd_chunk > kKdChunkMin && s->ns / s->kd_chunk < 8LL * s->nsm) s->kd_chunk /= 2;
     s->kd_host.clear();
     for (int r = 0; r < s->nrep; ++r)
-        for (long long b = 0; b < s->reps[r].ns; b += kKdChunk) s->kd_host.push_back(make_int2(r, (int)b));
+        for (long long b = 0; b < s->reps[r].ns; b += s->kd_chunk) s->kd_host.push_back(make_int2(r, (int)b));
     s->kd_blocks = (int)s->kd_host.size();
     s->kd_map = (int2 *)dalloc(s, sizeof(int2) * s->kd_host.size());
     if (!s->kd_map) return fail(s, MISA_EOOM, "device allocation failed (kick/drift map)");

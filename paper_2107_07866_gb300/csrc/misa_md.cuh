@@ -53,12 +53,15 @@ struct MdArgs {
     int reassign_period;
     double acc_conv;  // eV/A -> A/fs^2
     double mass;
-    // kick/drift blocks: block b sweeps sites [y, y + kKdChunk) of replica x
+    // kick/drift blocks: block b sweeps sites [y, y + kd_chunk) of replica x
     // (block counts proportional to the replicas' sizes)
     const int2 *kd_map;
+    int kd_chunk;
 };
 
-constexpr int kKdChunk = 4096;  // sites per kick/drift block (16 per thread)
+// sites per kick/drift block: 4,096 (16 per thread), fewer for a small
+// handle so that its blocks still fill two waves of four CTAs per SM
+constexpr int kKdChunkMax = 4096, kKdChunkMin = 512;
 
 // local site id <-> lattice coordinates (lattice units: (2cx + p, 2cy + p, 2cz + p))
 __device__ __forceinline__ void site_lat(long long s, int nx, int ny, int &X, int &Y, int &Z)
@@ -243,7 +246,7 @@ __global__ void __launch_bounds__(256, 4) k_kick_drift(MdArgs<T> m)
     const double dt = sc->dt, hdt = 0.5 * dt, dtl = dt * m.inv_half;
     const int base = sc->n_ra_old;
     const float skin2f = (float)m.skin2;
-    const long long lend = min(rd.ns, (long long)bm.y + kKdChunk);
+    const long long lend = min(rd.ns, (long long)bm.y + m.kd_chunk);
     for (long long ls = bm.y + threadIdx.x; ls < lend; ls += blockDim.x) {
         const long long s = rd.site_base + ls;
         int id = m.sid[s];
