@@ -56,13 +56,13 @@ BYTES_FORCE_SITE = 84
 # DRAM traffic of the force pass (k_force_p) per launch at the 54M-atom
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by the kernel sources it was measured on.
-NCU_FORCE_TRAFFIC = {"source_sha": "92a28ec4bcd64480", "bytes_per_launch": 4.8501e9,
-                     "note": "k_force_p<8,8,12> at 300^3 cells: 2.957e9 B read + 1.893e9 B written per launch "
+NCU_FORCE_TRAFFIC = {"source_sha": "ed485315566d1dd6", "bytes_per_launch": 4.8495e9,
+                     "note": "k_force_p<8,8,12> at 300^3 cells: 2.956e9 B read + 1.893e9 B written per launch "
                              "(mean of 3 launches), 89.8 B/site vs 84 algorithmic"}
 # Shared-memory (LSU) and texture wavefronts per site of the two gathers from
 # one ncu capture of the 2M-atom case (equilibrated crystal), same keying;
 # the L1 data pipe serves one wavefront per SM per clock.
-NCU_WAVEFRONTS = {"source_sha": "92a28ec4bcd64480", "density": (27.4, 16.4), "force": (37.5, 23.6)}
+NCU_WAVEFRONTS = {"source_sha": "ed485315566d1dd6", "density": (27.4, 16.4), "force": (37.5, 23.6)}
 
 
 def kernel_source_sha():
